@@ -1,0 +1,91 @@
+"""The benchmark workloads as seeded generators.
+
+* ``tiny_config``: 64 x 64 root cells of 10 m, 25 % of them split and 25 % of
+  those children split again (10 / 5 / 2.5 m cells); fBm amplitude 500 m; one
+  256^2 cascade, a 320 x 240 image, one camera 300 m above the ground,
+  pitched down 30 deg, 60 deg vertical field of view.
+* ``dem_config``: 4096^2 finest-equivalent cells of 10 m (256^2 root cells of
+  160 m, 5 levels) refined by terrain curvature to about 4.5 M leaves (the
+  Florence scenario's cell count, Table 1); fBm amplitude 2000 m; four
+  2048^2 cascades split with lambda = 0.5; a 1920 x 1080 image along a
+  120-frame flight path 200-1500 m above the ground.
+* ``precision_config``: ``tiny_config`` with the domain moved to a world
+  origin of (5e6, 5e6) m, which FP32 cannot hold to centimetres.
+* ``batch_config``: independent tiles of uneven finest size with 1-4
+  cascades each and a 960 x 540 view per tile.
+
+All use a Gaussian RBF with sigma = 1.5 cell sizes truncated at 3 cell sizes.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .cameras import Camera, fixed_camera, flight_path
+from .fbm import FBm
+from .quadtree import Quadtree, curvature_quadtree, random_split_quadtree
+
+RBF_SIGMA = 1.5
+RBF_RADIUS = 3.0
+
+
+@dataclass
+class Scene:
+    name: str
+    tree: Quadtree
+    fbm: FBm
+    sigma: float
+    radius: float
+    cameras: list = field(default_factory=list)
+
+
+def tiny_config(seed: int = 1, origin=(0.0, 0.0), shuffle=True) -> Scene:
+    fbm = FBm(seed, amplitude=500.0, wavelength=640.0)
+    tree = random_split_quadtree(64, 10.0, (0.25, 0.25), fbm, seed, origin=origin,
+                                 shuffle=shuffle)
+    cam = fixed_camera(tree, fbm, (320.0, 80.0), 300.0, 90.0, -30.0, 60.0, 320, 240,
+                       n_cascades=1, cascade_size=256, znear=1.0, zfar=1.0e4)
+    return Scene("tiny", tree, fbm, RBF_SIGMA, RBF_RADIUS, [cam])
+
+
+def precision_config(seed: int = 1) -> Scene:
+    s = tiny_config(seed, origin=(5.0e6, 5.0e6))
+    s.name = "precision"
+    return s
+
+
+def dem_config(seed: int = 2, n_frames: int = 120, target_leaves: int = 4_500_000,
+               root_n: int = 256, cascade_size: int = 2048, width: int = 1920,
+               height: int = 1080) -> Scene:
+    fbm = FBm(seed, amplitude=2000.0, wavelength=10240.0 * root_n / 256)
+    tree = curvature_quadtree(root_n, root_n, 160.0, 4, fbm, target_leaves, seed)
+    cams = flight_path(tree, fbm, seed, n_frames, width, height, n_cascades=4,
+                       cascade_size=cascade_size, split_lambda=0.5)
+    return Scene("dem", tree, fbm, RBF_SIGMA, RBF_RADIUS, cams)
+
+
+def batch_config(seed: int = 4, n_tiles: int = 64, min_side: int = 256,
+                 max_side: int = 4096, width: int = 960, height: int = 540,
+                 leaf_frac: float = 0.3) -> list:
+    """Independent tiles: finest side log-uniform in [min_side, max_side],
+    10 m finest cells, curvature refinement to ``leaf_frac`` of the finest
+    count, 1-4 cascades of 512^2-2048^2 and one camera each."""
+    rng = np.random.default_rng(seed)
+    scenes = []
+    for t in range(n_tiles):
+        side = int(2 ** np.round(rng.uniform(np.log2(min_side), np.log2(max_side))))
+        levels = 4 if side >= 256 else 2
+        root_n = max(side >> levels, 1)
+        fbm = FBm(seed * 100 + t, amplitude=float(rng.uniform(300, 2000)),
+                  wavelength=side * 10.0 / 4)
+        tree = curvature_quadtree(root_n, root_n, 10.0 * (1 << levels), levels, fbm,
+                                  max(int(leaf_frac * side * side), root_n * root_n),
+                                  seed * 100 + t)
+        n_c = int(rng.integers(1, 5))
+        n_tex = int(2 ** rng.integers(9, 12))
+        cam = flight_path(tree, fbm, seed * 100 + t, 2, width, height, n_c, n_tex,
+                          split_lambda=0.5)[0]
+        scenes.append(Scene(f"tile{t}", tree, fbm, RBF_SIGMA, RBF_RADIUS, [cam]))
+    return scenes

@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Frame benchmark of the adaptive-heightfield renderer on GB300.
+
+A step is one frame of the whole hot path on the DEM-scale workload
+(4.5 M quadtree leaves over 40.96 km, four 2048^2 FP32 cascades split with
+lambda = 0.5, a 1920 x 1080 image, frames of a seeded 120-frame flight
+path): host cascade fit, visible rows + RBF discretization, max mipmap,
+ray cast.  Inputs (the quadtree and its influence lists) are resident in
+HBM; the L2 is flushed between steps and each step is timed with CUDA
+events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line is printed by rank 0.  ``--impl reference`` times the CPU
+FP64 oracle on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frame ms (RBF discretize + ray cast), Grays/s, Gtexel/s; p99 latency"
+WORKLOAD = "dem: 4096^2-equivalent quadtree (10-160 m cells, 4.5 M leaves), 4x2048^2 FP32 cascades, 1920x1080, 120-frame flight"
+
+# Nominal sm_103a unit counts per SM and clock: FP32 lanes and MUFU (ex2) lanes.
+SMS = 152
+FP32_PER_SM = 128
+MUFU_PER_SM = 16
+FP32_OPS_PER_TERM = 9   # 2 sub, d^2 (mul + fma), scale, -K, max, sum, fma
+
+
+def frame_schedule(n_frames: int, steps: int, rank: int, world: int) -> list:
+    """Frames rendered by `rank`: each rank walks the flight path from its own
+    offset (weak scaling: the same number of frames per rank)."""
+    off = (rank * n_frames) // max(world, 1)
+    return [(off + k) % n_frames for k in range(steps)]
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the baseline, and the reference arm)
+
+def oracle_frame_sample(scene, cam, cells, n_texels: int, n_rays: int, seed: int) -> dict:
+    """Time the FP64 oracle on a sample of one frame and extrapolate to the
+    whole frame: Eq. 2 at `n_texels` random visible texels (scaled to all
+    visible texels of the four cascades), the max mipmaps in full, and
+    `n_rays` random pixels (scaled to 1920 x 1080).  The ray sample runs on
+    cascade textures filled from the terrain generator at the texel centres,
+    which have the traversal structure of the discretized surface."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    view = oracle.fit(cam, scene.tree, cells)
+    t_fit = time.perf_counter() - t0
+    n_vis, vis_list, texs, rcs = 0, [], [], []
+    for c in range(cam.n_cascades):
+        cas = view.cas[c]
+        vis, _ = oracle.mask(cas, cells)
+        vis = vis.reshape(cas.N, cas.N).astype(bool)
+        n_vis += int(vis.sum())
+        vis_list.append(vis)
+        xs = cas.ox + np.arange(cas.N) * cas.h
+        ys = cas.oy + np.arange(cas.N) * cas.h
+        tex = scene.fbm.grid(xs, ys).astype(np.float32)
+        tex[~vis] = -np.inf
+        texs.append(tex)
+        rcs.append(type("RC", (), dict(ox=cas.ox, oy=cas.oy, h=cas.h, near=cas.near,
+                                      far_ext=cas.far_ext, N=cas.N)))
+    # Eq. 2 on a sample of visible texels
+    weights = np.array([v.sum() for v in vis_list], float)
+    cas_pick = rng.choice(len(vis_list), size=n_texels, p=weights / weights.sum())
+    t_rbf = 0.0
+    for c in range(len(vis_list)):
+        k = int((cas_pick == c).sum())
+        if k == 0:
+            continue
+        jj, ii = np.nonzero(vis_list[c])
+        sel = rng.choice(jj.size, size=k, replace=True)
+        t0 = time.perf_counter()
+        oracle.texel_heights(view.cas[c], cells, scene.sigma, scene.radius, ii[sel], jj[sel])
+        t_rbf += time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for tex in texs:
+        oracle.maxmip(tex)
+    t_mip = time.perf_counter() - t0
+    px = rng.integers(0, cam.width, n_rays)
+    py = rng.integers(0, cam.height, n_rays)
+    t0 = time.perf_counter()
+    oracle.raycast(cam, scene.tree, rcs, texs, pixels=(px, py))
+    t_ray = time.perf_counter() - t0
+    npx = cam.width * cam.height
+    ms = 1e3 * (t_fit + t_rbf * n_vis / n_texels + t_mip + t_ray * npx / n_rays)
+    return {"frame_ms": ms, "visible_texels": n_vis, "sampled_s": t_fit + t_rbf + t_mip + t_ray,
+            "n_texels": n_texels, "n_rays": n_rays}
+
+
+def _oracle_sample_text(n_texels, n_rays):
+    return (f"per frame: Eq. 2 at {n_texels} random visible texels (scaled to all visible "
+            f"texels), full max mipmaps, {n_rays} random pixels (scaled to 1920x1080) on "
+            f"generator-filled cascade textures; FP64, OpenMP")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    oracle.build()
+    scene = workloads.dem_config(n_frames=args.frames)
+    cells = oracle.Cells(scene.tree)
+    frames = frame_schedule(args.frames, args.warmup + args.steps, 0, 1)
+    n_tex, n_ray = args.ref_texels, args.ref_rays
+    per = []
+    for k, f in enumerate(frames):
+        r = oracle_frame_sample(scene, scene.cameras[f], cells, n_tex, n_ray, seed=k)
+        if k >= args.warmup:
+            per.append(r["frame_ms"])
+    ms = statistics.mean(per)
+    cores = oracle.threads()
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 1, "parallelism": "none",
+                       "l2": "n/a (CPU)"},
+            "p50_ms": statistics.median(per), "p99_ms": _pct(per, 99),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": _oracle_sample_text(n_tex, n_ray)},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _pct(xs, p):
+    s = sorted(xs)
+    if not s:
+        return None
+    k = min(len(s) - 1, max(0, int(math.ceil(p / 100.0 * len(s))) - 1))
+    return s[k]
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2201_10887_gb300 import Renderer
+    from paper_2201_10887_gb300.renderer import camera_struct  # noqa: F401
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scene = workloads.dem_config(n_frames=args.frames)
+    cams = scene.cameras
+    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sched = frame_schedule(args.frames, args.steps, rank, world)
+    warm = frame_schedule(args.frames, args.warmup, rank, world)
+
+    for f in warm:
+        r.render(cams[f])
+    r.sync()
+
+    # algorithmic work of the scheduled frames (untimed counting pass)
+    work = {}
+    for f in sorted(set(sched)):
+        r.set_camera(cams[f])
+        r.discretize()
+        st = r.stats()
+        work[f] = (sum(st["visible_texels"]), sum(st["candidates"]), sum(st["influencers"]))
+    r.sync()
+
+    C, N = cams[0].n_cascades, cams[0].cascade_size
+    W, H = cams[0].width, cams[0].height
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in sched]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        wall0 = time.perf_counter()
+        for k, f in enumerate(sched):
+            flush.fill_(float(k))
+            e = ev[k]
+            e[0].record(stream)
+            r.set_camera(cams[f])
+            r.discretize()
+            e[1].record(stream)
+            r.build_maxmip()
+            e[2].record(stream)
+            r.raycast()
+            e[3].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    r.sync()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    disc_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    mip_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    ray_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    tot_ms = reduce_max(sum(step_ms), world)
+    frames_total = len(sched) * world
+    value = tot_ms / frames_total
+
+    # end to end through the public API with host buffers: camera in, t and hit out
+    t_host = torch.empty(W * H, dtype=torch.float32, pin_memory=True)
+    h_host = torch.empty(W * H, dtype=torch.uint8, pin_memory=True)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sched]
+    torch.cuda.synchronize(dev)
+    for k, f in enumerate(sched):
+        flush.fill_(float(k))
+        a, b = e2e_ev[k]
+        a.record(stream)
+        t_dev, hit_dev = r.render(cams[f])
+        t_host.copy_(t_dev.view(-1), non_blocking=True)
+        h_host.copy_(hit_dev.view(-1), non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev), world) / frames_total
+
+    vis = sum(work[f][0] for f in sched)
+    cand = sum(work[f][1] for f in sched)
+    infl = sum(work[f][2] for f in sched)
+    peaks = load_peaks()
+    fclk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = min(MUFU_PER_SM * SMS * fclk, FP32_PER_SM * SMS * fclk / FP32_OPS_PER_TERM) / 1e9
+    mip_bytes = C * (4 * N * N + 4 * ((4 * (1 << (N - 2).bit_length()) ** 2 - 1) // 3))
+    kern = {
+        "discretize": {"ms": statistics.mean(disc_ms), "bound": "alu",
+                       "achieved": infl / (sum(disc_ms) * 1e-3) / 1e9, "peak": alu_peak,
+                       "unit": "Gterm/s"},
+        "maxmip": {"ms": statistics.mean(mip_ms), "bound": "hbm",
+                   "achieved": mip_bytes / (statistics.mean(mip_ms) * 1e-3) / 1e9,
+                   "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"},
+        "raycast": {"ms": statistics.mean(ray_ms)},
+    }
+    dom = max(("discretize", "maxmip"), key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["achieved"] / d["peak"], "traffic": None, "kernel": dom,
+                "peak_source": ("derived from unit counts at %d MHz" % int(fclk / 1e6)
+                                if d["bound"] == "alu" else peaks["source"])}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": len(sched),
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 1,
+                   "parallelism": f"replicas{world}" if world > 1 else "none",
+                   "l2": "flushed between steps (256 MB write outside the step events)",
+                   "frames": args.frames},
+        "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
+        "grays_per_s": W * H * len(sched) / (sum(step_ms) * 1e-3) / 1e9,
+        "gtexel_per_s": vis / (sum(disc_ms) * 1e-3) / 1e9,
+        "kernel_grays_per_s": W * H * len(sched) / (sum(ray_ms) * 1e-3) / 1e9,
+        "visible_texels_per_frame": vis / len(sched),
+        "candidates_per_texel": cand / max(vis, 1), "influencers_per_texel": infl / max(vis, 1),
+        "kernels": {k: {kk: vv for kk, vv in v.items()} for k, v in kern.items()},
+        "roofline": roofline,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 128,
+                "d2h_bytes_per_step": W * H * 5,
+                "note": "camera struct in (kernel parameters), t + hit copied to pinned host memory"},
+        "gpu_launches": 5 * len(sched),
+        "wall_s": wall,
+    }
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            cells = oracle.Cells(scene.tree)
+            res = oracle_frame_sample(scene, cams[sched[0]], cells, args.ref_texels * 4,
+                                      args.ref_rays * 4, seed=0)
+            line["cpu_baseline"] = {"value": res["frame_ms"], "unit": "ms", "cores": oracle.threads(),
+                                    "kind": "oracle",
+                                    "sample": _oracle_sample_text(args.ref_texels * 4, args.ref_rays * 4)
+                                    + f"; frame {sched[0]}; {res['sampled_s']:.1f} s of CPU work"}
+        print(json.dumps(line), flush=True)
+    r.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=240)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=120)
+    ap.add_argument("--ref-texels", type=int, default=3000)
+    ap.add_argument("--ref-rays", type=int, default=3000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build_library()
+        run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * hf.h -- C ABI of the GB300 adaptive-heightfield renderer.
+ *
+ * Implements the per-frame two-step method of Cornel, Horvath and Waser,
+ * "An Attempt of Adaptive Heightfield Rendering with Complex Interpolants
+ * Using Ray Casting" (2022):
+ *   step 1  view-dependent discretization: the truncated Gaussian RBF
+ *           approximation (Eq. 1, Eq. 2) of a quadtree heightfield is
+ *           evaluated at every visible texel of frustum-split cascade
+ *           textures fitted to the view (Section 3, Section 4);
+ *   step 2  a maximum mipmap per cascade, then one ray per pixel through the
+ *           cascades with empty-space skipping and exact ray/bilinear-patch
+ *           intersection, blended where cascades overlap (Section 5).
+ *
+ * Conventions
+ *   - Every function returns HF_OK (0) or a negative HF_ERR_* code; no C++
+ *     exception crosses this boundary.  hf_last_error() describes the most
+ *     recent failure of the calling thread.
+ *   - The library never allocates device memory.  The caller allocates the
+ *     sizes hf_query_bytes() reports and keeps ownership; buffers must stay
+ *     alive and untouched while work that uses them is in flight.
+ *   - Host arrays passed in are copied before the call returns.
+ *   - `stream` is a cudaStream_t passed as an opaque pointer (NULL = the
+ *     legacy default stream).  Device work is enqueued asynchronously on it;
+ *     errors detected on the device are reported by hf_sync().
+ *   - Geometry: the heightfield domain is the rectangle
+ *     [0, root_nx*root_cell] x [0, root_ny*root_cell] in domain-local metres,
+ *     placed at (origin_x, origin_y) in world coordinates; z is up and is not
+ *     offset.  World positions are FP64 on the host; device work uses FP32
+ *     domain-local (or cascade-local) coordinates.
+ *   - Cascade texel (i, j) of a cascade with origin (ox, oy) and spacing h
+ *     sits at (ox + i h, oy + j h) domain-local; textures are N x N FP32,
+ *     row-major (index j*N + i).  Invisible texels hold -infinity.
+ *   - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HF_OK = 0,
+    HF_ERR_ARG = -1,     /* invalid argument or inconsistent input data */
+    HF_ERR_STATE = -2,   /* call out of order (e.g. ray cast before the mip build) */
+    HF_ERR_NOMEM = -3,   /* a caller buffer is smaller than required */
+    HF_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed */
+    HF_ERR_TIMEOUT = -5, /* a bounded device-side loop gave up; results are invalid */
+    HF_ERR_DATA = -6     /* device-side consistency check failed */
+};
+
+enum { HF_PREC_FP32 = 0, HF_PREC_FP16 = 1, HF_PREC_BF16 = 2 };
+
+#define HF_MAX_LEVEL 15
+#define HF_MAX_CASCADES 8
+#define HF_MAX_POLY 32
+#define HF_MAX_VIEWS 256
+
+/* Quadtree geometry (Section 2: an adaptive grid of square cells). */
+typedef struct {
+    double origin_x, origin_y; /* world position of the domain's lower corner (m) */
+    double root_cell;          /* edge of a level-0 cell (m) */
+    int32_t root_nx, root_ny;  /* level-0 grid size */
+    int32_t max_level;         /* deepest level, 0..HF_MAX_LEVEL; level-L cells have edge root_cell / 2^L */
+} hf_quadtree_desc;
+
+/* One leaf cell: level L, integer position (ix, iy) on level L's grid
+ * (0 <= ix < root_nx * 2^L), and the data value at the cell centre
+ * (Section 2).  16 bytes, no padding. */
+typedef struct {
+    int32_t level, ix, iy;
+    float value;
+} hf_leaf;
+
+/* Truncated Gaussian RBF (Eq. 1).  Cell i influences p when
+ * |p_i - p| < radius * c_i, with weight exp(-(|p_i - p|/c_i)^2 / (2 sigma^2))
+ * - exp(-radius^2 / (2 sigma^2)).  The paper's setting is sigma = 1 with
+ * truncation at 3.5 sigma, i.e. radius = 3.5.  precision selects the
+ * arithmetic of the distance / exp evaluation (HF_PREC_*); sums are FP32.
+ * The lists of potentially influencing cells (Section 4) are kept per
+ * square "bucket": every leaf at or below level bucket_level is a bucket,
+ * coarser leaves are split into their level-bucket_level descendants so a
+ * list never covers more than one level-bucket_level cell.  bucket_level
+ * = -1 selects max(0, max_level - 2). */
+typedef struct {
+    double sigma;
+    double radius;
+    int32_t precision;
+    int32_t bucket_level;
+} hf_rbf_params;
+
+/* A view (Section 3, Section 5).  eye is in world coordinates; forward and
+ * up need not be unit or orthogonal (up is made orthogonal to forward).
+ * vfov in radians; znear/zfar are clip distances along forward.
+ * n_cascades textures of cascade_size^2 texels are fitted; split_lambda
+ * blends logarithmic (1) and uniform (0) splits; the far plane of every
+ * cascade but the last is pushed out by overlap_frac of its depth span. */
+typedef struct {
+    double eye[3];
+    double forward[3];
+    double up[3];
+    double vfov, znear, zfar;
+    int32_t width, height;
+    int32_t n_cascades, cascade_size;
+    double split_lambda, overlap_frac;
+} hf_camera;
+
+/* Fitted cascade (Section 3) plus the device buffers bound to it. */
+typedef struct {
+    double near_depth, far_depth, far_ext_depth; /* projected-depth band; far_ext includes the overlap */
+    int32_t n_poly;                              /* vertices of the cascade polygon; 0 = empty */
+    int32_t N;                                   /* texture side */
+    double poly[HF_MAX_POLY][2];                 /* CCW, domain-local */
+    double aabb[4];                              /* x0, y0, x1, y1 of the polygon */
+    int64_t snap_x, snap_y, snap_k;              /* ox = snap_x c_min, oy = snap_y c_min, extent = 2 snap_k c_min */
+    double ox, oy, extent, texel;                /* texel = extent / (N - 1) */
+    float* tex;                                  /* device, N*N FP32 heights, -inf where invisible */
+    float* mip;                                  /* device, max mipmap (see hf_build_maxmip) */
+    int32_t* spans;                              /* device, N rows x {first, last} visible column; last < first = none */
+    int64_t mip_floats;                          /* number of floats in mip */
+} hf_cascade_info;
+
+typedef struct hf_ctx hf_ctx;
+
+/* Validates the leaves (levels and indices in range, values finite, the
+ * leaves tile the domain exactly) and builds the quadtree on the host: a
+ * per-level occupancy bitmap, and for every leaf the exact size of its list
+ * of potentially influencing cells (Section 4: the set I depends only on
+ * the grid and is precomputed once).  Allocates host memory only.
+ * Returns HF_ERR_ARG on invalid input; *out is set only on success. */
+int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int64_t n_leaves,
+                       const hf_rbf_params* rbf, hf_ctx** out);
+
+/* Device bytes the caller must provide: persistent_bytes for
+ * hf_bind_persistent (quadtree + influence lists), per_view_bytes for one
+ * hf_set_camera with n_cascades textures of cascade_size^2 texels.  Either
+ * output pointer may be NULL. */
+int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
+                   size_t* persistent_bytes, size_t* per_view_bytes);
+
+/* Uploads the quadtree into dev_persistent (>= persistent_bytes, 256-byte
+ * aligned) and builds the influence lists on the device.  The buffer is
+ * owned by the caller and must outlive the context's device work.
+ * Synchronises `stream` before returning.  HF_ERR_NOMEM if too small. */
+int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* stream);
+
+/* Replaces the leaf values (e.g. a new water level) without rebuilding the
+ * tree; `values` is a host array in the order of the leaves given to
+ * hf_create_quadtree.  Enqueued on `stream`. */
+int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* stream);
+
+/* Fits the cascades of `cam` (Section 3) on the host in FP64 and binds
+ * dev_view (>= per_view_bytes for cam's cascade settings, 256-byte aligned)
+ * to view slot `view_slot` (0..HF_MAX_VIEWS-1).  Host work only. */
+int hf_set_camera(hf_ctx* ctx, int32_t view_slot, const hf_camera* cam, void* dev_view,
+                  size_t bytes);
+
+/* Step 1 (Section 3 mask, Section 4 Eq. 2): computes the visible-texel rows
+ * of every cascade and evaluates the RBF approximation at every visible
+ * texel; invisible texels are set to -infinity. */
+int hf_discretize_cascades(hf_ctx* ctx, int32_t view_slot, void* stream);
+
+/* Step 2a (Section 5, maximum mipmap of Tevs et al.): level 0 holds, per
+ * bilinear patch (texels i..i+1, j..j+1), the maximum of its four corners,
+ * or -inf if a corner is invisible; patches are padded with -inf to P x P,
+ * P the smallest power of two >= N-1; level k (P>>k)^2 entries hold the
+ * maximum of 2x2 entries of level k-1; levels are stored one after another,
+ * row-major. */
+int hf_build_maxmip(hf_ctx* ctx, int32_t view_slot, void* stream);
+
+/* Step 2b (Section 5): one ray per pixel, nearest cascade first; writes
+ * t_dev[y*width + x] = distance from the eye to the hit (FP32, NaN on a
+ * miss) and hit_dev[y*width + x] = 0 on a miss, else 1 + the index of the
+ * first cascade hit.  Pixel (0, 0) is the top-left corner.  In the overlap
+ * of cascades c and c+1 both are intersected and the hit distances are
+ * blended linearly across the overlap band. */
+int hf_raycast(hf_ctx* ctx, int32_t view_slot, float* t_dev, uint8_t* hit_dev, void* stream);
+
+/* Descriptor and device pointers of cascade c of a view slot. */
+int hf_get_cascade(const hf_ctx* ctx, int32_t view_slot, int32_t c, hf_cascade_info* out);
+
+/* Work counts of the last discretization of a view slot, per cascade:
+ * visible texels, list entries walked (the candidates of Section 4), and
+ * weighted-sum terms with w > 0 (the influencing set I of Eq. 2).  Runs a
+ * counting pass of the discretization on `stream` and waits for it; meant
+ * for measurement, not for the frame loop. */
+typedef struct {
+    int64_t visible_texels[HF_MAX_CASCADES];
+    int64_t candidates[HF_MAX_CASCADES];
+    int64_t influencers[HF_MAX_CASCADES];
+} hf_view_stats_t;
+int hf_view_stats(hf_ctx* ctx, int32_t view_slot, hf_view_stats_t* out, void* stream);
+
+/* Waits for `stream` and reports errors recorded on the device since the
+ * last hf_sync (HF_ERR_TIMEOUT, HF_ERR_DATA) or by the CUDA runtime. */
+int hf_sync(hf_ctx* ctx, void* stream);
+
+/* Frees the context's host memory.  Device buffers belong to the caller. */
+void hf_destroy(hf_ctx* ctx);
+
+/* Message for the calling thread's most recent error ("" if none). */
+const char* hf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

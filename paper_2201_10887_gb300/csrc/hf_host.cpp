@@ -1,0 +1,643 @@
+// Host side of the C ABI declared in include/hf.h: input validation, the
+// quadtree bitmaps, exact sizing of the influence lists (Section 4), buffer
+// layout, and the per-frame launch sequence.  Device memory is never
+// allocated here; the caller provides it.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hf_internal.h"
+
+using namespace hfi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(int e, const char* what) {
+    return fail(HF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(cudaError_t(e)));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-level occupancy bitmaps on the host (see hfi::Bitmaps).
+struct HostBitmaps {
+    std::vector<uint64_t> bits;
+    std::vector<uint32_t> prefix;
+    int64_t word_off[kMaxLevels + 1] = {};
+    int64_t base[kMaxLevels + 1] = {};
+    int32_t nx[kMaxLevels] = {};
+    int32_t ny[kMaxLevels] = {};
+    int max_level = 0;
+
+    void init(int64_t rnx, int64_t rny, int M) {
+        max_level = M;
+        int64_t off = 0;
+        for (int L = 0; L <= M; ++L) {
+            nx[L] = int32_t(rnx << L);
+            ny[L] = int32_t(rny << L);
+            word_off[L] = off;
+            off += (int64_t(nx[L]) * ny[L] + 63) / 64;
+        }
+        word_off[M + 1] = off;
+        bits.assign(size_t(off), 0ull);
+    }
+    bool test(int L, int64_t ix, int64_t iy) const {
+        const int64_t b = iy * nx[L] + ix;
+        return (bits[size_t(word_off[L] + (b >> 6))] >> (b & 63)) & 1ull;
+    }
+    void set(int L, int64_t ix, int64_t iy) {
+        const int64_t b = iy * nx[L] + ix;
+        bits[size_t(word_off[L] + (b >> 6))] |= 1ull << (b & 63);
+    }
+    void finalize() {
+        prefix.assign(bits.size(), 0u);
+        int64_t total = 0;
+        for (int L = 0; L <= max_level; ++L) {
+            base[L] = total;
+            uint32_t run = 0;
+            for (int64_t w = word_off[L]; w < word_off[L + 1]; ++w) {
+                prefix[size_t(w)] = run;
+                run += uint32_t(__builtin_popcountll(bits[size_t(w)]));
+            }
+            total += run;
+        }
+        base[max_level + 1] = total;
+    }
+    int64_t rank(int L, int64_t ix, int64_t iy) const {
+        const int64_t b = iy * nx[L] + ix;
+        const int64_t w = word_off[L] + (b >> 6);
+        return base[L] + prefix[size_t(w)] +
+               __builtin_popcountll(bits[size_t(w)] & ((1ull << (b & 63)) - 1ull));
+    }
+    Bitmaps view(const uint64_t* b, const uint32_t* p) const {
+        Bitmaps v;
+        std::memset(&v, 0, sizeof(v));
+        v.bits = b;
+        v.prefix = p;
+        for (int L = 0; L <= max_level + 1; ++L) {
+            v.word_off[L] = word_off[L];
+            v.base[L] = base[L];
+        }
+        for (int L = 0; L <= max_level; ++L) {
+            v.nx[L] = nx[L];
+            v.ny[L] = ny[L];
+        }
+        v.max_level = max_level;
+        return v;
+    }
+};
+
+struct ViewSlot {
+    int stage = 0;  // 1 fitted, 2 discretized, 3 mip built
+    hf_camera cam{};
+    double eye_local[3] = {0, 0, 0};
+    FitResult fit{};
+    char* dev = nullptr;
+    size_t bytes = 0;
+    float* tex[HF_MAX_CASCADES] = {};
+    float* mip[HF_MAX_CASCADES] = {};
+    int2* spans[HF_MAX_CASCADES] = {};
+    float* xs[HF_MAX_CASCADES] = {};
+    float* ys[HF_MAX_CASCADES] = {};
+};
+
+// Device layout of the persistent buffer.
+struct PersistentLayout {
+    size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx, total;
+};
+
+}  // namespace
+
+struct hf_ctx {
+    hf_quadtree_desc desc{};
+    hf_rbf_params rbf{};
+    int M = 0, B = 0;
+    int64_t n_leaves = 0, n_buckets = 0, n_cand = 0;
+    double c_fin = 0, c_min = 0, c_max = 0, zmin = 0, zmax = 0, width = 0, height = 0;
+    double reach_q[kMaxLevels] = {};
+    HostBitmaps leaves, buckets;
+    std::vector<float4> recs;      // sorted by (level, iy, ix)
+    std::vector<int64_t> perm;     // input position -> sorted index
+    std::vector<int64_t> offsets;  // n_buckets + 1
+    std::vector<float> staged;     // values in sorted order for hf_update_values
+    char* dev = nullptr;
+    size_t dev_bytes = 0;
+    PersistentLayout lay{};
+    std::unique_ptr<ViewSlot> views[HF_MAX_VIEWS];
+
+    PersistentLayout layout() const {
+        PersistentLayout l{};
+        size_t o = 0;
+        l.status = o; o = align256(o + sizeof(DevStatus));
+        l.lbits = o; o = align256(o + leaves.bits.size() * 8);
+        l.lprefix = o; o = align256(o + leaves.prefix.size() * 4);
+        l.bbits = o; o = align256(o + buckets.bits.size() * 8);
+        l.bprefix = o; o = align256(o + buckets.prefix.size() * 4);
+        l.recs = o; o = align256(o + size_t(n_leaves) * 16);
+        l.offsets = o; o = align256(o + size_t(n_buckets + 1) * 8);
+        l.idx = o; o = align256(o + size_t(n_cand) * 4);
+        l.total = o;
+        return l;
+    }
+    DevStatus* d_status() const { return reinterpret_cast<DevStatus*>(dev + lay.status); }
+    EnumTables enum_tables(bool device) const {
+        EnumTables t;
+        std::memset(&t, 0, sizeof(t));
+        t.leaves = device ? leaves.view(reinterpret_cast<const uint64_t*>(dev + lay.lbits),
+                                        reinterpret_cast<const uint32_t*>(dev + lay.lprefix))
+                          : leaves.view(leaves.bits.data(), leaves.prefix.data());
+        for (int L = 0; L < kMaxLevels; ++L) t.reach_q[L] = reach_q[L];
+        return t;
+    }
+    LookupTables lookup_tables(bool device) const {
+        LookupTables t;
+        std::memset(&t, 0, sizeof(t));
+        t.buckets = device ? buckets.view(reinterpret_cast<const uint64_t*>(dev + lay.bbits),
+                                          reinterpret_cast<const uint32_t*>(dev + lay.bprefix))
+                           : buckets.view(buckets.bits.data(), buckets.prefix.data());
+        t.bucket_level = B;
+        t.inv_c_fin = float(1.0 / c_fin);
+        t.nx_fin = buckets.nx[M];
+        t.ny_fin = buckets.ny[M];
+        return t;
+    }
+    ListsView lists() const {
+        ListsView v;
+        v.offsets = reinterpret_cast<const int64_t*>(dev + lay.offsets);
+        v.idx = reinterpret_cast<int32_t*>(dev + lay.idx);
+        v.recs = reinterpret_cast<float4*>(dev + lay.recs);
+        return v;
+    }
+};
+
+namespace {
+
+size_t per_view_bytes(int C, int N) {
+    size_t o = 0;
+    for (int c = 0; c < C; ++c) {
+        o = align256(o + size_t(N) * N * 4);
+        o = align256(o + size_t(mip_floats(N)) * 4);
+        o = align256(o + size_t(N) * 8);
+        o = align256(o + size_t(N) * 4);
+        o = align256(o + size_t(N) * 4);
+    }
+    return o;
+}
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+ViewSlot* get_view(hf_ctx* ctx, int32_t slot) {
+    if (!ctx || slot < 0 || slot >= HF_MAX_VIEWS || !ctx->views[slot]) return nullptr;
+    return ctx->views[slot].get();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hf_last_error(void) { return g_err.c_str(); }
+
+int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int64_t n_leaves,
+                       const hf_rbf_params* rbf, hf_ctx** out) {
+    if (!desc || !rbf || !out) return fail(HF_ERR_ARG, "null argument");
+    if (n_leaves < 1 || !leaves) return fail(HF_ERR_ARG, "no leaves");
+    const hf_quadtree_desc& d = *desc;
+    if (!(std::isfinite(d.origin_x) && std::isfinite(d.origin_y) && std::isfinite(d.root_cell) &&
+          d.root_cell > 0.0))
+        return fail(HF_ERR_ARG, "origin / root_cell must be finite, root_cell > 0");
+    if (d.root_nx < 1 || d.root_ny < 1) return fail(HF_ERR_ARG, "root grid must be at least 1x1");
+    if (d.max_level < 0 || d.max_level > HF_MAX_LEVEL)
+        return fail(HF_ERR_ARG, "max_level must be in [0, %d]", HF_MAX_LEVEL);
+    const int M = d.max_level;
+    const int64_t fnx = int64_t(d.root_nx) << M, fny = int64_t(d.root_ny) << M;
+    if (fnx > (int64_t(1) << 30) || fny > (int64_t(1) << 30) || fnx * fny > (int64_t(1) << 34))
+        return fail(HF_ERR_ARG, "finest grid %lld x %lld too large", (long long)fnx, (long long)fny);
+    if (!(std::isfinite(rbf->sigma) && rbf->sigma > 0.0 && std::isfinite(rbf->radius) && rbf->radius > 0.0))
+        return fail(HF_ERR_ARG, "sigma and radius must be finite and > 0");
+    if (rbf->precision < HF_PREC_FP32 || rbf->precision > HF_PREC_BF16)
+        return fail(HF_ERR_ARG, "unknown precision %d", rbf->precision);
+    if (rbf->bucket_level > M) return fail(HF_ERR_ARG, "bucket_level %d > max_level %d", rbf->bucket_level, M);
+
+    std::unique_ptr<hf_ctx> ctx(new hf_ctx);
+    ctx->desc = d;
+    ctx->rbf = *rbf;
+    ctx->M = M;
+    ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 2) : rbf->bucket_level;
+    ctx->n_leaves = n_leaves;
+    ctx->c_fin = d.root_cell / double(int64_t(1) << M);
+    ctx->width = d.root_cell * d.root_nx;
+    ctx->height = d.root_cell * d.root_ny;
+
+    // occupancy, duplicates, ranges
+    HostBitmaps& lf = ctx->leaves;
+    lf.init(d.root_nx, d.root_ny, M);
+    int lmin = M, lmax = 0;
+    float vmin = INFINITY, vmax = -INFINITY;
+    int64_t area = 0;
+    for (int64_t k = 0; k < n_leaves; ++k) {
+        const hf_leaf& l = leaves[k];
+        if (l.level < 0 || l.level > M) return fail(HF_ERR_ARG, "leaf %lld: level %d out of range", (long long)k, l.level);
+        if (l.ix < 0 || l.iy < 0 || l.ix >= lf.nx[l.level] || l.iy >= lf.ny[l.level])
+            return fail(HF_ERR_ARG, "leaf %lld: index (%d, %d) outside level %d", (long long)k, l.ix, l.iy, l.level);
+        if (!std::isfinite(l.value)) return fail(HF_ERR_ARG, "leaf %lld: value not finite", (long long)k);
+        if (lf.test(l.level, l.ix, l.iy)) return fail(HF_ERR_ARG, "leaf %lld: duplicate cell", (long long)k);
+        lf.set(l.level, l.ix, l.iy);
+        lmin = std::min(lmin, l.level);
+        lmax = std::max(lmax, l.level);
+        vmin = std::min(vmin, l.value);
+        vmax = std::max(vmax, l.value);
+        area += int64_t(1) << (2 * (M - l.level));
+    }
+    // no leaf may lie inside another; with the area sum this is an exact tiling
+    for (int64_t k = 0; k < n_leaves; ++k) {
+        const hf_leaf& l = leaves[k];
+        for (int A = 0; A < l.level; ++A)
+            if (lf.test(A, l.ix >> (l.level - A), l.iy >> (l.level - A)))
+                return fail(HF_ERR_ARG, "leaf %lld lies inside a coarser leaf", (long long)k);
+    }
+    if (area != fnx * fny) return fail(HF_ERR_ARG, "leaves do not cover the domain (gap)");
+    lf.finalize();
+    ctx->c_min = d.root_cell / double(int64_t(1) << lmax);
+    ctx->c_max = d.root_cell / double(int64_t(1) << lmin);
+    ctx->zmin = vmin;
+    ctx->zmax = vmax;
+
+    // records in (level, iy, ix) order: centre, exponent scale, value
+    const double log2e = 1.4426950408889634;
+    ctx->perm.resize(size_t(n_leaves));
+    ctx->recs.resize(size_t(n_leaves));
+    for (int64_t k = 0; k < n_leaves; ++k) {
+        const hf_leaf& l = leaves[k];
+        const int64_t s = lf.rank(l.level, l.ix, l.iy);
+        const double c = d.root_cell / double(int64_t(1) << l.level);
+        ctx->perm[size_t(k)] = s;
+        ctx->recs[size_t(s)] = make_float4(float((l.ix + 0.5) * c), float((l.iy + 0.5) * c),
+                                           float(-log2e / (2.0 * rbf->sigma * rbf->sigma * c * c)),
+                                           l.value);
+    }
+
+    // buckets: leaves at or below level B, coarser leaves split down to B
+    HostBitmaps& bk = ctx->buckets;
+    bk.init(d.root_nx, d.root_ny, M);
+    const int B = ctx->B;
+    for (int64_t k = 0; k < n_leaves; ++k) {
+        const hf_leaf& l = leaves[k];
+        if (l.level >= B) {
+            bk.set(l.level, l.ix, l.iy);
+        } else {
+            const int sh = B - l.level;
+            for (int64_t y = int64_t(l.iy) << sh; y < (int64_t(l.iy) + 1) << sh; ++y)
+                for (int64_t x = int64_t(l.ix) << sh; x < (int64_t(l.ix) + 1) << sh; ++x) bk.set(B, x, y);
+        }
+    }
+    bk.finalize();
+    ctx->n_buckets = bk.base[M + 1];
+
+    // reach of a level-L centre, R c_L plus a margin covering FP32 rounding of
+    // texel positions, in units of half a finest cell
+    const double ext = std::max(ctx->width, ctx->height);
+    const double ulp = std::ldexp(1.0, std::ilogb(ext) - 23);
+    const double margin = std::max(1e-3 * ctx->c_fin, 8.0 * ulp);
+    const double q = 0.5 * ctx->c_fin;
+    for (int L = 0; L <= M; ++L)
+        ctx->reach_q[L] = (rbf->radius * (d.root_cell / double(int64_t(1) << L)) + margin) / q;
+
+    std::vector<int64_t> counts(size_t(ctx->n_buckets), 0);
+    const int nt = std::max(1, std::min(64, int(std::thread::hardware_concurrency())));
+    count_lists_host(ctx->enum_tables(false), ctx->lookup_tables(false), counts.data(), nt);
+    ctx->offsets.resize(size_t(ctx->n_buckets) + 1);
+    int64_t run = 0;
+    for (int64_t b = 0; b < ctx->n_buckets; ++b) {
+        ctx->offsets[size_t(b)] = run;
+        run += counts[size_t(b)];
+    }
+    ctx->offsets[size_t(ctx->n_buckets)] = run;
+    ctx->n_cand = run;
+    ctx->lay = ctx->layout();
+    *out = ctx.release();
+    g_err.clear();
+    return HF_OK;
+}
+
+int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
+                   size_t* persistent_bytes, size_t* view_bytes) {
+    if (!ctx) return fail(HF_ERR_ARG, "null context");
+    if (persistent_bytes) *persistent_bytes = ctx->lay.total;
+    if (view_bytes) {
+        if (n_cascades < 1 || n_cascades > HF_MAX_CASCADES || cascade_size < 2 || cascade_size > kMaxCascadeSize)
+            return fail(HF_ERR_ARG, "cascades must be 1..%d of side 2..%d", HF_MAX_CASCADES, kMaxCascadeSize);
+        *view_bytes = per_view_bytes(n_cascades, cascade_size);
+    }
+    return HF_OK;
+}
+
+int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* stream) {
+    if (!ctx || !dev_persistent) return fail(HF_ERR_ARG, "null argument");
+    if (reinterpret_cast<uintptr_t>(dev_persistent) & 255) return fail(HF_ERR_ARG, "buffer must be 256-byte aligned");
+    if (bytes < ctx->lay.total)
+        return fail(HF_ERR_NOMEM, "persistent buffer has %zu bytes, %zu needed", bytes, ctx->lay.total);
+    cudaStream_t s = cudaStream_t(stream);
+    char* dev = static_cast<char*>(dev_persistent);
+    const PersistentLayout& l = ctx->lay;
+    int e = cudaMemsetAsync(dev + l.status, 0, sizeof(DevStatus), s);
+    if (!e) e = cudaMemcpyAsync(dev + l.lbits, ctx->leaves.bits.data(), ctx->leaves.bits.size() * 8, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(dev + l.lprefix, ctx->leaves.prefix.data(), ctx->leaves.prefix.size() * 4, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(dev + l.bbits, ctx->buckets.bits.data(), ctx->buckets.bits.size() * 8, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(dev + l.bprefix, ctx->buckets.prefix.data(), ctx->buckets.prefix.size() * 4, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(dev + l.recs, ctx->recs.data(), ctx->recs.size() * 16, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(dev + l.offsets, ctx->offsets.data(), ctx->offsets.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e) return cuda_fail(e, "upload of the quadtree");
+    ctx->dev = dev;
+    ctx->dev_bytes = bytes;
+    e = launch_fill_lists(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
+    if (e) return cuda_fail(e, "influence-list kernel launch");
+    e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "influence-list build");
+    DevStatus st;
+    e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "status read-back");
+    if (st.flags) {
+        ctx->dev = nullptr;
+        return fail(HF_ERR_DATA, "influence-list build disagreed with the host count at bucket %u", st.detail);
+    }
+    return HF_OK;
+}
+
+int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* stream) {
+    if (!ctx || !values) return fail(HF_ERR_ARG, "null argument");
+    if (n_values != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld values", (long long)ctx->n_leaves);
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    ctx->staged.resize(size_t(n_values));
+    float vmin = INFINITY, vmax = -INFINITY;
+    for (int64_t k = 0; k < n_values; ++k) {
+        if (!std::isfinite(values[k])) return fail(HF_ERR_ARG, "value %lld not finite", (long long)k);
+        const int64_t s = ctx->perm[size_t(k)];
+        ctx->staged[size_t(s)] = values[k];
+        ctx->recs[size_t(s)].w = values[k];
+        vmin = std::min(vmin, values[k]);
+        vmax = std::max(vmax, values[k]);
+    }
+    ctx->zmin = vmin;
+    ctx->zmax = vmax;
+    cudaStream_t s = cudaStream_t(stream);
+    int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
+                              cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "value upload");
+    return HF_OK;
+}
+
+int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes) {
+    if (!ctx || !cam || !dev_view) return fail(HF_ERR_ARG, "null argument");
+    if (slot < 0 || slot >= HF_MAX_VIEWS) return fail(HF_ERR_ARG, "view slot %d out of range", slot);
+    const hf_camera& c = *cam;
+    if (!finite3(c.eye) || !finite3(c.forward) || !finite3(c.up))
+        return fail(HF_ERR_ARG, "camera vectors must be finite");
+    if (c.forward[0] == 0.0 && c.forward[1] == 0.0 && c.forward[2] == 0.0) return fail(HF_ERR_ARG, "zero forward vector");
+    if (!(c.vfov > 0.0 && c.vfov < 3.1)) return fail(HF_ERR_ARG, "vfov must be in (0, 3.1) radians");
+    if (!(c.znear > 0.0 && c.zfar > c.znear && std::isfinite(c.zfar))) return fail(HF_ERR_ARG, "need 0 < znear < zfar");
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return fail(HF_ERR_ARG, "image size out of range");
+    if (c.n_cascades < 1 || c.n_cascades > HF_MAX_CASCADES) return fail(HF_ERR_ARG, "n_cascades must be 1..%d", HF_MAX_CASCADES);
+    if (c.cascade_size < 2 || c.cascade_size > kMaxCascadeSize) return fail(HF_ERR_ARG, "cascade_size must be 2..%d", kMaxCascadeSize);
+    if (!(c.split_lambda >= 0.0 && c.split_lambda <= 1.0)) return fail(HF_ERR_ARG, "split_lambda must be in [0, 1]");
+    if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
+    if (reinterpret_cast<uintptr_t>(dev_view) & 255) return fail(HF_ERR_ARG, "view buffer must be 256-byte aligned");
+    const size_t need = per_view_bytes(c.n_cascades, c.cascade_size);
+    if (bytes < need) return fail(HF_ERR_NOMEM, "view buffer has %zu bytes, %zu needed", bytes, need);
+    if (!ctx->views[slot]) ctx->views[slot].reset(new ViewSlot);
+    ViewSlot& v = *ctx->views[slot];
+    v.stage = 0;
+    v.cam = c;
+    v.eye_local[0] = c.eye[0] - ctx->desc.origin_x;
+    v.eye_local[1] = c.eye[1] - ctx->desc.origin_y;
+    v.eye_local[2] = c.eye[2];
+    FitDomain dom{ctx->width, ctx->height, ctx->zmin, ctx->zmax, ctx->c_min};
+    int rc = fit_cascades(c, v.eye_local, dom, &v.fit);
+    if (rc) return fail(rc, "cascade fit produced an oversized polygon");
+    v.dev = static_cast<char*>(dev_view);
+    v.bytes = bytes;
+    const int N = c.cascade_size;
+    size_t o = 0;
+    for (int k = 0; k < c.n_cascades; ++k) {
+        v.tex[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * N * 4);
+        v.mip[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(mip_floats(N)) * 4);
+        v.spans[k] = reinterpret_cast<int2*>(v.dev + o); o = align256(o + size_t(N) * 8);
+        v.xs[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * 4);
+        v.ys[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * 4);
+        hf_cascade_info& ci = v.fit.cas[k];
+        ci.tex = v.tex[k];
+        ci.mip = v.mip[k];
+        ci.spans = reinterpret_cast<int32_t*>(v.spans[k]);
+        ci.mip_floats = mip_floats(N);
+    }
+    v.stage = 1;
+    return HF_OK;
+}
+
+namespace {
+
+DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
+    const int C = v->cam.n_cascades, N = v->cam.cascade_size;
+    DiscParams dp;
+    std::memset(&dp, 0, sizeof(dp));
+    dp.C = C;
+    dp.max_N = N;
+    dp.precision = ctx->rbf.precision;
+    dp.K = float(std::exp(-ctx->rbf.radius * ctx->rbf.radius / (2.0 * ctx->rbf.sigma * ctx->rbf.sigma)));
+    for (int k = 0; k < C; ++k) {
+        DiscCascade& dc = dp.cas[k];
+        dc.N = N;
+        dc.spans = v->spans[k];
+        dc.xs = v->xs[k];
+        dc.ys = v->ys[k];
+        dc.tex = v->tex[k];
+    }
+    return dp;
+}
+
+}  // namespace
+
+int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    const int C = v->cam.n_cascades, N = v->cam.cascade_size;
+    PrepParams pp;
+    std::memset(&pp, 0, sizeof(pp));
+    pp.C = C;
+    pp.max_N = N;
+    pp.dom_w = ctx->width;
+    pp.dom_h = ctx->height;
+    pp.eps_frac = 1e-6;
+    for (int k = 0; k < C; ++k) {
+        const hf_cascade_info& ci = v->fit.cas[k];
+        PrepCascade& q = pp.cas[k];
+        q.ox = ci.ox;
+        q.oy = ci.oy;
+        q.h = ci.texel;
+        q.inv_h = 1.0 / ci.texel;
+        q.N = N;
+        q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
+        // polygon grown by one texel diagonal: n.p <= n.a + sqrt(2) h per edge
+        const double delta = std::sqrt(2.0) * ci.texel;
+        for (int e = 0; e < q.n_edges; ++e) {
+            const double ax = ci.poly[e][0], ay = ci.poly[e][1];
+            const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
+            const double len = std::hypot(bx - ax, by - ay);
+            const double nx = (by - ay) / len, ny = -(bx - ax) / len;
+            q.ny[e] = ny;
+            q.c[e] = nx * ax + ny * ay + delta;
+            q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
+            q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
+        }
+        q.spans = v->spans[k];
+        q.xs = v->xs[k];
+        q.ys = v->ys[k];
+    }
+    int e = launch_prep(pp, stream);
+    if (e) return cuda_fail(e, "visible-row kernel launch");
+    e = launch_discretize(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
+    if (e) return cuda_fail(e, "discretization kernel launch");
+    v->stage = 2;
+    return HF_OK;
+}
+
+int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
+    const int C = v->cam.n_cascades, N = v->cam.cascade_size;
+    MipParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.C = C;
+    mp.max_P = mip_pow2(N);
+    mp.max_K = mip_levels(mp.max_P);
+    for (int k = 0; k < C; ++k) {
+        mp.cas[k].tex = v->tex[k];
+        mp.cas[k].mip = v->mip[k];
+        mp.cas[k].N = N;
+        mp.cas[k].P = mp.max_P;
+        mp.cas[k].K = mp.max_K;
+    }
+    int e = launch_maxmip(mp, stream);
+    if (e) return cuda_fail(e, "max-mip kernel launch");
+    v->stage = 3;
+    return HF_OK;
+}
+
+int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
+    if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
+    const hf_camera& c = v->cam;
+    const FitResult& f = v->fit;
+    RayParams rp;
+    std::memset(&rp, 0, sizeof(rp));
+    rp.C = c.n_cascades;
+    rp.W = c.width;
+    rp.H = c.height;
+    rp.ez = float(v->eye_local[2]);
+    for (int a = 0; a < 3; ++a) {
+        rp.F[a] = float(f.F[a]);
+        rp.R[a] = float(f.R[a]);
+        rp.U[a] = float(f.U[a]);
+    }
+    rp.tan_v = float(std::tan(0.5 * c.vfov));
+    rp.tan_h = float(std::tan(0.5 * c.vfov) * double(c.width) / double(c.height));
+    rp.dir2x = float(f.dir2[0]);
+    rp.dir2y = float(f.dir2[1]);
+    rp.znear = float(c.znear);
+    rp.zfar = float(c.zfar);
+    const int N = c.cascade_size, P = mip_pow2(N);
+    for (int k = 0; k < rp.C; ++k) {
+        const hf_cascade_info& ci = f.cas[k];
+        RayCascade& rc = rp.cas[k];
+        rc.tex = v->tex[k];
+        rc.mip = v->mip[k];
+        rc.N = N;
+        rc.P = P;
+        rc.K = mip_levels(P);
+        rc.eu = float((v->eye_local[0] - ci.ox) / ci.texel);
+        rc.ev = float((v->eye_local[1] - ci.oy) / ci.texel);
+        rc.inv_h = float(1.0 / ci.texel);
+        rc.near_d = float(ci.near_depth);
+        rc.far_ext = float(ci.far_ext_depth);
+    }
+    rp.t_out = t_dev;
+    rp.hit_out = hit_dev;
+    int e = launch_raycast(rp, ctx->d_status(), stream);
+    if (e) return cuda_fail(e, "ray-cast kernel launch");
+    return HF_OK;
+}
+
+int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!out) return fail(HF_ERR_ARG, "null argument");
+    if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
+    cudaStream_t s = cudaStream_t(stream);
+    DevStatus* st = ctx->d_status();
+    int e = cudaMemsetAsync(st->counters, 0, sizeof(st->counters), s);
+    if (!e) e = launch_stats(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), st, stream);
+    if (e) return cuda_fail(e, "counting pass launch");
+    unsigned long long c[3 * HF_MAX_CASCADES];
+    e = cudaMemcpyAsync(c, st->counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "counting pass");
+    std::memset(out, 0, sizeof(*out));
+    for (int k = 0; k < v->cam.n_cascades; ++k) {
+        out->visible_texels[k] = int64_t(c[k]);
+        out->candidates[k] = int64_t(c[HF_MAX_CASCADES + k]);
+        out->influencers[k] = int64_t(c[2 * HF_MAX_CASCADES + k]);
+    }
+    return HF_OK;
+}
+
+int hf_get_cascade(const hf_ctx* ctx, int32_t slot, int32_t c, hf_cascade_info* out) {
+    if (!ctx || !out) return fail(HF_ERR_ARG, "null argument");
+    if (slot < 0 || slot >= HF_MAX_VIEWS || !ctx->views[slot] || ctx->views[slot]->stage < 1)
+        return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+    const ViewSlot& v = *ctx->views[slot];
+    if (c < 0 || c >= v.cam.n_cascades) return fail(HF_ERR_ARG, "cascade %d out of range", c);
+    *out = v.fit.cas[c];
+    return HF_OK;
+}
+
+int hf_sync(hf_ctx* ctx, void* stream) {
+    if (!ctx) return fail(HF_ERR_ARG, "null context");
+    int e = cudaStreamSynchronize(cudaStream_t(stream));
+    if (e) return cuda_fail(e, "stream synchronize");
+    e = cudaGetLastError();
+    if (e) return cuda_fail(e, "pending CUDA error");
+    if (!ctx->dev) return HF_OK;
+    DevStatus st;
+    e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "status read-back");
+    if (st.flags) {
+        e = cudaMemset(ctx->d_status(), 0, 8);
+        if (e) return cuda_fail(e, "status reset");
+        if (st.flags & kStatusTimeout)
+            return fail(HF_ERR_TIMEOUT, "a ray traversal exceeded its step budget (pixel %u)", st.detail);
+        return fail(HF_ERR_DATA, "device consistency check failed (item %u)", st.detail);
+    }
+    return HF_OK;
+}
+
+void hf_destroy(hf_ctx* ctx) { delete ctx; }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations shared by the host code (hf_host.cpp, hf_fit.cpp)
+// and the CUDA kernels (hf_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hf.h"
+
+namespace hfi {
+
+constexpr int kMaxLevels = HF_MAX_LEVEL + 1;
+constexpr int kMaxCascadeSize = 8192;
+
+// Device status block at the start of the persistent buffer.  Kernels OR
+// error bits into `flags` and record the first failing item in `detail`.
+enum : uint32_t { kStatusTimeout = 1u, kStatusData = 2u };
+struct DevStatus {
+    uint32_t flags;
+    uint32_t detail;
+    unsigned long long counters[3 * HF_MAX_CASCADES];  // measurement pass (hf_view_stats)
+    uint32_t pad[14];
+};
+static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
+
+// Per-level occupancy bitmaps of a set of quadtree cells: bit (iy*nx[L]+ix)
+// of level L is set when cell (L, ix, iy) is in the set.  prefix[w] counts
+// the set bits of level L before word w, so the index of a cell is
+// base[L] + prefix[w] + popcount(lower bits of word w).  Cells are thereby
+// numbered by (level, iy, ix).  Levels without cells have no words.
+struct Bitmaps {
+    const uint64_t* bits;
+    const uint32_t* prefix;
+    int64_t word_off[kMaxLevels + 1];  // word_off[max_level + 1] = total words
+    int64_t base[kMaxLevels + 1];      // base[max_level + 1] = total cells
+    int32_t nx[kMaxLevels];
+    int32_t ny[kMaxLevels];
+    int32_t max_level;
+};
+
+// Candidate enumeration: the real leaves (the RBF centres) and the reach of
+// a level-L centre, R * c_L + margin, in units of half a finest cell.
+struct EnumTables {
+    Bitmaps leaves;
+    double reach_q[kMaxLevels];
+};
+
+// Texel -> bucket lookup.  Buckets are the leaves at or below level
+// `bucket_level`; coarser leaves are split into their level-bucket_level
+// descendants, so that each list covers a small square.
+struct LookupTables {
+    Bitmaps buckets;
+    int32_t bucket_level;
+    float inv_c_fin;  // 1 / finest cell edge
+    int32_t nx_fin, ny_fin;
+};
+
+struct ListsView {
+    const int64_t* offsets;  // n_buckets + 1
+    int32_t* idx;            // candidate leaf indices, ascending within a bucket
+    float4* recs;            // per leaf: centre x, y (domain-local), -log2(e)/(2 sigma^2 c^2), value
+};
+
+// Per-frame cascade data for the prep kernel (visible rows, texel coordinates).
+struct PrepCascade {
+    double ox, oy, h, inv_h;
+    int32_t N;
+    int32_t n_edges;  // 0 = empty cascade
+    // grown polygon edge e: nx x + ny y <= c, i.e. x <= or >= (c - ny y) / nx
+    double ny[HF_MAX_POLY];
+    double c[HF_MAX_POLY];
+    double inv_nx[HF_MAX_POLY];
+    int32_t sgn[HF_MAX_POLY];
+    int2* spans;
+    float* xs;
+    float* ys;
+};
+
+struct PrepParams {
+    int32_t C;
+    int32_t max_N;
+    double dom_w, dom_h, eps_frac;  // domain extents and the boundary slack (fraction of h)
+    PrepCascade cas[HF_MAX_CASCADES];
+};
+
+struct DiscCascade {
+    int32_t N;
+    const int2* spans;
+    const float* xs;
+    const float* ys;
+    float* tex;
+};
+
+struct DiscParams {
+    int32_t C;
+    int32_t max_N;
+    int32_t precision;
+    float K;  // exp(-R^2 / (2 sigma^2))
+    DiscCascade cas[HF_MAX_CASCADES];
+};
+
+struct MipCascade {
+    const float* tex;
+    float* mip;
+    int32_t N, P, K;
+};
+
+struct MipParams {
+    int32_t C;
+    int32_t max_P;
+    int32_t max_K;
+    MipCascade cas[HF_MAX_CASCADES];
+};
+
+struct RayCascade {
+    const float* tex;
+    const float* mip;
+    int32_t N, P, K;
+    float eu, ev;  // eye in this cascade's patch units
+    float inv_h;
+    float near_d, far_ext;  // projected-depth band
+};
+
+struct RayParams {
+    int32_t C, W, H;
+    float ez;                // eye height (m)
+    float F[3], R[3], U[3];  // camera basis
+    float tan_h, tan_v;
+    float dir2x, dir2y;      // normalised ground projection of the view
+    float znear, zfar;
+    RayCascade cas[HF_MAX_CASCADES];
+    float* t_out;
+    uint8_t* hit_out;
+};
+
+// Kernel launchers (hf_kernels.cu); they return a cudaError_t value.
+int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
+                      DevStatus* status, void* stream);
+int launch_prep(const PrepParams& p, void* stream);
+int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
+                      DevStatus* status, void* stream);
+int launch_maxmip(const MipParams& p, void* stream);
+int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
+                 DevStatus* status, void* stream);
+int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
+
+// Host-side count of each bucket's candidates (same enumeration as the fill
+// kernel, in exact integer arithmetic).  Bitmaps must hold host pointers.
+void count_lists_host(const EnumTables& et, const LookupTables& lt, int64_t* counts,
+                      int n_threads);
+
+// Mip geometry shared by host and device code.
+inline int mip_pow2(int N) {
+    int P = 1;
+    while (P < N - 1) P <<= 1;
+    return P;
+}
+inline int mip_levels(int P) {
+    int K = 0;
+    while ((1 << K) < P) K++;
+    return K;
+}
+inline int64_t mip_floats(int N) {
+    int64_t P = mip_pow2(N);
+    return (4 * P * P - 1) / 3;
+}
+
+// Cascade fitting (hf_fit.cpp).
+struct FitDomain {
+    double width, height, zmin, zmax, c_min;
+};
+struct FitResult {
+    double F[3], U[3], R[3];
+    double dir2[2];
+    double n, f;
+    int n_hull;
+    double hull[64][2];
+    hf_cascade_info cas[HF_MAX_CASCADES];
+};
+// eye_local: eye relative to the domain origin (FP64).
+int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomain& dom,
+                 FitResult* out);
+
+}  // namespace hfi

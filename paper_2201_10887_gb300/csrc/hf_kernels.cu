@@ -1,0 +1,692 @@
+// CUDA kernels for sm_103a: influence-list build, visible-row prep,
+// RBF discretization (Eq. 1, Eq. 2), max mipmap and ray casting
+// (Cornel et al., 2022, Sections 3-5).
+//
+// None of these steps is a dense contraction, so no tensor-core path is
+// used: the discretization is bound by exp (MUFU) and FP32 issue, the mip
+// build by HBM/L2 bandwidth, the ray caster by dependent loads.
+#include <cmath>
+#include <cstdint>
+#include <thread>
+#include <vector>
+
+#include "hf_internal.h"
+
+namespace hfi {
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+__host__ __device__ inline int popc64(uint64_t w) {
+#ifdef __CUDA_ARCH__
+    return __popcll(w);
+#else
+    return __builtin_popcountll(w);
+#endif
+}
+
+__device__ __forceinline__ void report(DevStatus* st, uint32_t flag, uint32_t detail) {
+    if (atomicOr(&st->flags, flag) == 0) st->detail = detail;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------
+// Candidate enumeration for one bucket square (Section 4: the cells that can
+// influence any point of the square).  Exact integer geometry in units of
+// half a finest cell: a level-L centre sits at (2 ix + 1) 2^(M-L) and
+// influences the square when its distance to the square is below
+// reach_q[L].  The same code counts on the host and fills on the device.
+
+template <class Visit>
+__host__ __device__ inline int64_t for_each_candidate(const EnumTables& t, int Lb, int64_t bx,
+                                                      int64_t by, Visit&& visit) {
+    const Bitmaps& lf = t.leaves;
+    const int M = lf.max_level;
+    const int64_t s = int64_t(1) << (M - Lb + 1);
+    const int64_t x0 = bx * s, x1 = x0 + s, y0 = by * s, y1 = y0 + s;
+    int64_t n = 0;
+    for (int L = 0; L <= M; ++L) {
+        if (lf.base[L + 1] == lf.base[L]) continue;  // no leaves on this level
+        const double r = t.reach_q[L], r2 = r * r;
+        const int64_t g = int64_t(1) << (M - L);
+        const double inv2g = 0.5 / double(g);
+        int64_t lx = int64_t(floor((double(x0) - r) * inv2g - 0.5)) - 1;
+        int64_t hx = int64_t(ceil((double(x1) + r) * inv2g - 0.5)) + 1;
+        int64_t ly = int64_t(floor((double(y0) - r) * inv2g - 0.5)) - 1;
+        int64_t hy = int64_t(ceil((double(y1) + r) * inv2g - 0.5)) + 1;
+        lx = lx < 0 ? 0 : lx;
+        ly = ly < 0 ? 0 : ly;
+        hx = hx > lf.nx[L] - 1 ? lf.nx[L] - 1 : hx;
+        hy = hy > lf.ny[L] - 1 ? lf.ny[L] - 1 : hy;
+        for (int64_t iy = ly; iy <= hy; ++iy) {
+            const int64_t Y = (2 * iy + 1) * g;
+            const int64_t dy = Y < y0 ? y0 - Y : (Y > y1 ? Y - y1 : 0);
+            if (double(dy * dy) >= r2) continue;
+            for (int64_t ix = lx; ix <= hx; ++ix) {
+                const int64_t X = (2 * ix + 1) * g;
+                const int64_t dx = X < x0 ? x0 - X : (X > x1 ? X - x1 : 0);
+                if (double(dx * dx + dy * dy) >= r2) continue;
+                const int64_t b = iy * lf.nx[L] + ix;
+                const int64_t w = lf.word_off[L] + (b >> 6);
+                const uint64_t word = lf.bits[w];
+                if ((word >> (b & 63)) & 1ull) {
+                    const int64_t id =
+                        lf.base[L] + lf.prefix[w] + popc64(word & ((1ull << (b & 63)) - 1ull));
+                    visit(n, id);
+                    ++n;
+                }
+            }
+        }
+    }
+    return n;
+}
+
+// Locate the bucket word/bit of a linear bit position over all levels.
+__host__ __device__ inline bool bucket_of_bit(const Bitmaps& bk, int64_t w, int bit, int& Lb,
+                                              int64_t& bx, int64_t& by, int64_t& id) {
+    int L = 0;
+    while (L < bk.max_level && w >= bk.word_off[L + 1]) ++L;
+    if (w < bk.word_off[L] || w >= bk.word_off[L + 1]) return false;
+    const uint64_t word = bk.bits[w];
+    if (!((word >> bit) & 1ull)) return false;
+    const int64_t b = (w - bk.word_off[L]) * 64 + bit;
+    Lb = L;
+    bx = b % bk.nx[L];
+    by = b / bk.nx[L];
+    id = bk.base[L] + bk.prefix[w] + popc64(word & ((1ull << bit) - 1ull));
+    return true;
+}
+
+struct CountOnly {
+    __host__ __device__ void operator()(int64_t, int64_t) const {}
+};
+
+void count_lists_host(const EnumTables& et, const LookupTables& lt, int64_t* counts,
+                      int n_threads) {
+    const Bitmaps& bk = lt.buckets;
+    const int64_t words = bk.word_off[bk.max_level + 1];
+    if (n_threads < 1) n_threads = 1;
+    auto work = [&](int64_t w0, int64_t w1) {
+        for (int64_t w = w0; w < w1; ++w) {
+            uint64_t word = bk.bits[w];
+            while (word) {
+                const int bit = __builtin_ctzll(word);
+                word &= word - 1;
+                int Lb;
+                int64_t bx, by, id;
+                if (bucket_of_bit(bk, w, bit, Lb, bx, by, id))
+                    counts[id] = for_each_candidate(et, Lb, bx, by, CountOnly{});
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    const int64_t chunk = (words + n_threads - 1) / n_threads;
+    for (int t = 0; t < n_threads; ++t) {
+        int64_t a = t * chunk, b = a + chunk < words ? a + chunk : words;
+        if (a >= b) break;
+        pool.emplace_back(work, a, b);
+    }
+    for (auto& th : pool) th.join();
+}
+
+// One thread per (bucket word, bit): fill that bucket's candidate list.
+struct FillArgs {
+    EnumTables et;
+    Bitmaps buckets;
+    ListsView lv;
+    DevStatus* status;
+};
+
+__global__ void __launch_bounds__(256) k_fill_lists(const __grid_constant__ FillArgs a) {
+    __shared__ EnumTables et;
+    __shared__ Bitmaps bk;
+    if (threadIdx.x == 0) {
+        et = a.et;
+        bk = a.buckets;
+    }
+    __syncthreads();
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t w = g >> 6;
+    if (w >= bk.word_off[bk.max_level + 1]) return;
+    int Lb;
+    int64_t bx, by, id;
+    if (!bucket_of_bit(bk, w, int(g & 63), Lb, bx, by, id)) return;
+    const int64_t beg = a.lv.offsets[id], cap = a.lv.offsets[id + 1] - beg;
+    int32_t* out = a.lv.idx + beg;
+    const int64_t n = for_each_candidate(et, Lb, bx, by, [&](int64_t k, int64_t leaf) {
+        if (k < cap) out[k] = int32_t(leaf);
+    });
+    if (n != cap) report(a.status, kStatusData, uint32_t(id));
+}
+
+int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
+                      DevStatus* status, void* stream) {
+    FillArgs a{et, lt.buckets, lv, status};
+    const int64_t words = lt.buckets.word_off[lt.buckets.max_level + 1];
+    const int64_t threads = words * 64;
+    if (threads == 0) return cudaSuccess;
+    const int64_t blocks = (threads + 255) / 256;
+    k_fill_lists<<<dim3(unsigned(blocks)), 256, 0, cudaStream_t(stream)>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Visible rows (Section 3 mask) and texel coordinates of every cascade, FP64.
+// Row j of cascade c sees columns [spans.x, spans.y]: the texel centres inside
+// the cascade polygon grown by one texel diagonal and inside the domain.
+
+__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams p) {
+    const int c = blockIdx.y;
+    const PrepCascade& q = p.cas[c];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= q.N) return;
+    const double h = q.h;
+    q.xs[t] = float(q.ox + double(t) * h);
+    const double y = q.oy + double(t) * h;
+    q.ys[t] = float(y);
+    const double eps = p.eps_frac * h;
+    int lo = 0, hi = -1;
+    if (q.n_edges >= 3 && y >= -eps && y <= p.dom_h + eps) {
+        double xlo = -eps, xhi = p.dom_w + eps;
+        bool empty = false;
+        for (int e = 0; e < q.n_edges; ++e) {
+            const double rhs = q.c[e] - q.ny[e] * y;
+            if (q.sgn[e] > 0) xhi = fmin(xhi, rhs * q.inv_nx[e]);
+            else if (q.sgn[e] < 0) xlo = fmax(xlo, rhs * q.inv_nx[e]);
+            else if (rhs < 0.0) empty = true;
+        }
+        if (!empty && xlo <= xhi) {
+            double flo = ceil((xlo - q.ox) * q.inv_h), fhi = floor((xhi - q.ox) * q.inv_h);
+            flo = fmax(flo, 0.0);
+            fhi = fmin(fhi, double(q.N - 1));
+            if (flo <= fhi) {
+                lo = int(flo);
+                hi = int(fhi);
+            }
+        }
+    }
+    q.spans[t] = make_int2(lo, hi);
+}
+
+int launch_prep(const PrepParams& p, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_N + 127) / 128, p.C);
+    k_prep<<<grid, 128, 0, cudaStream_t(stream)>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Texel -> bucket.  The finest-cell coordinates of the texel are computed once;
+// the cell containing it on level L is their shift by max_level - L, so the
+// levels are consistent by construction.  Exactly one level holds a bucket.
+
+__device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float px, float py) {
+    const Bitmaps& bk = lt.buckets;
+    int fx = int(floorf(px * lt.inv_c_fin));
+    int fy = int(floorf(py * lt.inv_c_fin));
+    fx = min(max(fx, 0), lt.nx_fin - 1);
+    fy = min(max(fy, 0), lt.ny_fin - 1);
+    const int M = bk.max_level;
+    int64_t found = -1;
+#pragma unroll
+    for (int L = 0; L < kMaxLevels; ++L) {
+        if (L >= lt.bucket_level && L <= M) {
+            const int sh = M - L;
+            const int64_t b = int64_t(fy >> sh) * bk.nx[L] + (fx >> sh);
+            const int64_t w = bk.word_off[L] + (b >> 6);
+            const uint64_t word = __ldg(reinterpret_cast<const unsigned long long*>(bk.bits) + w);
+            if ((word >> (b & 63)) & 1ull)
+                found = bk.base[L] + __ldg(bk.prefix + w) + __popcll(word & ((1ull << (b & 63)) - 1ull));
+        }
+    }
+    return found;
+}
+
+// ---------------------------------------------------------------------------
+// RBF discretization (Eq. 1, Eq. 2): one thread per texel, a warp per 32
+// consecutive texels of a row.  Each visible texel walks its bucket's list:
+//   w_i = max(2^(k_i d_i^2) - K, 0),  k_i = -log2(e) / (2 sigma^2 c_i^2)
+//   v   = sum w_i v_i / sum w_i.
+// Invisible texels are written as -inf so the texture is fully defined.
+
+__global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
+                                                        const __grid_constant__ LookupTables lt,
+                                                        const ListsView lv, DevStatus* status) {
+    const DiscCascade& q = p.cas[blockIdx.z];
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= q.N || j >= q.N) return;
+    const int2 sp = __ldg(q.spans + j);
+    float* out = q.tex + size_t(j) * q.N + i;
+    if (i < sp.x || i > sp.y) {
+        *out = -INFINITY;
+        return;
+    }
+    const float px = __ldg(q.xs + i), py = __ldg(q.ys + j);
+    const int64_t bucket = lookup_bucket(lt, px, py);
+    if (bucket < 0) {
+        report(status, kStatusData, 0xFFFFFFFFu);
+        *out = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int64_t beg = __ldg(lv.offsets + bucket);
+    const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
+    const int32_t* ids = lv.idx + beg;
+    const float K = p.K;
+    float sw = 0.f, swv = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < n; ++k) {
+        const float4 r = __ldg(lv.recs + __ldg(ids + k));
+        const float dx = r.x - px, dy = r.y - py;
+        const float w = fmaxf(ex2_approx(r.z * fmaf(dx, dx, dy * dy)) - K, 0.f);
+        sw += w;
+        swv = fmaf(w, r.w, swv);
+    }
+    *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
+                      DevStatus* status, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
+    k_discretize_f32<<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    return cudaGetLastError();
+}
+
+// Measurement pass: the discretization's texel mapping and inner loop, but
+// counting visible texels, list entries walked and terms with w > 0 instead
+// of writing heights.  Warp sums, one 64-bit atomic per warp and counter.
+__global__ void __launch_bounds__(256) k_stats_f32(const __grid_constant__ DiscParams p,
+                                                   const __grid_constant__ LookupTables lt,
+                                                   const ListsView lv, DevStatus* status) {
+    const int c = blockIdx.z;
+    const DiscCascade& q = p.cas[c];
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    unsigned vis = 0, cand = 0, infl = 0;
+    if (i < q.N && j < q.N) {
+        const int2 sp = __ldg(q.spans + j);
+        if (i >= sp.x && i <= sp.y) {
+            const float px = __ldg(q.xs + i), py = __ldg(q.ys + j);
+            const int64_t bucket = lookup_bucket(lt, px, py);
+            if (bucket >= 0) {
+                const int64_t beg = __ldg(lv.offsets + bucket);
+                const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
+                const int32_t* ids = lv.idx + beg;
+                vis = 1;
+                cand = unsigned(n);
+                for (int k = 0; k < n; ++k) {
+                    const float4 r = __ldg(lv.recs + __ldg(ids + k));
+                    const float dx = r.x - px, dy = r.y - py;
+                    infl += (ex2_approx(r.z * fmaf(dx, dx, dy * dy)) - p.K) > 0.f ? 1u : 0u;
+                }
+            }
+        }
+    }
+    vis = __reduce_add_sync(0xffffffffu, vis);
+    cand = __reduce_add_sync(0xffffffffu, cand);
+    infl = __reduce_add_sync(0xffffffffu, infl);
+    if ((threadIdx.x & 31) == 0 && vis) {
+        atomicAdd(&status->counters[c], (unsigned long long)vis);
+        atomicAdd(&status->counters[HF_MAX_CASCADES + c], (unsigned long long)cand);
+        atomicAdd(&status->counters[2 * HF_MAX_CASCADES + c], (unsigned long long)infl);
+    }
+}
+
+int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
+                 DevStatus* status, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
+    k_stats_f32<<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Maximum mipmap (Section 5, Tevs et al.).  Level 0 entry (pi, pj) is the max
+// of the patch's four corner texels, -inf if one is invisible or the patch
+// lies in the padding; level k is the max of 2x2 entries of level k-1.
+// k_mip_lo: one CTA per 64x64 block of level 0 builds levels 0..6 of it
+// (each thread 4x4 level-0 entries from a 5x5 texel window, then 2x2, 1,
+// then shared memory).  k_mip_hi: one CTA per cascade builds levels 7..K.
+
+__device__ __forceinline__ int64_t mip_off(int P, int k) {
+    const int64_t a = int64_t(P) * P, b = int64_t(P >> k) * (P >> k);
+    return (a - b) * 4 / 3;
+}
+
+__global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParams p) {
+    const MipCascade& c = p.cas[blockIdx.z];
+    const int P = c.P, N = c.N, K = c.K;
+    if (int(blockIdx.x) * 64 >= P || int(blockIdx.y) * 64 >= P) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int pi0 = blockIdx.x * 64 + tx * 4, pj0 = blockIdx.y * 64 + ty * 4;
+    float t[5][5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int ii = pi0 + s, jj = pj0 + r;
+            t[r][s] = (ii < N && jj < N) ? __ldg(c.tex + size_t(jj) * N + ii) : -INFINITY;
+        }
+    float m0[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float a = t[r][s], b = t[r][s + 1], d = t[r + 1][s], e = t[r + 1][s + 1];
+            const bool ok = (pi0 + s < N - 1) && (pj0 + r < N - 1) && isfinite(a) && isfinite(b) &&
+                            isfinite(d) && isfinite(e);
+            m0[r][s] = ok ? fmaxf(fmaxf(a, b), fmaxf(d, e)) : -INFINITY;
+        }
+    if (pi0 < P && pj0 < P) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (pj0 + r >= P) break;
+            float* dst = c.mip + size_t(pj0 + r) * P + pi0;
+            if (P >= 4) {
+                *reinterpret_cast<float4*>(dst) = make_float4(m0[r][0], m0[r][1], m0[r][2], m0[r][3]);
+            } else {
+                for (int s = 0; s < 4 && pi0 + s < P; ++s) dst[s] = m0[r][s];
+            }
+        }
+    }
+    if (K < 1) return;
+    float m1[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            m1[r][s] = fmaxf(fmaxf(m0[2 * r][2 * s], m0[2 * r][2 * s + 1]),
+                             fmaxf(m0[2 * r + 1][2 * s], m0[2 * r + 1][2 * s + 1]));
+    {
+        const int P1 = P >> 1, pi1 = pi0 >> 1, pj1 = pj0 >> 1;
+        float* base = c.mip + mip_off(P, 1);
+        for (int r = 0; r < 2; ++r)
+            for (int s = 0; s < 2; ++s)
+                if (pi1 + s < P1 && pj1 + r < P1) base[size_t(pj1 + r) * P1 + pi1 + s] = m1[r][s];
+    }
+    const float m2 = fmaxf(fmaxf(m1[0][0], m1[0][1]), fmaxf(m1[1][0], m1[1][1]));
+    if (K >= 2) {
+        const int P2 = P >> 2, pi2 = pi0 >> 2, pj2 = pj0 >> 2;
+        if (pi2 < P2 && pj2 < P2) c.mip[mip_off(P, 2) + size_t(pj2) * P2 + pi2] = m2;
+    }
+    __shared__ float sm[16][17];
+    sm[ty][tx] = m2;
+    __syncthreads();
+    int n = 8;
+    for (int k = 3; k <= 6; ++k, n >>= 1) {
+        if (k > K) break;
+        float v = -INFINITY;
+        const int x = threadIdx.x % n, y = threadIdx.x / n;
+        const bool act = threadIdx.x < n * n;
+        if (act) v = fmaxf(fmaxf(sm[2 * y][2 * x], sm[2 * y][2 * x + 1]),
+                           fmaxf(sm[2 * y + 1][2 * x], sm[2 * y + 1][2 * x + 1]));
+        __syncthreads();
+        if (act) {
+            sm[y][x] = v;
+            const int Pk = P >> k, gx = blockIdx.x * n + x, gy = blockIdx.y * n + y;
+            if (gx < Pk && gy < Pk) c.mip[mip_off(P, k) + size_t(gy) * Pk + gx] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipParams p) {
+    const MipCascade& c = p.cas[blockIdx.x];
+    const int P = c.P, K = c.K;
+    if (K < 7) return;
+    __shared__ float sm[2][4096];
+    // level 7 from level 6 in global memory
+    const int n6 = P >> 6, n7 = P >> 7;
+    const float* l6 = c.mip + mip_off(P, 6);
+    for (int e = threadIdx.x; e < n7 * n7; e += blockDim.x) {
+        const int x = e % n7, y = e / n7;
+        const float v = fmaxf(fmaxf(l6[size_t(2 * y) * n6 + 2 * x], l6[size_t(2 * y) * n6 + 2 * x + 1]),
+                              fmaxf(l6[size_t(2 * y + 1) * n6 + 2 * x], l6[size_t(2 * y + 1) * n6 + 2 * x + 1]));
+        sm[0][e] = v;
+        c.mip[mip_off(P, 7) + e] = v;
+    }
+    __syncthreads();
+    int cur = 0, n = n7;
+    for (int k = 8; k <= K; ++k) {
+        const int m = n >> 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int x = e % m, y = e / m;
+            const float v = fmaxf(fmaxf(sm[cur][(2 * y) * n + 2 * x], sm[cur][(2 * y) * n + 2 * x + 1]),
+                                  fmaxf(sm[cur][(2 * y + 1) * n + 2 * x], sm[cur][(2 * y + 1) * n + 2 * x + 1]));
+            sm[cur ^ 1][e] = v;
+            c.mip[mip_off(P, k) + e] = v;
+        }
+        __syncthreads();
+        cur ^= 1;
+        n = m;
+    }
+}
+
+int launch_maxmip(const MipParams& p, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_P + 63) / 64, (p.max_P + 63) / 64, p.C);
+    k_mip_lo<<<grid, 256, 0, cudaStream_t(stream)>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (p.max_K >= 7) {
+        k_mip_hi<<<p.C, 1024, 0, cudaStream_t(stream)>>>(p);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Ray casting (Section 5).  One thread per pixel; rays are traced through the
+// cascades nearest first.  Within a cascade the max mipmap is traversed top
+// down: a node whose maximum lies below the ray over the node's extent is
+// skipped whole, otherwise refined; single patches are intersected exactly
+// (first root of the quadratic bilinear(x(t), y(t)) - z(t)).  The current
+// level-0 patch is tracked in integers so rounding can never move the walk
+// backwards; after leaving a node the walk climbs to the largest node it has
+// newly entered.
+
+struct Ray {
+    float eu, ev, ez;  // origin in patch units (u, v) and metres (z)
+    float du, dv, dz;  // per metre of t
+    float idu, idv;    // 1/du, 1/dv (0 when the component is 0)
+};
+
+__device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, int ci, int cj,
+                                          const Ray& r, float t0, float t1, float& t_hit) {
+    const float* p = tex + size_t(cj) * N + ci;
+    const float h00 = __ldg(p), h10 = __ldg(p + 1), h01 = __ldg(p + N), h11 = __ldg(p + N + 1);
+    const float a0 = fmaf(t0, r.du, r.eu) - float(ci);
+    const float b0 = fmaf(t0, r.dv, r.ev) - float(cj);
+    const float z0 = fmaf(t0, r.dz, r.ez);
+    const float e = h10 - h00, g = h01 - h00, q = (h00 - h10) - (h01 - h11);
+    const float C = fmaf(fmaf(q, a0, g), b0, fmaf(e, a0, h00)) - z0;
+    if (C >= 0.f) {
+        t_hit = t0;
+        return true;
+    }
+    const float B = fmaf(e, r.du, fmaf(g, r.dv, q * fmaf(a0, r.dv, b0 * r.du))) - r.dz;
+    const float A = q * r.du * r.dv;
+    const float dt = t1 - t0;
+    const float slack = 4.f * 1.1920929e-7f * fabsf(t1);  // closes cracks between patches
+    float tau = INFINITY;
+    if (A == 0.f) {
+        if (B != 0.f) {
+            const float x = -C / B;
+            if (x >= -slack && x <= dt + slack) tau = x;
+        }
+    } else {
+        const float disc = fmaf(B, B, -4.f * A * C);
+        if (disc >= 0.f) {
+            const float s = sqrtf(disc);
+            const float qq = -0.5f * (B + copysignf(s, B));
+            const float x1 = qq / A, x2 = (qq != 0.f) ? C / qq : x1;
+            if (x1 >= -slack && x1 <= dt + slack) tau = x1;
+            if (x2 >= -slack && x2 <= dt + slack) tau = fminf(tau, x2);
+        }
+    }
+    if (tau == INFINITY) return false;
+    t_hit = t0 + fminf(fmaxf(tau, 0.f), dt);
+    return true;
+}
+
+__device__ bool trace_cascade(const RayCascade& c, const Ray& r, float ta, float tb, float& t_hit,
+                              DevStatus* status, uint32_t pixel) {
+    const int N = c.N, P = c.P, K = c.K;
+    int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
+    int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
+    int k = K;
+    float t = ta;
+    int64_t off = mip_off(P, k);
+    const int budget = 8 * (2 * N + 8) * (K + 2);
+    for (int it = 0; it < budget; ++it) {
+        const int ni = ci >> k, nj = cj >> k, size = 1 << k;
+        const float tx = r.du > 0.f ? (float((ni + 1) * size) - r.eu) * r.idu
+                         : (r.du < 0.f ? (float(ni * size) - r.eu) * r.idu : INFINITY);
+        const float ty = r.dv > 0.f ? (float((nj + 1) * size) - r.ev) * r.idv
+                         : (r.dv < 0.f ? (float(nj * size) - r.ev) * r.idv : INFINITY);
+        const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
+        const float zmin = fminf(fmaf(t, r.dz, r.ez), fmaf(te, r.dz, r.ez));
+        const float mx = __ldg(c.mip + off + size_t(nj) * (P >> k) + ni);
+        if (zmin <= mx + 2e-6f * fabsf(mx)) {
+            if (k > 0) {
+                --k;
+                off = mip_off(P, k);
+                continue;
+            }
+            if (ci <= N - 2 && cj <= N - 2 && patch_hit(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
+        }
+        if (te >= tb) return false;
+        const int oi = ni, oj = nj;
+        if (tx <= ty) {
+            ci = r.du > 0.f ? (ni + 1) * size : ni * size - 1;
+            int c2 = int(floorf(fmaf(te, r.dv, r.ev)));
+            c2 = r.dv > 0.f ? max(c2, cj) : (r.dv < 0.f ? min(c2, cj) : cj);
+            cj = min(max(c2, nj * size), nj * size + size - 1);
+        } else {
+            cj = r.dv > 0.f ? (nj + 1) * size : nj * size - 1;
+            int c2 = int(floorf(fmaf(te, r.du, r.eu)));
+            c2 = r.du > 0.f ? max(c2, ci) : (r.du < 0.f ? min(c2, ci) : ci);
+            ci = min(max(c2, ni * size), ni * size + size - 1);
+        }
+        if (ci < 0 || ci >= P || cj < 0 || cj >= P) return false;
+        t = te;
+        int kk = k, a = oi, b = oj;
+        while (kk < K && ((ci >> (kk + 1)) != (a >> 1) || (cj >> (kk + 1)) != (b >> 1))) {
+            ++kk;
+            a >>= 1;
+            b >>= 1;
+        }
+        if (kk != k) {
+            k = kk;
+            off = mip_off(P, k);
+        }
+    }
+    report(status, kStatusTimeout, pixel);
+    return false;
+}
+
+// t-interval of the ray inside cascade c: projected depth in [near, far_ext],
+// texel region u, v in [0, N-1], camera clip range [tmin, tmax].
+__device__ __forceinline__ bool cascade_interval(const RayCascade& c, const Ray& r, float ks,
+                                                 float tmin, float tmax, float& ta, float& tb) {
+    float lo = tmin, hi = tmax;
+    if (ks > 0.f) {
+        lo = fmaxf(lo, c.near_d / ks);
+        hi = fminf(hi, c.far_ext / ks);
+    } else if (ks < 0.f) {
+        lo = fmaxf(lo, c.far_ext / ks);
+        hi = fminf(hi, c.near_d / ks);
+    } else if (!(c.near_d <= 0.f && 0.f <= c.far_ext)) {
+        return false;
+    }
+    const float top = float(c.N - 1);
+    if (r.du != 0.f) {
+        const float t0 = (0.f - r.eu) * r.idu, t1 = (top - r.eu) * r.idu;
+        lo = fmaxf(lo, fminf(t0, t1));
+        hi = fminf(hi, fmaxf(t0, t1));
+    } else if (r.eu < 0.f || r.eu > top) {
+        return false;
+    }
+    if (r.dv != 0.f) {
+        const float t0 = (0.f - r.ev) * r.idv, t1 = (top - r.ev) * r.idv;
+        lo = fmaxf(lo, fminf(t0, t1));
+        hi = fminf(hi, fmaxf(t0, t1));
+    } else if (r.ev < 0.f || r.ev > top) {
+        return false;
+    }
+    ta = lo;
+    tb = hi;
+    return lo <= hi;
+}
+
+__device__ __forceinline__ Ray make_ray(const RayCascade& c, float ez, float dx, float dy, float dz) {
+    Ray r;
+    r.eu = c.eu;
+    r.ev = c.ev;
+    r.ez = ez;
+    r.du = dx * c.inv_h;
+    r.dv = dy * c.inv_h;
+    r.dz = dz;
+    r.idu = r.du != 0.f ? 1.f / r.du : 0.f;
+    r.idv = r.dv != 0.f ? 1.f / r.dv : 0.f;
+    return r;
+}
+
+__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
+    const int x = blockIdx.x * 16 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= p.W || y >= p.H) return;
+    const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
+    const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
+    float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
+    float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
+    float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
+    const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    dx *= il;
+    dy *= il;
+    dz *= il;
+    const float fd = fmaf(dx, p.F[0], fmaf(dy, p.F[1], dz * p.F[2]));
+    const float tmin = p.znear / fd, tmax = p.zfar / fd;
+    const float ks = fmaf(dx, p.dir2x, dy * p.dir2y);
+    const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
+    int hit = 0;
+    float t = __int_as_float(0x7fc00000);
+    for (int c = 0; c < p.C && !hit; ++c) {
+        const RayCascade& cc = p.cas[c];
+        const Ray r = make_ray(cc, p.ez, dx, dy, dz);
+        float ta, tb, tc;
+        if (!cascade_interval(cc, r, ks, tmin, tmax, ta, tb)) continue;
+        if (!trace_cascade(cc, r, ta, tb, tc, status, pix)) continue;
+        hit = 1 + c;
+        t = tc;
+        const float s = tc * ks;
+        if (c + 1 < p.C) {
+            const RayCascade& cn = p.cas[c + 1];
+            if (s >= cn.near_d && cc.far_ext > cn.near_d) {
+                const Ray r2 = make_ray(cn, p.ez, dx, dy, dz);
+                float ta2, tb2, t2;
+                if (cascade_interval(cn, r2, ks, tmin, tmax, ta2, tb2) &&
+                    trace_cascade(cn, r2, ta2, tb2, t2, status, pix)) {
+                    const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
+                    t = fmaf(al, t2 - tc, tc);
+                }
+            }
+        }
+    }
+    p.t_out[pix] = t;
+    p.hit_out[pix] = uint8_t(hit);
+}
+
+int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
+    dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
+    k_raycast<<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
+    return cudaGetLastError();
+}
+
+}  // namespace hfi

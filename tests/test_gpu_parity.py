@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle,
+element by element on the same seeded inputs (tolerances in _parity.py)."""
+
+import math
+
+import numpy as np
+import pytest
+
+from _parity import (HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, check_mask, check_rays,
+                     height_error, mask_from_spans, ocas, silhouettes)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True):
+    from paper_2201_10887_gb300 import Renderer
+    r = Renderer(scene.tree, scene.sigma, scene.radius, bucket_level=bucket_level)
+    t, hit = r.render(cam)
+    r.sync()
+    cells = orc.Cells(scene.tree)
+    amp = float(np.abs(cells.cv).max())
+    ov = orc.fit(cam, scene.tree, cells)
+    texs, rcs, worst = [], [], 0.0
+    for c in range(cam.n_cascades):
+        info = r.cascade(0, c)
+        oc = ov.cas[c]
+        assert (info.snap_x, info.snap_y, info.snap_k) == (oc.snap_x, oc.snap_y, oc.snap_k)
+        spans = r.spans(0, c).cpu().numpy()
+        bad, vis = check_mask(orc, info, cells, spans)
+        assert bad == 0, f"cascade {c}: {bad} mask mismatches"
+        tex = r.texture(0, c).cpu().numpy()
+        ref = orc.texel_heights(ocas(orc, info), cells, scene.sigma, scene.radius).reshape(info.N, info.N)
+        assert np.array_equal(np.isfinite(tex), mask_from_spans(spans, info.N))
+        both = np.isfinite(tex) & np.isfinite(ref)
+        worst = max(worst, height_error(np.where(both, tex, -np.inf), np.where(both, ref, -np.inf), amp))
+        mip = r.mip(0, c).cpu().numpy()
+        assert np.array_equal(mip, orc.maxmip(tex)), f"cascade {c}: max mip differs"
+        texs.append(tex)
+        rcs.append(RC(info))
+    assert worst <= HEIGHT_REL, worst
+    ot, oh, seg, _ = orc.raycast(cam, scene.tree, rcs, texs)
+    gt, gh = t.cpu().numpy(), hit.cpu().numpy()
+    frac, off, terr, _ = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width))
+    assert frac <= HIT_MISMATCH and off == 0, (frac, off)
+    assert terr <= RAY_REL, terr
+    # the reported first-hit cascade agrees where both hit
+    both = (gh.ravel() > 0) & (oh > 0)
+    assert np.mean(gh.ravel()[both] != oh[both]) < 1e-3
+    r.close()
+    return worst, terr, int((oh > 0).sum())
+
+
+def test_tiny_frame(orc, torch_cuda, tiny):
+    """The tiny workload as specified: one 256^2 cascade, 320 x 240."""
+    w, terr, hits = _frame_parity(orc, torch_cuda, tiny, tiny.cameras[0])
+    assert hits > 20000
+
+
+@pytest.mark.parametrize("N,W,H,C,lam", [(100, 173, 97, 3, 0.5), (129, 64, 200, 2, 1.0),
+                                         (37, 50, 31, 4, 0.0)])
+def test_ragged_sizes_and_cascades(orc, torch_cuda, tiny, N, W, H, C, lam):
+    """Texture sides and image sizes that are not multiples of any tile."""
+    cam = tiny.cameras[0].with_(n_cascades=C, cascade_size=N, width=W, height=H, split_lambda=lam)
+    _frame_parity(orc, torch_cuda, tiny, cam)
+
+
+def test_far_world_origin(orc, torch_cuda):
+    """World origin at (5e6, 5e6) m: FP64 camera-relative set-up keeps the
+    FP32 path within tolerance."""
+    import workloads
+    s = workloads.precision_config()
+    _frame_parity(orc, torch_cuda, s, s.cameras[0].with_(n_cascades=3, split_lambda=0.5))
+
+
+@pytest.mark.parametrize("bucket_level", [0, 1, 2])
+def test_bucket_levels_agree(orc, torch_cuda, tiny, bucket_level):
+    """Superset lists of any bucket size give the same heights (Section 4)."""
+    cam = tiny.cameras[0].with_(n_cascades=2, cascade_size=128)
+    _frame_parity(orc, torch_cuda, tiny, cam, bucket_level=bucket_level)
+
+
+def test_steep_and_sideways_views(orc, torch_cuda, tiny):
+    base = tiny.cameras[0]
+    for cam in [base.with_(n_cascades=2, forward=(0.0, 0.2, -1.0)),
+                base.with_(n_cascades=3, forward=(-0.8, 0.1, -0.6), vfov=math.radians(40)),
+                base.with_(n_cascades=2, forward=(0.0, 0.0, -1.0), up=(0.0, 1.0, 0.0))]:
+        _frame_parity(orc, torch_cuda, tiny, cam)
+
+
+def test_empty_view(orc, torch_cuda, tiny):
+    from paper_2201_10887_gb300 import Renderer
+    cam = tiny.cameras[0].with_(forward=(0.0, -1.0, 0.2), n_cascades=2)
+    cam = cam.with_(eye=(cam.eye[0], tiny.tree.origin_y - 100.0, cam.eye[2]))
+    r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    t, hit = r.render(cam)
+    r.sync()
+    assert int(hit.sum()) == 0 and bool(torch_cuda.isnan(t).all())
+    for c in range(2):
+        assert r.cascade(0, c).n_poly == 0
+        assert bool(torch_cuda.isinf(r.texture(0, c)).all())
+    r.close()
+
+
+def test_flat_terrain_plane_hits(orc, torch_cuda, tiny):
+    """Constant cell values: every visible texel equals the constant and rays
+    hit the plane at t = (o_z - h0) / (-d_z)."""
+    import copy
+    from paper_2201_10887_gb300 import Renderer
+    tree = copy.copy(tiny.tree)
+    tree.value = np.full_like(tiny.tree.value, 250.0)
+    cam = tiny.cameras[0].with_(n_cascades=2, cascade_size=128)
+    r = Renderer(tree, tiny.sigma, tiny.radius)
+    t, hit = r.render(cam)
+    r.sync()
+    for c in range(2):
+        tex = r.texture(0, c).cpu().numpy()
+        fin = np.isfinite(tex)
+        assert fin.sum() > 1000 and np.max(np.abs(tex[fin] - 250.0)) < 1e-3
+    gt, gh = t.cpu().numpy().ravel(), hit.cpu().numpy().ravel()
+    # independent ray directions from the camera basis
+    F = np.array(cam.forward) / np.linalg.norm(cam.forward)
+    U = np.array(cam.up) - np.dot(cam.up, F) * F
+    U /= np.linalg.norm(U)
+    R = np.cross(F, U)
+    tv = math.tan(cam.vfov / 2)
+    th = tv * cam.width / cam.height
+    py, px = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    sx = (2 * (px.ravel() + 0.5) / cam.width - 1) * th
+    sy = (1 - 2 * (py.ravel() + 0.5) / cam.height) * tv
+    d = F[None] + sx[:, None] * R[None] + sy[:, None] * U[None]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    tp = (cam.eye[2] - 250.0) / (-d[:, 2])
+    ok = gh > 0
+    assert ok.sum() > 10000
+    assert np.max(np.abs(gt[ok] - tp[ok]) / tp[ok]) < 2e-5
+    r.close()
+
+
+def test_update_values(orc, torch_cuda, tiny):
+    """New cell values (e.g. a water level update) without rebuilding."""
+    import copy
+    from paper_2201_10887_gb300 import Renderer
+    cam = tiny.cameras[0].with_(n_cascades=2, cascade_size=96)
+    r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    r.render(cam)
+    new = (tiny.tree.value * 0.5 + 40.0).astype(np.float32)
+    r.update_values(new)
+    r.render(cam)
+    r.sync()
+    tree2 = copy.copy(tiny.tree)
+    tree2.value = new
+    cells = orc.Cells(tree2)
+    amp = float(np.abs(cells.cv).max())
+    for c in range(2):
+        info = r.cascade(0, c)
+        ref = orc.texel_heights(ocas(orc, info), cells, tiny.sigma, tiny.radius).reshape(info.N, info.N)
+        assert height_error(r.texture(0, c).cpu().numpy(), ref, amp) <= HEIGHT_REL
+    r.close()
+
+
+def test_minimal_texture(orc, torch_cuda, tiny):
+    """N = 2: one patch per cascade, a single-entry max mipmap."""
+    cam = tiny.cameras[0].with_(n_cascades=1, cascade_size=2, width=16, height=12)
+    from paper_2201_10887_gb300 import Renderer
+    r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    r.render(cam)
+    r.sync()
+    tex = r.texture(0, 0).cpu().numpy()
+    assert np.array_equal(r.mip(0, 0).cpu().numpy(), orc.maxmip(tex))
+    r.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("frame", [0, 60])
+def test_dem_frame_sampled(orc, torch_cuda, frame):
+    """DEM-scale workload (4.5 M leaves, four 2048^2 cascades, 1920 x 1080)
+    in the bench's launch configuration: full mask and max-mip comparison,
+    sampled texels and pixels against the oracle."""
+    import workloads
+    from paper_2201_10887_gb300 import Renderer
+    s = workloads.dem_config(n_frames=120)
+    cam = s.cameras[frame]
+    r = Renderer(s.tree, s.sigma, s.radius)
+    t, hit = r.render(cam)
+    r.sync()
+    cells = orc.Cells(s.tree)
+    amp = float(np.abs(cells.cv).max())
+    rng = np.random.default_rng(frame)
+    texs, rcs = [], []
+    for c in range(cam.n_cascades):
+        info = r.cascade(0, c)
+        spans = r.spans(0, c).cpu().numpy()
+        bad, vis = check_mask(orc, info, cells, spans)
+        assert bad == 0
+        tex = r.texture(0, c).cpu().numpy()
+        assert np.array_equal(np.isfinite(tex), mask_from_spans(spans, info.N))
+        jj, ii = np.nonzero(vis & np.isfinite(tex))
+        pick = rng.choice(jj.size, size=min(4000, jj.size), replace=False)
+        ref = orc.texel_heights(ocas(orc, info), cells, s.sigma, s.radius, ii[pick], jj[pick])
+        got = tex[jj[pick], ii[pick]]
+        err = np.max(np.abs(got - ref) / np.maximum(np.abs(ref), amp))
+        assert err <= HEIGHT_REL, (c, err)
+        assert np.array_equal(r.mip(0, c).cpu().numpy(), orc.maxmip(tex))
+        texs.append(tex)
+        rcs.append(RC(info))
+    H, W = cam.height, cam.width
+    gt, gh = t.cpu().numpy(), hit.cpu().numpy()
+    py = rng.integers(1, H - 1, 6000)
+    px = rng.integers(1, W - 1, 6000)
+    ot, oh, seg, _ = orc.raycast(cam, s.tree, rcs, texs, pixels=(px, py))
+    g_t, g_h = gt[py, px], gh[py, px]
+    mism = np.nonzero((g_h > 0) != (oh > 0))[0]
+    assert mism.size <= HIT_MISMATCH * px.size + 1
+    for q in mism:  # every mismatch must sit on a silhouette of the reference
+        yy, xx = np.meshgrid(np.arange(py[q] - 1, py[q] + 2), np.arange(px[q] - 1, px[q] + 2), indexing="ij")
+        nt, nh, _, _ = orc.raycast(cam, s.tree, rcs, texs, pixels=(xx.ravel(), yy.ravel()))
+        assert silhouettes(nh.reshape(3, 3), nt.reshape(3, 3))[1, 1]
+    both = (g_h > 0) & (oh > 0)
+    assert np.max(np.abs(g_t[both] - ot[both]) / seg[both]) <= RAY_REL
+    r.close()

@@ -1,0 +1,172 @@
+"""CPU checks of the C-ABI library: it loads, exports every entry point that
+include/hf.h declares, validates its inputs, and its host-side cascade fit
+agrees with the oracle's independent fit (no device work is launched)."""
+
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hfmod():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2201_10887_gb300 import hf
+    return hf
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hf_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(hfmod):
+    names = _declared()
+    assert len(names) >= 12
+    lib = ct.CDLL(hfmod.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(hfmod.EXPORTED) <= set(names)
+
+
+def test_product_does_not_use_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2201_10887_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
+                assert "hf_oracle" not in txt and "liboracle" not in txt, f
+
+
+def _tiny_ctx(hfmod, tiny, **kw):
+    t = tiny.tree
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    rbf = hfmod.hf_rbf_params(kw.get("sigma", tiny.sigma), kw.get("radius", tiny.radius), 0, -1)
+    return hfmod.hf_create_quadtree(desc, hfmod.leaves_array(t.level, t.ix, t.iy, t.value), rbf)
+
+
+def test_create_and_query(hfmod, tiny):
+    ctx = _tiny_ctx(hfmod, tiny)
+    p, v = hfmod.hf_query_bytes(ctx, 3, 256)
+    assert p > tiny.tree.n_leaves * 16 and v >= 3 * 256 * 256 * 4
+    with pytest.raises(hfmod.HFError) as e:
+        hfmod.hf_query_bytes(ctx, 9, 256)
+    assert e.value.code == hfmod.HF_ERR_ARG
+    hfmod.hf_destroy(ctx)
+
+
+def _bad(hfmod, tiny, mutate):
+    t = tiny.tree
+    lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    rbf = hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1)
+    lv, desc, rbf = mutate(lv, desc, rbf)
+    with pytest.raises(hfmod.HFError) as e:
+        hfmod.hf_create_quadtree(desc, lv, rbf)
+    return e.value.code
+
+
+def test_rejects_invalid_quadtrees(hfmod, tiny):
+    def dup(lv, d, r):
+        return np.concatenate([lv, lv[:1]]), d, r
+
+    def gap(lv, d, r):
+        return lv[1:], d, r
+
+    def overlap(lv, d, r):
+        k = int(np.nonzero(lv["level"] == 1)[0][0])
+        extra = lv[k:k + 1].copy()
+        extra["level"] = 0
+        extra["ix"] //= 2
+        extra["iy"] //= 2
+        return np.concatenate([lv, extra]), d, r
+
+    def out_of_range(lv, d, r):
+        lv = lv.copy()
+        lv["ix"][0] = 10 ** 6
+        return lv, d, r
+
+    def nan_value(lv, d, r):
+        lv = lv.copy()
+        lv["value"][3] = np.nan
+        return lv, d, r
+
+    def bad_sigma(lv, d, r):
+        r.sigma = 0.0
+        return lv, d, r
+
+    def bad_level(lv, d, r):
+        d.max_level = 16
+        return lv, d, r
+
+    for m in [dup, gap, overlap, out_of_range, nan_value, bad_sigma, bad_level]:
+        assert _bad(hfmod, tiny, m) == hfmod.HF_ERR_ARG, m.__name__
+
+
+def _set_camera_fake(hfmod, ctx, cam, C, N):
+    """Host-only fit: hf_set_camera only records the buffer address."""
+    from paper_2201_10887_gb300.renderer import camera_struct
+    need = hfmod.hf_query_bytes(ctx, C, N)[1]
+    return hfmod.lib().hf_set_camera(ctx, 0, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
+                                     ct.c_size_t(need))
+
+
+def test_call_order_and_buffer_checks(hfmod, tiny):
+    ctx = _tiny_ctx(hfmod, tiny)
+    cam = tiny.cameras[0]
+    lib = hfmod.lib()
+    assert lib.hf_discretize_cascades(ctx, 0, None) == hfmod.HF_ERR_STATE
+    assert lib.hf_raycast(ctx, 0, ct.c_void_p(1 << 20), ct.c_void_p(1 << 20), None) == hfmod.HF_ERR_STATE
+    from paper_2201_10887_gb300.renderer import camera_struct
+    assert lib.hf_set_camera(ctx, 0, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
+                             ct.c_size_t(1000)) == hfmod.HF_ERR_NOMEM
+    assert lib.hf_set_camera(ctx, 0, ct.byref(camera_struct(cam)), ct.c_void_p((1 << 30) + 8),
+                             ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
+    assert lib.hf_set_camera(ctx, 256, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
+                             ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
+    assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
+    # the mip build needs a discretized view
+    assert lib.hf_build_maxmip(ctx, 0, None) == hfmod.HF_ERR_STATE
+    # no persistent buffer bound yet
+    assert lib.hf_discretize_cascades(ctx, 0, None) == hfmod.HF_ERR_STATE
+    bad = camera_struct(cam.with_(vfov=0.0))
+    assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
+    hfmod.hf_destroy(ctx)
+
+
+@pytest.mark.parametrize("variant", ["base", "three", "steep", "side", "far_origin"])
+def test_library_fit_matches_oracle(hfmod, orc, tiny, variant):
+    import math
+    import workloads
+    scene = tiny if variant != "far_origin" else workloads.precision_config()
+    base = scene.cameras[0]
+    cam = {"base": base,
+           "three": base.with_(n_cascades=3, split_lambda=1.0),
+           "steep": base.with_(n_cascades=2, forward=(0.0, 0.2, -1.0)),
+           "side": base.with_(n_cascades=4, split_lambda=0.5, forward=(-0.8, 0.1, -0.6),
+                              vfov=math.radians(40)),
+           "far_origin": base.with_(n_cascades=3, split_lambda=0.5)}[variant]
+    ctx = _tiny_ctx(hfmod, scene)
+    assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
+    cells = orc.Cells(scene.tree)
+    ov = orc.fit(cam, scene.tree, cells)
+    for c in range(cam.n_cascades):
+        li = hfmod.hf_get_cascade(ctx, 0, c)
+        oc = ov.cas[c]
+        assert (li.snap_x, li.snap_y, li.snap_k) == (oc.snap_x, oc.snap_y, oc.snap_k)
+        assert li.n_poly == oc.n_poly
+        if li.n_poly:
+            assert np.max(np.abs(li.polygon() - oc.polygon())) < 1e-9 * scene.tree.width
+        assert li.near == pytest.approx(oc.near, abs=1e-9) and li.far_ext == pytest.approx(oc.far_ext, abs=1e-9)
+        assert li.texel == oc.h and li.ox == oc.ox and li.oy == oc.oy
+    hfmod.hf_destroy(ctx)

@@ -126,65 +126,79 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (the baseline, and the reference arm)
 
-def oracle_frame_sample(scene, cam, cells, n_texels: int, n_rays: int, seed: int) -> dict:
-    """Time the FP64 oracle on a sample of one frame and extrapolate to the
-    whole frame: Eq. 2 at `n_texels` random visible texels (scaled to all
-    visible texels of the four cascades), the max mipmaps in full, and
-    `n_rays` random pixels (scaled to 1920 x 1080).  The ray sample runs on
-    cascade textures filled from the terrain generator at the texel centres,
-    which have the traversal structure of the discretized surface."""
+def oracle_frame_sample(scene, cam, cells, target_s: float, seed: int) -> dict:
+    """Time the FP64 oracle on a bounded sample of one frame and extrapolate
+    to the whole frame.  Timed in full: the cascade fit, the visible-texel
+    masks and the max mipmaps.  Sampled: Eq. 2 at random visible texels
+    (scaled to all visible texels of the cascades) and random pixels (scaled
+    to the image), each sized to about half of `target_s` after a short
+    calibration.  The ray sample runs on cascade textures filled from the
+    terrain generator at the texel centres, which have the traversal
+    structure of the discretized surface."""
     import numpy as np
     import oracle
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     view = oracle.fit(cam, scene.tree, cells)
-    t_fit = time.perf_counter() - t0
-    n_vis, vis_list, texs, rcs = 0, [], [], []
+    vis_list = []
+    for c in range(cam.n_cascades):
+        vis, _ = oracle.mask(view.cas[c], cells)
+        vis_list.append(vis.reshape(view.cas[c].N, view.cas[c].N).astype(bool))
+    t_fixed = time.perf_counter() - t0
+    texs, rcs = [], []
     for c in range(cam.n_cascades):
         cas = view.cas[c]
-        vis, _ = oracle.mask(cas, cells)
-        vis = vis.reshape(cas.N, cas.N).astype(bool)
-        n_vis += int(vis.sum())
-        vis_list.append(vis)
         xs = cas.ox + np.arange(cas.N) * cas.h
         ys = cas.oy + np.arange(cas.N) * cas.h
         tex = scene.fbm.grid(xs, ys).astype(np.float32)
-        tex[~vis] = -np.inf
+        tex[~vis_list[c]] = -np.inf
         texs.append(tex)
         rcs.append(type("RC", (), dict(ox=cas.ox, oy=cas.oy, h=cas.h, near=cas.near,
                                       far_ext=cas.far_ext, N=cas.N)))
-    # Eq. 2 on a sample of visible texels
-    weights = np.array([v.sum() for v in vis_list], float)
-    cas_pick = rng.choice(len(vis_list), size=n_texels, p=weights / weights.sum())
-    t_rbf = 0.0
-    for c in range(len(vis_list)):
-        k = int((cas_pick == c).sum())
-        if k == 0:
-            continue
-        jj, ii = np.nonzero(vis_list[c])
-        sel = rng.choice(jj.size, size=k, replace=True)
-        t0 = time.perf_counter()
-        oracle.texel_heights(view.cas[c], cells, scene.sigma, scene.radius, ii[sel], jj[sel])
-        t_rbf += time.perf_counter() - t0
     t0 = time.perf_counter()
     for tex in texs:
         oracle.maxmip(tex)
-    t_mip = time.perf_counter() - t0
-    px = rng.integers(0, cam.width, n_rays)
-    py = rng.integers(0, cam.height, n_rays)
-    t0 = time.perf_counter()
-    oracle.raycast(cam, scene.tree, rcs, texs, pixels=(px, py))
-    t_ray = time.perf_counter() - t0
+    t_fixed += time.perf_counter() - t0
+    n_vis = int(sum(v.sum() for v in vis_list))
+    weights = np.array([v.sum() for v in vis_list], float)
+    pix = [(jj, ii) for jj, ii in (np.nonzero(v) for v in vis_list)]
+
+    def rbf(n):
+        cas_pick = rng.choice(len(vis_list), size=n, p=weights / weights.sum())
+        dt = 0.0
+        for c in range(len(vis_list)):
+            k = int((cas_pick == c).sum())
+            if k:
+                jj, ii = pix[c]
+                sel = rng.integers(0, jj.size, k)
+                t1 = time.perf_counter()
+                oracle.texel_heights(view.cas[c], cells, scene.sigma, scene.radius, ii[sel], jj[sel])
+                dt += time.perf_counter() - t1
+        return dt / n
+
+    def rays(n):
+        px = rng.integers(0, cam.width, n)
+        py = rng.integers(0, cam.height, n)
+        t1 = time.perf_counter()
+        oracle.raycast(cam, scene.tree, rcs, texs, pixels=(px, py))
+        return (time.perf_counter() - t1) / n
+
+    cal = 400
+    per_texel, per_ray = rbf(cal), rays(cal)
+    n_tex = int(min(max(0.5 * target_s / max(per_texel, 1e-9), cal), 5e6))
+    n_ray = int(min(max(0.5 * target_s / max(per_ray, 1e-9), cal), 5e6))
+    per_texel, per_ray = rbf(n_tex), rays(n_ray)
     npx = cam.width * cam.height
-    ms = 1e3 * (t_fit + t_rbf * n_vis / n_texels + t_mip + t_ray * npx / n_rays)
-    return {"frame_ms": ms, "visible_texels": n_vis, "sampled_s": t_fit + t_rbf + t_mip + t_ray,
-            "n_texels": n_texels, "n_rays": n_rays}
+    ms = 1e3 * (t_fixed + per_texel * n_vis + per_ray * npx)
+    return {"frame_ms": ms, "visible_texels": n_vis, "n_texels": n_tex, "n_rays": n_ray,
+            "sampled_s": t_fixed + per_texel * n_tex + per_ray * n_ray}
 
 
-def _oracle_sample_text(n_texels, n_rays):
-    return (f"per frame: Eq. 2 at {n_texels} random visible texels (scaled to all visible "
-            f"texels), full max mipmaps, {n_rays} random pixels (scaled to 1920x1080) on "
-            f"generator-filled cascade textures; FP64, OpenMP")
+def _oracle_sample_text(res):
+    return (f"per frame: fit, masks and max mipmaps in full; Eq. 2 at {res['n_texels']} random "
+            f"visible texels (scaled to {res['visible_texels']}), {res['n_rays']} random pixels "
+            f"(scaled to 1920x1080) on generator-filled cascade textures; FP64, OpenMP; "
+            f"{res['sampled_s']:.1f} s of CPU work")
 
 
 def run_reference(args, rank, world):
@@ -196,12 +210,12 @@ def run_reference(args, rank, world):
     scene = workloads.dem_config(n_frames=args.frames)
     cells = oracle.Cells(scene.tree)
     frames = frame_schedule(args.frames, args.warmup + args.steps, 0, 1)
-    n_tex, n_ray = args.ref_texels, args.ref_rays
-    per = []
+    per_step_s = min(args.ref_step_s, 150.0 / max(len(frames), 1))
+    per, last = [], None
     for k, f in enumerate(frames):
-        r = oracle_frame_sample(scene, scene.cameras[f], cells, n_tex, n_ray, seed=k)
+        last = oracle_frame_sample(scene, scene.cameras[f], cells, per_step_s, seed=k)
         if k >= args.warmup:
-            per.append(r["frame_ms"])
+            per.append(last["frame_ms"])
     ms = statistics.mean(per)
     cores = oracle.threads()
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -212,7 +226,7 @@ def run_reference(args, rank, world):
                        "l2": "n/a (CPU)"},
             "p50_ms": statistics.median(per), "p99_ms": _pct(per, 99),
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
-                             "sample": _oracle_sample_text(n_tex, n_ray)},
+                             "sample": _oracle_sample_text(last) + f"; {per_step_s:.2f} s target per step"},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -357,12 +371,10 @@ def run_ours(args, rank, world, local_rank):
             import oracle
             oracle.build()
             cells = oracle.Cells(scene.tree)
-            res = oracle_frame_sample(scene, cams[sched[0]], cells, args.ref_texels * 4,
-                                      args.ref_rays * 4, seed=0)
+            res = oracle_frame_sample(scene, cams[sched[0]], cells, args.cpu_s, seed=0)
             line["cpu_baseline"] = {"value": res["frame_ms"], "unit": "ms", "cores": oracle.threads(),
                                     "kind": "oracle",
-                                    "sample": _oracle_sample_text(args.ref_texels * 4, args.ref_rays * 4)
-                                    + f"; frame {sched[0]}; {res['sampled_s']:.1f} s of CPU work"}
+                                    "sample": _oracle_sample_text(res) + f"; frame {sched[0]}"}
         print(json.dumps(line), flush=True)
     r.close()
 
@@ -374,8 +386,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=120)
-    ap.add_argument("--ref-texels", type=int, default=3000)
-    ap.add_argument("--ref-rays", type=int, default=3000)
+    ap.add_argument("--ref-step-s", type=float, default=4.0, help="CPU seconds per reference step")
+    ap.add_argument("--cpu-s", type=float, default=15.0, help="CPU seconds of the baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

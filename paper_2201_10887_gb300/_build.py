@@ -19,7 +19,7 @@ OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = ["hf_host.cpp", "hf_fit.cpp", "hf_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-pthread",
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-pthread,-ffp-contract=off",
           "-I" + CSRC, "-I" + INCLUDE]
 
 

@@ -57,12 +57,17 @@ struct P2 {
     double x, y;
 };
 
-// Andrew's monotone chain; counter-clockwise, collinear points dropped.
+// Andrew's monotone chain; counter-clockwise.  The chain pops only on a
+// non-left turn, so it is convex for the points as given; afterwards
+// near-coincident vertices and vertices within 1e-9 of the line through
+// their neighbours are removed.  On a convex chain such a vertex lies between
+// its neighbours, so removing it never loses an extreme point, whatever
+// rounding noise (e.g. from fused multiply-adds) tilted a straight run.
 std::vector<P2> monotone_hull(std::vector<P2> pts) {
     if (pts.size() < 3) return {};
     double scale = 1.0;
     for (const P2& p : pts) scale = std::max(scale, std::max(std::fabs(p.x), std::fabs(p.y)));
-    const double eps = 1e-12 * scale * scale;
+    const double same = 1e-9 * scale;
     std::sort(pts.begin(), pts.end(), [](const P2& a, const P2& b) {
         return a.x < b.x || (a.x == b.x && a.y < b.y);
     });
@@ -72,32 +77,39 @@ std::vector<P2> monotone_hull(std::vector<P2> pts) {
     std::vector<P2> h(2 * pts.size());
     size_t k = 0;
     for (size_t i = 0; i < pts.size(); ++i) {
-        while (k >= 2 && turn(h[k - 2], h[k - 1], pts[i]) <= eps) k--;
+        while (k >= 2 && turn(h[k - 2], h[k - 1], pts[i]) <= 0.0) k--;
         h[k++] = pts[i];
     }
     for (size_t i = pts.size() - 1, t = k + 1; i-- > 0;) {
-        while (k >= t && turn(h[k - 2], h[k - 1], pts[i]) <= eps) k--;
+        while (k >= t && turn(h[k - 2], h[k - 1], pts[i]) <= 0.0) k--;
         h[k++] = pts[i];
     }
     h.resize(k > 0 ? k - 1 : 0);
-    // drop near-coincident neighbours left by rounding
-    std::vector<P2> out;
-    const double same = 1e-9 * scale;
-    for (const P2& p : h)
-        if (out.empty() || std::fabs(p.x - out.back().x) > same || std::fabs(p.y - out.back().y) > same)
-            out.push_back(p);
-    while (out.size() > 1 && std::fabs(out.front().x - out.back().x) <= same &&
-           std::fabs(out.front().y - out.back().y) <= same)
-        out.pop_back();
-    if (out.size() < 3) return {};
+    bool changed = true;
+    while (changed && h.size() >= 3) {
+        changed = false;
+        for (size_t i = 0; i < h.size() && h.size() >= 3; ++i) {
+            const P2& a = h[(i + h.size() - 1) % h.size()];
+            const P2& m = h[i];
+            const P2& b = h[(i + 1) % h.size()];
+            const double len = std::hypot(b.x - a.x, b.y - a.y);
+            const bool coincident = std::fabs(m.x - a.x) <= same && std::fabs(m.y - a.y) <= same;
+            if (coincident || std::fabs(turn(a, m, b)) <= same * len) {
+                h.erase(h.begin() + long(i));
+                changed = true;
+                break;
+            }
+        }
+    }
+    if (h.size() < 3) return {};
     double area = 0.0;
-    for (size_t i = 0; i < out.size(); ++i) {
-        const P2& a = out[i];
-        const P2& b = out[(i + 1) % out.size()];
+    for (size_t i = 0; i < h.size(); ++i) {
+        const P2& a = h[i];
+        const P2& b = h[(i + 1) % h.size()];
         area += a.x * b.y - b.x * a.y;
     }
-    if (0.5 * area <= eps) return {};
-    return out;
+    if (0.5 * area <= same * scale) return {};
+    return h;
 }
 
 // 2-D half-plane clip: keep s(p) = (p - e).dir >= lo (keep_ge) or <= hi.
@@ -182,7 +194,9 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
             if (poly.empty()) break;
             poly = clip_poly(poly, pl);
         }
-        for (const V3& p : poly) ground.push_back({p.x, p.y});
+        // the volume lies inside the box: clamp away rounding excursions
+        for (const V3& p : poly)
+            ground.push_back({std::min(std::max(p.x, 0.0), W), std::min(std::max(p.y, 0.0), H)});
     };
     for (const auto& f : ffaces) add_clipped(f, box);
     for (const auto& f : bfaces) add_clipped(f, fr);

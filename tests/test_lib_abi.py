@@ -170,3 +170,44 @@ def test_library_fit_matches_oracle(hfmod, orc, tiny, variant):
         assert li.near == pytest.approx(oc.near, abs=1e-9) and li.far_ext == pytest.approx(oc.far_ext, abs=1e-9)
         assert li.texel == oc.h and li.ox == oc.ox and li.oy == oc.oy
     hfmod.hf_destroy(ctx)
+
+
+def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
+    """Random cameras (position, heading, pitch, roll, field of view, cascade
+    settings): the library's fit and the oracle's agree on every integer snap
+    and on the polygons."""
+    import math
+    rng = np.random.default_rng(11)
+    ctx = _tiny_ctx(hfmod, tiny)
+    cells = orc.Cells(tiny.tree)
+    W = tiny.tree.width
+    checked = 0
+    for trial in range(300):
+        yaw, pitch = rng.uniform(0, 2 * math.pi), rng.uniform(-1.5, 0.3)
+        fwd = (math.cos(pitch) * math.cos(yaw), math.cos(pitch) * math.sin(yaw), math.sin(pitch))
+        roll = rng.uniform(-0.3, 0.3)
+        up = (math.sin(roll) * math.sin(yaw), -math.sin(roll) * math.cos(yaw), math.cos(roll))
+        eye = (tiny.tree.origin_x + rng.uniform(-200, 840), tiny.tree.origin_y + rng.uniform(-200, 840),
+               rng.uniform(150, 1200))
+        cam = tiny.cameras[0].with_(eye=eye, forward=fwd, up=up, vfov=rng.uniform(0.3, 1.5),
+                                    n_cascades=int(rng.integers(1, 9)),
+                                    cascade_size=int(rng.integers(2, 600)),
+                                    width=int(rng.integers(16, 400)), height=int(rng.integers(16, 400)),
+                                    split_lambda=float(rng.uniform(0, 1)),
+                                    overlap_frac=float(rng.uniform(0, 0.2)))
+        assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
+        ov = orc.fit(cam, tiny.tree, cells)
+        for c in range(cam.n_cascades):
+            li = hfmod.hf_get_cascade(ctx, 0, c)
+            oc = ov.cas[c]
+            assert (li.snap_x, li.snap_y, li.snap_k) == (oc.snap_x, oc.snap_y, oc.snap_k), (trial, c)
+            assert (li.n_poly == 0) == (oc.n_poly == 0), (trial, c)
+            if li.n_poly:
+                lp, op = li.polygon(), oc.polygon()
+                # every vertex of one polygon is a vertex of the other
+                d1 = np.min(np.linalg.norm(lp[:, None] - op[None], axis=2), axis=1)
+                d2 = np.min(np.linalg.norm(op[:, None] - lp[None], axis=2), axis=1)
+                assert d1.max() < 1e-7 * W and d2.max() < 1e-7 * W, (trial, c)
+                checked += 1
+    assert checked > 300
+    hfmod.hf_destroy(ctx)

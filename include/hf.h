@@ -195,6 +195,29 @@ typedef struct {
 } hf_view_stats_t;
 int hf_view_stats(hf_ctx* ctx, int32_t view_slot, hf_view_stats_t* out, void* stream);
 
+/* Allocation-free discretization.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at all, such
+ * as a plug-in whose host application owns every device allocation and only
+ * hands it finished output buffers, or a render loop that forbids cudaMalloc
+ * after start-up because it can synchronise the device and stall a frame.
+ * It fits `cam` (as hf_set_camera does) and computes the same visible texels
+ * and heights as hf_discretize_cascades, writing cascade c's N x N FP32
+ * texture to tex_out[c] (a host array of cam->n_cascades device pointers,
+ * each 256-byte aligned with room for N*N floats).  Its scratch (visible-row
+ * spans and texel coordinates, 16 bytes per texture row per cascade) lives in
+ * a fixed 256 KiB array inside the library, so n_cascades * cascade_size may
+ * not exceed 16384 (HF_ERR_ARG otherwise); nothing is allocated.  The array is
+ * loaded on every device that loads the library and stays until exit.  The
+ * first call on a device looks the array's address up, so make that first
+ * call before capturing any stream.  All calls share the array: calls that
+ * overlap on the GPU (e.g. on two streams at once) race and must be ordered
+ * by the caller.  If info_out is not NULL it receives the cam->n_cascades
+ * fitted cascades (device pointers other than tex are NULL).  The context's
+ * persistent buffer must be bound. */
+#define HF_NOALLOC_SCRATCH_BYTES (256 * 1024)
+int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_out,
+                          hf_cascade_info* info_out, void* stream);
+
 /* Waits for `stream` and reports errors recorded on the device since the
  * last hf_sync (HF_ERR_TIMEOUT, HF_ERR_DATA) or by the CUDA runtime. */
 int hf_sync(hf_ctx* ctx, void* stream);

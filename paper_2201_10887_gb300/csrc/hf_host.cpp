@@ -210,6 +210,95 @@ ViewSlot* get_view(hf_ctx* ctx, int32_t slot) {
 
 }  // namespace
 
+int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
+                                   char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
+                                   PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
+                                   DevStatus** status) {
+    if (!ctx || !cam || !tex) return fail(HF_ERR_ARG, "null argument");
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    const hf_camera& c = *cam;
+    if (!finite3(c.eye) || !finite3(c.forward) || !finite3(c.up))
+        return fail(HF_ERR_ARG, "camera vectors must be finite");
+    if (c.forward[0] == 0.0 && c.forward[1] == 0.0 && c.forward[2] == 0.0) return fail(HF_ERR_ARG, "zero forward vector");
+    if (!(c.vfov > 0.0 && c.vfov < 3.1)) return fail(HF_ERR_ARG, "vfov must be in (0, 3.1) radians");
+    if (!(c.znear > 0.0 && c.zfar > c.znear && std::isfinite(c.zfar))) return fail(HF_ERR_ARG, "need 0 < znear < zfar");
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return fail(HF_ERR_ARG, "image size out of range");
+    if (c.n_cascades < 1 || c.n_cascades > HF_MAX_CASCADES) return fail(HF_ERR_ARG, "n_cascades must be 1..%d", HF_MAX_CASCADES);
+    if (c.cascade_size < 2 || c.cascade_size > kMaxCascadeSize) return fail(HF_ERR_ARG, "cascade_size must be 2..%d", kMaxCascadeSize);
+    if (!(c.split_lambda >= 0.0 && c.split_lambda <= 1.0)) return fail(HF_ERR_ARG, "split_lambda must be in [0, 1]");
+    if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
+    const int C = c.n_cascades, N = c.cascade_size;
+    const size_t need = size_t(C) * size_t(N) * 16;
+    if (need > scratch_bytes)
+        return fail(HF_ERR_ARG, "n_cascades * cascade_size = %lld exceeds the %zu rows of the built-in scratch",
+                    (long long)C * N, scratch_bytes / 16);
+    for (int k = 0; k < C; ++k)
+        if (!tex[k] || (reinterpret_cast<uintptr_t>(tex[k]) & 255))
+            return fail(HF_ERR_ARG, "output texture %d is null or not 256-byte aligned", k);
+    double eye_local[3] = {c.eye[0] - ctx->desc.origin_x, c.eye[1] - ctx->desc.origin_y, c.eye[2]};
+    FitDomain dom{ctx->width, ctx->height, ctx->zmin, ctx->zmax, ctx->c_min};
+    std::unique_ptr<FitResult> fit(new FitResult);
+    int rc = fit_cascades(c, eye_local, dom, fit.get());
+    if (rc) return fail(rc, "cascade fit produced an oversized polygon");
+    std::memset(pp, 0, sizeof(*pp));
+    std::memset(dp, 0, sizeof(*dp));
+    pp->C = C;
+    pp->max_N = N;
+    pp->dom_w = ctx->width;
+    pp->dom_h = ctx->height;
+    pp->eps_frac = 1e-6;
+    dp->C = C;
+    dp->max_N = N;
+    dp->precision = ctx->rbf.precision;
+    dp->K = float(std::exp(-ctx->rbf.radius * ctx->rbf.radius / (2.0 * ctx->rbf.sigma * ctx->rbf.sigma)));
+    int2* spans = reinterpret_cast<int2*>(scratch);
+    float* xs = reinterpret_cast<float*>(scratch + size_t(C) * N * 8);
+    float* ys = xs + size_t(C) * N;
+    for (int k = 0; k < C; ++k) {
+        const hf_cascade_info& ci = fit->cas[k];
+        PrepCascade& q = pp->cas[k];
+        q.ox = ci.ox;
+        q.oy = ci.oy;
+        q.h = ci.texel;
+        q.inv_h = 1.0 / ci.texel;
+        q.N = N;
+        q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
+        const double delta = std::sqrt(2.0) * ci.texel;
+        for (int e = 0; e < q.n_edges; ++e) {
+            const double ax = ci.poly[e][0], ay = ci.poly[e][1];
+            const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
+            const double len = std::hypot(bx - ax, by - ay);
+            const double nx = (by - ay) / len, ny = -(bx - ax) / len;
+            q.ny[e] = ny;
+            q.c[e] = nx * ax + ny * ay + delta;
+            q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
+            q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
+        }
+        q.spans = spans + size_t(k) * N;
+        q.xs = xs + size_t(k) * N;
+        q.ys = ys + size_t(k) * N;
+        DiscCascade& d = dp->cas[k];
+        d.N = N;
+        d.spans = q.spans;
+        d.xs = q.xs;
+        d.ys = q.ys;
+        d.tex = tex[k];
+        if (info_out) {
+            info_out[k] = ci;
+            info_out[k].tex = tex[k];
+            info_out[k].mip = nullptr;
+            info_out[k].spans = nullptr;
+            info_out[k].mip_floats = mip_floats(N);
+        }
+    }
+    *lt = ctx->lookup_tables(true);
+    *lv = ctx->lists();
+    *status = ctx->d_status();
+    return HF_OK;
+}
+
+int hfi::set_cuda_error(int e, const char* what) { return cuda_fail(e, what); }
+
 extern "C" {
 
 const char* hf_last_error(void) { return g_err.c_str(); }

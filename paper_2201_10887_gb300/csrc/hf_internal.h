@@ -146,6 +146,16 @@ int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& l
                  DevStatus* status, void* stream);
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
 
+// Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the
+// prep / discretize parameters for output textures `tex` and the scratch
+// block `scratch` (spans, then xs, then ys of every cascade).
+int noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
+                              char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
+                              PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
+                              DevStatus** status);
+// Records a CUDA failure as the calling thread's last error; returns HF_ERR_CUDA.
+int set_cuda_error(int e, const char* what);
+
 // Host-side count of each bucket's candidates (same enumeration as the fill
 // kernel, in exact integer arithmetic).  Bitmaps must hold host pointers.
 void count_lists_host(const EnumTables& et, const LookupTables& lt, int64_t* counts,

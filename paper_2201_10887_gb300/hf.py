@@ -26,7 +26,9 @@ LEAF_DTYPE = np.dtype([("level", "<i4"), ("ix", "<i4"), ("iy", "<i4"), ("value",
 
 EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_update_values",
             "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
-            "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error"]
+            "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
+            "hf_discretize_noalloc"]
+HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 
 class HFError(RuntimeError):
@@ -98,6 +100,7 @@ def _load():
         "hf_get_cascade": [vp, i32, i32, P(hf_cascade_info)],
         "hf_view_stats": [vp, i32, P(hf_view_stats_t), vp],
         "hf_sync": [vp, vp],
+        "hf_discretize_noalloc": [vp, P(hf_camera), P(vp), P(hf_cascade_info), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -199,6 +202,17 @@ def hf_view_stats(ctx, slot: int, n_cascades: int, stream=None) -> dict:
     return {"visible_texels": list(st.visible_texels)[:n_cascades],
             "candidates": list(st.candidates)[:n_cascades],
             "influencers": list(st.influencers)[:n_cascades]}
+
+
+def hf_discretize_noalloc(ctx, cam: hf_camera, tex_out, stream=None):
+    """Allocation-free discretization into caller-provided textures (one
+    contiguous CUDA float32 tensor of N*N elements per cascade); returns the
+    fitted cascades.  See include/hf.h for the limits and the shared scratch."""
+    n = len(tex_out)
+    ptrs = (ct.c_void_p * n)(*[_dptr(t).value for t in tex_out])
+    info = (hf_cascade_info * n)()
+    _check(_lib.hf_discretize_noalloc(ctx, ct.byref(cam), ptrs, info, _stream(stream)))
+    return list(info)
 
 
 def hf_sync(ctx, stream=None):

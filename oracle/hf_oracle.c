@@ -628,8 +628,10 @@ static int trace_dda(const float* tex, int N, const prj_ray* r, double ta, doubl
 /* First hit by maximum-mipmap traversal (Tevs et al.): a node whose maximum
  * lies below the ray over the node's extent is skipped whole; otherwise it
  * is refined down to single patches, which are intersected exactly.  The
- * current level-0 patch (ci, cj) is tracked as integers; after leaving a
- * node the walk moves up to the largest node it has newly entered.        */
+ * current level-0 patch (ci, cj) is tracked as integers; after a step the
+ * walk climbs one level when it has left its parent node.  The part of the
+ * segment above the top entry (the global maximum) cannot hit and is
+ * skipped first.                                                          */
 static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r, double ta,
                      double tb, double* t_hit, long long* visits) {
     int P = mip_P(N), K = 0;
@@ -637,6 +639,13 @@ static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r
     long off[32];
     off[0] = 0;
     for (int k = 1; k <= K; ++k) off[k] = off[k - 1] + (long)(P >> (k - 1)) * (P >> (k - 1));
+    double top = (double)mip[off[K]];
+    if (r->ez + ta * r->dz > top) {
+        if (!(r->dz < 0.0)) return 0;
+        double tz = (top - r->ez) / r->dz;
+        if (tz > tb) return 0;
+        if (tz > ta) ta = tz;
+    }
     int ci = clampi((int)floor(r->eu + ta * r->du), 0, N - 2);
     int cj = clampi((int)floor(r->ev + ta * r->dv), 0, N - 2);
     int k = K;
@@ -669,11 +678,7 @@ static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r
         }
         if (ci < 0 || ci >= P || cj < 0 || cj >= P) return 0;
         t = te;
-        while (k < K && ((ci >> (k + 1)) != (oi >> 1) || (cj >> (k + 1)) != (oj >> 1))) {
-            k++;
-            oi >>= 1;
-            oj >>= 1;
-        }
+        if (k < K && ((ci >> (k + 1)) != (oi >> 1) || (cj >> (k + 1)) != (oj >> 1))) k++;
     }
     return 0;
 }

@@ -38,6 +38,8 @@ SMS = 152
 FP32_PER_SM = 128
 MUFU_PER_SM = 16
 FP32_OPS_PER_TERM = 9   # 2 sub, d^2 (mul + fma), scale, -K, max, sum, fma
+RAY_OPS_PER_VISIT = 20  # exit times, z range, node index, compare
+RAY_OPS_PER_TEST = 30   # bilinear coefficients, quadratic, root selection (+ 1 sqrt)
 
 
 def frame_schedule(n_frames: int, steps: int, rank: int, world: int) -> list:
@@ -286,7 +288,10 @@ def run_ours(args, rank, world, local_rank):
         r.set_camera(cams[f])
         r.discretize()
         st = r.stats()
-        work[f] = (sum(st["visible_texels"]), sum(st["candidates"]), sum(st["influencers"]))
+        r.build_maxmip()
+        rs = r.ray_stats()
+        work[f] = (sum(st["visible_texels"]), sum(st["candidates"]), sum(st["influencers"]),
+                   rs["visits"], rs["patch_tests"])
     r.sync()
 
     C, N = cams[0].n_cascades, cams[0].cascade_size
@@ -340,6 +345,8 @@ def run_ours(args, rank, world, local_rank):
     vis = sum(work[f][0] for f in sched)
     cand = sum(work[f][1] for f in sched)
     infl = sum(work[f][2] for f in sched)
+    visits = sum(work[f][3] for f in sched)
+    ptests = sum(work[f][4] for f in sched)
     peaks = load_peaks()
     fclk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     alu_peak = min(MUFU_PER_SM * SMS * fclk, FP32_PER_SM * SMS * fclk / FP32_OPS_PER_TERM) / 1e9
@@ -351,11 +358,16 @@ def run_ours(args, rank, world, local_rank):
         "maxmip": {"ms": statistics.mean(mip_ms), "bound": "hbm",
                    "achieved": mip_bytes / (statistics.mean(mip_ms) * 1e-3) / 1e9,
                    "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"},
-        "raycast": {"ms": statistics.mean(ray_ms)},
+        "raycast": {"ms": statistics.mean(ray_ms), "bound": "alu",
+                    "achieved": (RAY_OPS_PER_VISIT * visits + RAY_OPS_PER_TEST * ptests)
+                    / (sum(ray_ms) * 1e-3) / 1e9,
+                    "peak": FP32_PER_SM * SMS * fclk / 1e9, "unit": "GFLOP/s",
+                    "visits_per_ray": visits / (W * H * len(sched)),
+                    "patch_tests_per_ray": ptests / (W * H * len(sched))},
     }
-    dom = max(("discretize", "maxmip"), key=lambda k: kern[k]["ms"])
+    dom = max(("discretize", "maxmip", "raycast"), key=lambda k: kern[k]["ms"])
     d = kern[dom]
-    kname = {"discretize": "k_discretize_f32", "maxmip": "k_mip_lo"}[dom]
+    kname = {"discretize": "k_discretize_f32", "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["achieved"] / d["peak"], "traffic": profiled_traffic(kname), "kernel": dom,
                 "peak_source": ("derived from unit counts at %d MHz" % int(fclk / 1e6)

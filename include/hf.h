@@ -195,6 +195,13 @@ typedef struct {
 } hf_view_stats_t;
 int hf_view_stats(hf_ctx* ctx, int32_t view_slot, hf_view_stats_t* out, void* stream);
 
+/* Work counts of the ray cast of a view slot (whose max mipmap is built):
+ * max-mipmap nodes tested and ray/patch intersections solved, summed over
+ * all pixels.  Runs a counting pass of the ray caster (no outputs written) on
+ * `stream` and waits for it; meant for measurement. */
+int hf_ray_stats(hf_ctx* ctx, int32_t view_slot, int64_t* visits, int64_t* patch_tests,
+                 void* stream);
+
 /* Allocation-free discretization.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at all, such
  * as a plug-in whose host application owns every device allocation and only

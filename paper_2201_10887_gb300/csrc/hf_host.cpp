@@ -630,10 +630,9 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
     return HF_OK;
 }
 
-int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
-    if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
+namespace {
+
+RayParams ray_params(const ViewSlot* v) {
     const hf_camera& c = v->cam;
     const FitResult& f = v->fit;
     RayParams rp;
@@ -664,14 +663,48 @@ int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* 
         rc.K = mip_levels(P);
         rc.eu = float((v->eye_local[0] - ci.ox) / ci.texel);
         rc.ev = float((v->eye_local[1] - ci.oy) / ci.texel);
+        rc.h = float(ci.texel);
         rc.inv_h = float(1.0 / ci.texel);
         rc.near_d = float(ci.near_depth);
         rc.far_ext = float(ci.far_ext_depth);
+        int64_t off = 0;
+        for (int L = 0; L < kMaxLevels; ++L) {
+            rc.lvl_off[L] = int32_t(off);
+            if (L <= rc.K) off += int64_t(P >> L) * (P >> L);
+        }
     }
+    return rp;
+}
+
+}  // namespace
+
+int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
+    if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
+    RayParams rp = ray_params(v);
     rp.t_out = t_dev;
     rp.hit_out = hit_dev;
     int e = launch_raycast(rp, ctx->d_status(), stream);
     if (e) return cuda_fail(e, "ray-cast kernel launch");
+    return HF_OK;
+}
+
+int hf_ray_stats(hf_ctx* ctx, int32_t slot, int64_t* visits, int64_t* patch_tests, void* stream) {
+    ViewSlot* v = get_view(ctx, slot);
+    if (!visits || !patch_tests) return fail(HF_ERR_ARG, "null argument");
+    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
+    cudaStream_t s = cudaStream_t(stream);
+    DevStatus* st = ctx->d_status();
+    int e = cudaMemsetAsync(st->ray_counters, 0, sizeof(st->ray_counters), s);
+    if (!e) e = launch_raycast_count(ray_params(v), st, stream);
+    if (e) return cuda_fail(e, "ray counting pass launch");
+    unsigned long long c[2];
+    e = cudaMemcpyAsync(c, st->ray_counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "ray counting pass");
+    *visits = int64_t(c[0]);
+    *patch_tests = int64_t(c[1]);
     return HF_OK;
 }
 

@@ -21,7 +21,8 @@ struct DevStatus {
     uint32_t flags;
     uint32_t detail;
     unsigned long long counters[3 * HF_MAX_CASCADES];  // measurement pass (hf_view_stats)
-    uint32_t pad[14];
+    unsigned long long ray_counters[2];                  // measurement pass (hf_ray_stats)
+    uint32_t pad[10];
 };
 static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
 
@@ -119,8 +120,9 @@ struct RayCascade {
     const float* mip;
     int32_t N, P, K;
     float eu, ev;  // eye in this cascade's patch units
-    float inv_h;
+    float h, inv_h;
     float near_d, far_ext;  // projected-depth band
+    int32_t lvl_off[kMaxLevels];  // first float of mip level k
 };
 
 struct RayParams {
@@ -145,6 +147,7 @@ int launch_maxmip(const MipParams& p, void* stream);
 int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
                  DevStatus* status, void* stream);
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
+int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream);
 
 // Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the
 // prep / discretize parameters for output textures `tex` and the scratch

@@ -484,17 +484,26 @@ int launch_maxmip(const MipParams& p, void* stream) {
 // ---------------------------------------------------------------------------
 // Ray casting (Section 5).  One thread per pixel; rays are traced through the
 // cascades nearest first.  Within a cascade the max mipmap is traversed top
-// down: a node whose maximum lies below the ray over the node's extent is
-// skipped whole, otherwise refined; single patches are intersected exactly
-// (first root of the quadratic bilinear(x(t), y(t)) - z(t)).  The current
-// level-0 patch is tracked in integers so rounding can never move the walk
-// backwards; after leaving a node the walk climbs to the largest node it has
-// newly entered.
+// down (Tevs et al.): a node whose maximum lies below the ray over the node's
+// extent is skipped whole, otherwise refined; single patches are intersected
+// exactly (first root of the quadratic bilinear(x(t), y(t)) - z(t)).  The
+// current level-0 patch is tracked in integers, so rounding can never move
+// the walk backwards; after a step the walk climbs one level when it has left
+// its parent node.  The segment above the cascade's global maximum (the top
+// mip entry) is skipped before the walk starts.
+//
+// Per-step arithmetic is kept small: exit times are fma(boundary, 1/d, -e/d)
+// with 1/d = 0, -e/d = +inf for an axis-parallel ray (no branch), integer
+// node boundaries become floats through the exact 2^23 bit trick, level
+// offsets come from shared memory, and all divisions happen once per ray.
+
+__device__ __forceinline__ float exact_float(int x) {  // 0 <= x < 2^23
+    return __int_as_float(x | 0x4B000000) - 8388608.0f;
+}
 
 struct Ray {
     float eu, ev, ez;  // origin in patch units (u, v) and metres (z)
     float du, dv, dz;  // per metre of t
-    float idu, idv;    // 1/du, 1/dv (0 when the component is 0)
 };
 
 __device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, int ci, int cj,
@@ -535,57 +544,89 @@ __device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, 
     return true;
 }
 
-__device__ bool trace_cascade(const RayCascade& c, const Ray& r, float ta, float tb, float& t_hit,
-                              DevStatus* status, uint32_t pixel) {
+// Per-ray quantities that do not depend on the cascade.
+struct RayDir {
+    float dx, dy, dz;
+    float rdx, rdy, rdz;  // reciprocals, 0 for a zero component
+    float ks, rks;        // projected-depth rate and its reciprocal
+    float tmin, tmax;
+};
+
+template <bool COUNT>
+__device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
+                              float ez, float ta, float tb, float& t_hit, DevStatus* status,
+                              uint32_t pixel, unsigned& visits, unsigned& tests) {
     const int N = c.N, P = c.P, K = c.K;
+    const float top = __ldg(c.mip + off[K]);
+    if (!(top > -INFINITY)) return false;  // nothing visible in this cascade
+    Ray r;
+    r.eu = c.eu;
+    r.ev = c.ev;
+    r.ez = ez;
+    r.du = d.dx * c.inv_h;
+    r.dv = d.dy * c.inv_h;
+    r.dz = d.dz;
+    // skip the part of the segment above the cascade's global maximum
+    if (fmaf(ta, r.dz, ez) > top) {
+        if (!(r.dz < 0.f)) return false;
+        const float tz = (top - ez) * d.rdz;
+        if (tz > tb) return false;
+        ta = fmaxf(ta, tz);
+    }
+    const float idu = d.rdx * c.h, idv = d.rdy * c.h;
+    const float ou = d.dx != 0.f ? -r.eu * idu : INFINITY;
+    const float ov = d.dy != 0.f ? -r.ev * idv : INFINITY;
+    const int bu = r.du > 0.f ? 1 : 0, bv = r.dv > 0.f ? 1 : 0;
+    const bool zneg = r.dz < 0.f;
+    const float slack = 2e-6f * fabsf(top);
     int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
     int k = K;
     float t = ta;
-    int64_t off = mip_off(P, k);
     const int budget = 8 * (2 * N + 8) * (K + 2);
     for (int it = 0; it < budget; ++it) {
-        const int ni = ci >> k, nj = cj >> k, size = 1 << k;
-        const float tx = r.du > 0.f ? (float((ni + 1) * size) - r.eu) * r.idu
-                         : (r.du < 0.f ? (float(ni * size) - r.eu) * r.idu : INFINITY);
-        const float ty = r.dv > 0.f ? (float((nj + 1) * size) - r.ev) * r.idv
-                         : (r.dv < 0.f ? (float(nj * size) - r.ev) * r.idv : INFINITY);
+        const int ni = ci >> k, nj = cj >> k;
+        const float tx = fmaf(exact_float((ni + bu) << k), idu, ou);
+        const float ty = fmaf(exact_float((nj + bv) << k), idv, ov);
         const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
-        const float zmin = fminf(fmaf(t, r.dz, r.ez), fmaf(te, r.dz, r.ez));
-        const float mx = __ldg(c.mip + off + size_t(nj) * (P >> k) + ni);
-        if (zmin <= mx + 2e-6f * fabsf(mx)) {
+        const float zmin = fmaf(zneg ? te : t, r.dz, ez);
+        const float mx = __ldg(c.mip + off[k] + nj * (P >> k) + ni);
+        if (COUNT) ++visits;
+        if (zmin <= mx + slack) {
             if (k > 0) {
                 --k;
-                off = mip_off(P, k);
                 continue;
             }
-            if (ci <= N - 2 && cj <= N - 2 && patch_hit(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
+            if (ci <= N - 2 && cj <= N - 2) {
+                if (COUNT) ++tests;
+                if (patch_hit(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
+            }
         }
         if (te >= tb) return false;
-        const int oi = ni, oj = nj;
+        int nci, ncj;
         if (tx <= ty) {
-            ci = r.du > 0.f ? (ni + 1) * size : ni * size - 1;
-            int c2 = int(floorf(fmaf(te, r.dv, r.ev)));
-            c2 = r.dv > 0.f ? max(c2, cj) : (r.dv < 0.f ? min(c2, cj) : cj);
-            cj = min(max(c2, nj * size), nj * size + size - 1);
+            nci = bu ? (ni + 1) << k : (ni << k) - 1;
+            ncj = cj;
+            if (k > 0) {
+                int c2 = __float2int_rd(fmaf(te, r.dv, r.ev));
+                c2 = r.dv > 0.f ? max(c2, cj) : (r.dv < 0.f ? min(c2, cj) : cj);
+                ncj = min(max(c2, nj << k), ((nj + 1) << k) - 1);
+            }
         } else {
-            cj = r.dv > 0.f ? (nj + 1) * size : nj * size - 1;
-            int c2 = int(floorf(fmaf(te, r.du, r.eu)));
-            c2 = r.du > 0.f ? max(c2, ci) : (r.du < 0.f ? min(c2, ci) : ci);
-            ci = min(max(c2, ni * size), ni * size + size - 1);
+            ncj = bv ? (nj + 1) << k : (nj << k) - 1;
+            nci = ci;
+            if (k > 0) {
+                int c2 = __float2int_rd(fmaf(te, r.du, r.eu));
+                c2 = r.du > 0.f ? max(c2, ci) : (r.du < 0.f ? min(c2, ci) : ci);
+                nci = min(max(c2, ni << k), ((ni + 1) << k) - 1);
+            }
         }
-        if (ci < 0 || ci >= P || cj < 0 || cj >= P) return false;
+        if (unsigned(nci) >= unsigned(P) || unsigned(ncj) >= unsigned(P)) return false;
+        const int diff = (nci ^ ci) | (ncj ^ cj);
+        ci = nci;
+        cj = ncj;
         t = te;
-        int kk = k, a = oi, b = oj;
-        while (kk < K && ((ci >> (kk + 1)) != (a >> 1) || (cj >> (kk + 1)) != (b >> 1))) {
-            ++kk;
-            a >>= 1;
-            b >>= 1;
-        }
-        if (kk != k) {
-            k = kk;
-            off = mip_off(P, k);
-        }
+        if (k < K && (diff >> (k + 1)) != 0) ++k;
     }
     report(status, kStatusTimeout, pixel);
     return false;
@@ -593,31 +634,33 @@ __device__ bool trace_cascade(const RayCascade& c, const Ray& r, float ta, float
 
 // t-interval of the ray inside cascade c: projected depth in [near, far_ext],
 // texel region u, v in [0, N-1], camera clip range [tmin, tmax].
-__device__ __forceinline__ bool cascade_interval(const RayCascade& c, const Ray& r, float ks,
-                                                 float tmin, float tmax, float& ta, float& tb) {
-    float lo = tmin, hi = tmax;
-    if (ks > 0.f) {
-        lo = fmaxf(lo, c.near_d / ks);
-        hi = fminf(hi, c.far_ext / ks);
-    } else if (ks < 0.f) {
-        lo = fmaxf(lo, c.far_ext / ks);
-        hi = fminf(hi, c.near_d / ks);
+__device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayDir& d, float& ta,
+                                                 float& tb) {
+    float lo = d.tmin, hi = d.tmax;
+    if (d.ks > 0.f) {
+        lo = fmaxf(lo, c.near_d * d.rks);
+        hi = fminf(hi, c.far_ext * d.rks);
+    } else if (d.ks < 0.f) {
+        lo = fmaxf(lo, c.far_ext * d.rks);
+        hi = fminf(hi, c.near_d * d.rks);
     } else if (!(c.near_d <= 0.f && 0.f <= c.far_ext)) {
         return false;
     }
     const float top = float(c.N - 1);
-    if (r.du != 0.f) {
-        const float t0 = (0.f - r.eu) * r.idu, t1 = (top - r.eu) * r.idu;
+    if (d.dx != 0.f) {
+        const float idu = d.rdx * c.h;
+        const float t0 = (0.f - c.eu) * idu, t1 = (top - c.eu) * idu;
         lo = fmaxf(lo, fminf(t0, t1));
         hi = fminf(hi, fmaxf(t0, t1));
-    } else if (r.eu < 0.f || r.eu > top) {
+    } else if (c.eu < 0.f || c.eu > top) {
         return false;
     }
-    if (r.dv != 0.f) {
-        const float t0 = (0.f - r.ev) * r.idv, t1 = (top - r.ev) * r.idv;
+    if (d.dy != 0.f) {
+        const float idv = d.rdy * c.h;
+        const float t0 = (0.f - c.ev) * idv, t1 = (top - c.ev) * idv;
         lo = fmaxf(lo, fminf(t0, t1));
         hi = fminf(hi, fmaxf(t0, t1));
-    } else if (r.ev < 0.f || r.ev > top) {
+    } else if (c.ev < 0.f || c.ev > top) {
         return false;
     }
     ta = lo;
@@ -625,67 +668,82 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const Ray&
     return lo <= hi;
 }
 
-__device__ __forceinline__ Ray make_ray(const RayCascade& c, float ez, float dx, float dy, float dz) {
-    Ray r;
-    r.eu = c.eu;
-    r.ev = c.ev;
-    r.ez = ez;
-    r.du = dx * c.inv_h;
-    r.dv = dy * c.inv_h;
-    r.dz = dz;
-    r.idu = r.du != 0.f ? 1.f / r.du : 0.f;
-    r.idv = r.dv != 0.f ? 1.f / r.dv : 0.f;
-    return r;
-}
-
+template <bool COUNT>
 __global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
+    __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
+    for (int e = threadIdx.y * 16 + threadIdx.x; e < p.C * kMaxLevels; e += 128)
+        s_off[e / kMaxLevels][e % kMaxLevels] = p.cas[e / kMaxLevels].lvl_off[e % kMaxLevels];
+    __syncthreads();
     const int x = blockIdx.x * 16 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= p.W || y >= p.H) return;
-    const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
-    const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
-    float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
-    float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
-    float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
-    const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    dx *= il;
-    dy *= il;
-    dz *= il;
-    const float fd = fmaf(dx, p.F[0], fmaf(dy, p.F[1], dz * p.F[2]));
-    const float tmin = p.znear / fd, tmax = p.zfar / fd;
-    const float ks = fmaf(dx, p.dir2x, dy * p.dir2y);
-    const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
-    int hit = 0;
-    float t = __int_as_float(0x7fc00000);
-    for (int c = 0; c < p.C && !hit; ++c) {
-        const RayCascade& cc = p.cas[c];
-        const Ray r = make_ray(cc, p.ez, dx, dy, dz);
-        float ta, tb, tc;
-        if (!cascade_interval(cc, r, ks, tmin, tmax, ta, tb)) continue;
-        if (!trace_cascade(cc, r, ta, tb, tc, status, pix)) continue;
-        hit = 1 + c;
-        t = tc;
-        const float s = tc * ks;
-        if (c + 1 < p.C) {
-            const RayCascade& cn = p.cas[c + 1];
-            if (s >= cn.near_d && cc.far_ext > cn.near_d) {
-                const Ray r2 = make_ray(cn, p.ez, dx, dy, dz);
-                float ta2, tb2, t2;
-                if (cascade_interval(cn, r2, ks, tmin, tmax, ta2, tb2) &&
-                    trace_cascade(cn, r2, ta2, tb2, t2, status, pix)) {
-                    const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
-                    t = fmaf(al, t2 - tc, tc);
+    unsigned visits = 0, tests = 0;
+    if (x < p.W && y < p.H) {
+        const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
+        const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
+        float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
+        float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
+        float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
+        const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        RayDir d;
+        d.dx = dx * il;
+        d.dy = dy * il;
+        d.dz = dz * il;
+        d.rdx = d.dx != 0.f ? __frcp_rn(d.dx) : 0.f;
+        d.rdy = d.dy != 0.f ? __frcp_rn(d.dy) : 0.f;
+        d.rdz = d.dz != 0.f ? __frcp_rn(d.dz) : 0.f;
+        const float rfd = __frcp_rn(fmaf(d.dx, p.F[0], fmaf(d.dy, p.F[1], d.dz * p.F[2])));
+        d.tmin = p.znear * rfd;
+        d.tmax = p.zfar * rfd;
+        d.ks = fmaf(d.dx, p.dir2x, d.dy * p.dir2y);
+        d.rks = d.ks != 0.f ? __frcp_rn(d.ks) : 0.f;
+        const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
+        int hit = 0;
+        float t = __int_as_float(0x7fc00000);
+        for (int c = 0; c < p.C && !hit; ++c) {
+            const RayCascade& cc = p.cas[c];
+            float ta, tb, tc;
+            if (!cascade_interval(cc, d, ta, tb)) continue;
+            if (!trace_cascade<COUNT>(cc, s_off[c], d, p.ez, ta, tb, tc, status, pix, visits, tests)) continue;
+            hit = 1 + c;
+            t = tc;
+            const float s = tc * d.ks;
+            if (c + 1 < p.C) {
+                const RayCascade& cn = p.cas[c + 1];
+                if (s >= cn.near_d && cc.far_ext > cn.near_d) {
+                    float ta2, tb2, t2;
+                    if (cascade_interval(cn, d, ta2, tb2) &&
+                        trace_cascade<COUNT>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, status, pix, visits,
+                                             tests)) {
+                        const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
+                        t = fmaf(al, t2 - tc, tc);
+                    }
                 }
             }
         }
+        if (!COUNT) {
+            p.t_out[pix] = t;
+            p.hit_out[pix] = uint8_t(hit);
+        }
     }
-    p.t_out[pix] = t;
-    p.hit_out[pix] = uint8_t(hit);
+    if (COUNT) {
+        visits = __reduce_add_sync(0xffffffffu, visits);
+        tests = __reduce_add_sync(0xffffffffu, tests);
+        if (((threadIdx.y * 16 + threadIdx.x) & 31) == 0) {
+            atomicAdd(&status->ray_counters[0], (unsigned long long)visits);
+            atomicAdd(&status->ray_counters[1], (unsigned long long)tests);
+        }
+    }
 }
 
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
     dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
-    k_raycast<<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
+    k_raycast<false><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
+    return cudaGetLastError();
+}
+
+int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream) {
+    dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
+    k_raycast<true><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ LEAF_DTYPE = np.dtype([("level", "<i4"), ("ix", "<i4"), ("iy", "<i4"), ("value",
 EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_update_values",
             "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
-            "hf_discretize_noalloc"]
+            "hf_discretize_noalloc", "hf_ray_stats"]
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 
@@ -101,6 +101,7 @@ def _load():
         "hf_view_stats": [vp, i32, P(hf_view_stats_t), vp],
         "hf_sync": [vp, vp],
         "hf_discretize_noalloc": [vp, P(hf_camera), P(vp), P(hf_cascade_info), vp],
+        "hf_ray_stats": [vp, i32, P(i64), P(i64), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -213,6 +214,12 @@ def hf_discretize_noalloc(ctx, cam: hf_camera, tex_out, stream=None):
     info = (hf_cascade_info * n)()
     _check(_lib.hf_discretize_noalloc(ctx, ct.byref(cam), ptrs, info, _stream(stream)))
     return list(info)
+
+
+def hf_ray_stats(ctx, slot: int, stream=None) -> dict:
+    v, t = ct.c_int64(), ct.c_int64()
+    _check(_lib.hf_ray_stats(ctx, slot, ct.byref(v), ct.byref(t), _stream(stream)))
+    return {"visits": v.value, "patch_tests": t.value}
 
 
 def hf_sync(ctx, stream=None):

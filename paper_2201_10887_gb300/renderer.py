@@ -94,6 +94,9 @@ class Renderer:
     def stats(self, slot: int = 0, stream=None) -> dict:
         return hf.hf_view_stats(self.ctx, slot, self.views[slot]["C"], stream)
 
+    def ray_stats(self, slot: int = 0, stream=None) -> dict:
+        return hf.hf_ray_stats(self.ctx, slot, stream)
+
     def sync(self, stream=None):
         hf.hf_sync(self.ctx, stream)
 

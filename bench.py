@@ -394,6 +394,9 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 5 * len(sched),
         "wall_s": wall,
     }
+    if not args.no_variants:
+        line["precision_variants"] = time_precision_variants(scene, cams, sched[:min(len(sched), 240)],
+                                                             args.warmup, dev, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
@@ -408,6 +411,38 @@ def run_ours(args, rank, world, local_rank):
     r.close()
 
 
+def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream):
+    """Frame and discretization time of the FP16x2 / BF16x2 discretization on
+    the same frames (same timing method as the main line)."""
+    import torch
+    from paper_2201_10887_gb300 import Renderer
+    out = {}
+    for name, prec in (("fp16", 1), ("bf16", 2)):
+        r = Renderer(scene.tree, scene.sigma, scene.radius, precision=prec, device=dev)
+        for f in sched[:warmup]:
+            r.render(cams[f])
+        r.sync()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in sched]
+        for k, f in enumerate(sched):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            r.set_camera(cams[f])
+            r.discretize()
+            ev[k][1].record(stream)
+            r.build_maxmip()
+            r.raycast()
+            ev[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+        r.sync()
+        out[name] = {"frame_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in ev),
+                     "discretize_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                     "frames": len(sched)}
+        r.close()
+        del r
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,6 +453,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="CPU seconds per reference step")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="CPU seconds of the baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 timing")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

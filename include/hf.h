@@ -81,6 +81,11 @@ typedef struct {
  * - exp(-radius^2 / (2 sigma^2)).  The paper's setting is sigma = 1 with
  * truncation at 3.5 sigma, i.e. radius = 3.5.  precision selects the
  * arithmetic of the distance / exp evaluation (HF_PREC_*); sums are FP32.
+ * HF_PREC_FP16 / HF_PREC_BF16 evaluate distances, scales and exp two
+ * candidates at a time in packed 16-bit arithmetic from compact per-bucket
+ * lists (more device memory); candidate offsets must stay exact in the
+ * 16-bit type, else hf_create_quadtree returns HF_ERR_ARG.
+ * hf_discretize_noalloc always evaluates in FP32.
  * The lists of potentially influencing cells (Section 4) are kept per
  * square "bucket": every leaf at or below level bucket_level is a bucket,
  * coarser leaves are split into their level-bucket_level descendants so a

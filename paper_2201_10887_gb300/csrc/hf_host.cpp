@@ -120,7 +120,9 @@ struct ViewSlot {
 
 // Device layout of the persistent buffer.
 struct PersistentLayout {
-    size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx, total;
+    size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx;
+    size_t pair_offsets, coords, values;  // reduced-precision lists (0 bytes for FP32)
+    size_t total;
 };
 
 }  // namespace
@@ -136,6 +138,8 @@ struct hf_ctx {
     std::vector<float4> recs;      // sorted by (level, iy, ix)
     std::vector<int64_t> perm;     // input position -> sorted index
     std::vector<int64_t> offsets;  // n_buckets + 1
+    std::vector<int64_t> pair_offsets;  // n_buckets + 1 (reduced precision only)
+    int64_t n_pairs = 0;
     std::vector<float> staged;     // values in sorted order for hf_update_values
     char* dev = nullptr;
     size_t dev_bytes = 0;
@@ -153,6 +157,10 @@ struct hf_ctx {
         l.recs = o; o = align256(o + size_t(n_leaves) * 16);
         l.offsets = o; o = align256(o + size_t(n_buckets + 1) * 8);
         l.idx = o; o = align256(o + size_t(n_cand) * 4);
+        const bool compact = rbf.precision != HF_PREC_FP32;
+        l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
+        l.coords = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
+        l.values = o; o = align256(o + (compact ? size_t(n_pairs) * 8 : 0));
         l.total = o;
         return l;
     }
@@ -177,6 +185,15 @@ struct hf_ctx {
         t.nx_fin = buckets.nx[M];
         t.ny_fin = buckets.ny[M];
         return t;
+    }
+    CompactView compact() const {
+        CompactView v;
+        v.pair_offsets = reinterpret_cast<const int64_t*>(dev + lay.pair_offsets);
+        v.coords = reinterpret_cast<uint4*>(dev + lay.coords);
+        v.values = reinterpret_cast<float2*>(dev + lay.values);
+        v.q = float(0.5 * c_fin);
+        v.inv_q = float(2.0 / c_fin);
+        return v;
     }
     ListsView lists() const {
         ListsView v;
@@ -419,6 +436,25 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     }
     ctx->offsets[size_t(ctx->n_buckets)] = run;
     ctx->n_cand = run;
+    if (rbf->precision != HF_PREC_FP32) {
+        // bucket-relative offsets must be exact small integers in the 16-bit type
+        double rmax = 0.0;
+        for (int L = 0; L <= M; ++L)
+            if (lf.base[L + 1] > lf.base[L]) rmax = std::max(rmax, ctx->reach_q[L]);
+        const double span = rmax + double(int64_t(1) << (M - ctx->B + 1)) + 1.0;
+        const double limit = rbf->precision == HF_PREC_FP16 ? 1024.0 : 256.0;
+        if (span > limit)
+            return fail(HF_ERR_ARG, "candidate offsets span %.0f half-cells, more than the %s path holds exactly (%.0f)",
+                        span, rbf->precision == HF_PREC_FP16 ? "FP16" : "BF16", limit);
+        ctx->pair_offsets.resize(size_t(ctx->n_buckets) + 1);
+        int64_t pr = 0;
+        for (int64_t b = 0; b < ctx->n_buckets; ++b) {
+            ctx->pair_offsets[size_t(b)] = pr;
+            pr += (counts[size_t(b)] + 1) / 2;
+        }
+        ctx->pair_offsets[size_t(ctx->n_buckets)] = pr;
+        ctx->n_pairs = pr;
+    }
     ctx->lay = ctx->layout();
     *out = ctx.release();
     g_err.clear();
@@ -452,11 +488,19 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
     if (!e) e = cudaMemcpyAsync(dev + l.bprefix, ctx->buckets.prefix.data(), ctx->buckets.prefix.size() * 4, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(dev + l.recs, ctx->recs.data(), ctx->recs.size() * 16, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(dev + l.offsets, ctx->offsets.data(), ctx->offsets.size() * 8, cudaMemcpyHostToDevice, s);
+    if (!e && ctx->rbf.precision != HF_PREC_FP32)
+        e = cudaMemcpyAsync(dev + l.pair_offsets, ctx->pair_offsets.data(), ctx->pair_offsets.size() * 8,
+                            cudaMemcpyHostToDevice, s);
     if (e) return cuda_fail(e, "upload of the quadtree");
     ctx->dev = dev;
     ctx->dev_bytes = bytes;
     e = launch_fill_lists(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
     if (e) return cuda_fail(e, "influence-list kernel launch");
+    if (ctx->rbf.precision != HF_PREC_FP32) {
+        e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
+                                ctx->rbf.precision, stream);
+        if (e) return cuda_fail(e, "compact-list kernel launch");
+    }
     e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "influence-list build");
     DevStatus st;
@@ -488,6 +532,9 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
     cudaStream_t s = cudaStream_t(stream);
     int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
                               cudaMemcpyHostToDevice, s);
+    if (!e && ctx->rbf.precision != HF_PREC_FP32)  // the compact lists carry copies of the values
+        e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
+                                ctx->rbf.precision, stream);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "value upload");
     return HF_OK;
@@ -602,7 +649,11 @@ int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
     }
     int e = launch_prep(pp, stream);
     if (e) return cuda_fail(e, "visible-row kernel launch");
-    e = launch_discretize(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
+    if (ctx->rbf.precision == HF_PREC_FP32)
+        e = launch_discretize(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
+    else
+        e = launch_discretize_mixed(disc_params(ctx, v), ctx->lookup_tables(true), ctx->compact(), ctx->d_status(),
+                                    stream);
     if (e) return cuda_fail(e, "discretization kernel launch");
     v->stage = 2;
     return HF_OK;

@@ -64,6 +64,20 @@ struct ListsView {
     float4* recs;            // per leaf: centre x, y (domain-local), -log2(e)/(2 sigma^2 c^2), value
 };
 
+// Compact candidate lists of the reduced-precision discretization: per bucket
+// its candidates in pairs.  Pair p holds eight 16-bit values (FP16 or BF16)
+// {x0, x1, y0, y1, k0, k1, 0, 0}: the candidates' centres relative to the
+// bucket's lower corner in units of half a finest cell (small integers, exact
+// in the 16-bit type) and their exponent scales -log2(e) q^2 / (2 sigma^2 c^2)
+// per squared unit; the two values stay FP32.  An odd list is padded with a
+// far-away, zero-weight entry.
+struct CompactView {
+    const int64_t* pair_offsets;  // n_buckets + 1
+    uint4* coords;                // per pair
+    float2* values;               // per pair
+    float q, inv_q;               // half a finest cell (m) and its inverse
+};
+
 // Per-frame cascade data for the prep kernel (visible rows, texel coordinates).
 struct PrepCascade {
     double ox, oy, h, inv_h;
@@ -141,6 +155,10 @@ struct RayParams {
 int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
 int launch_prep(const PrepParams& p, void* stream);
+int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
+                        const CompactView& cv, int precision, void* stream);
+int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
+                            DevStatus* status, void* stream);
 int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
 int launch_maxmip(const MipParams& p, void* stream);

@@ -10,6 +10,9 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "hf_internal.h"
 
 namespace hfi {
@@ -175,6 +178,72 @@ int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsV
     return cudaGetLastError();
 }
 
+// Compact pair lists for the reduced-precision path, one thread per bucket
+// (same (word, bit) mapping as the list fill).  Centres are converted from
+// the FP32 records: x / q is an exact integer for cells of a power-of-two
+// hierarchy, so the bucket-relative offsets are exact.
+template <int PREC>
+__device__ __forceinline__ unsigned short to16(float x) {
+    if (PREC == HF_PREC_FP16) return __half_as_ushort(__float2half_rn(x));
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_fill_compact(const __grid_constant__ FillArgs a,
+                                                      const CompactView cv) {
+    __shared__ Bitmaps bk;
+    if (threadIdx.x == 0) bk = a.buckets;
+    __syncthreads();
+    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t w = g >> 6;
+    if (w >= bk.word_off[bk.max_level + 1]) return;
+    int Lb;
+    int64_t bx, by, id;
+    if (!bucket_of_bit(bk, w, int(g & 63), Lb, bx, by, id)) return;
+    const int M = a.et.leaves.max_level;
+    const float x0q = float(bx << (M - Lb + 1)), y0q = float(by << (M - Lb + 1));
+    const int64_t beg = a.lv.offsets[id], n = a.lv.offsets[id + 1] - beg;
+    const int64_t pb = cv.pair_offsets[id];
+    const float q2 = cv.q * cv.q;
+    for (int64_t m = 0; m < 2 * ((n + 1) / 2); m += 2) {
+        float xs[2], ys[2], ks[2], vs[2];
+        for (int s = 0; s < 2; ++s) {
+            if (m + s < n) {
+                const float4 r = a.lv.recs[a.lv.idx[beg + m + s]];
+                xs[s] = r.x * cv.inv_q - x0q;
+                ys[s] = r.y * cv.inv_q - y0q;
+                ks[s] = r.z * q2;
+                vs[s] = r.w;
+            } else {  // padding: far away, zero weight
+                xs[s] = 1024.f;
+                ys[s] = 1024.f;
+                ks[s] = -1024.f;
+                vs[s] = 0.f;
+            }
+        }
+        uint4 c;
+        c.x = uint32_t(to16<PREC>(xs[0])) | (uint32_t(to16<PREC>(xs[1])) << 16);
+        c.y = uint32_t(to16<PREC>(ys[0])) | (uint32_t(to16<PREC>(ys[1])) << 16);
+        c.z = uint32_t(to16<PREC>(ks[0])) | (uint32_t(to16<PREC>(ks[1])) << 16);
+        c.w = 0u;
+        cv.coords[pb + m / 2] = c;
+        cv.values[pb + m / 2] = make_float2(vs[0], vs[1]);
+    }
+}
+
+int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
+                        const CompactView& cv, int precision, void* stream) {
+    FillArgs a{et, lt.buckets, lv, nullptr};
+    const int64_t words = lt.buckets.word_off[lt.buckets.max_level + 1];
+    if (words == 0) return cudaSuccess;
+    const unsigned blocks = unsigned((words * 64 + 255) / 256);
+    if (precision == HF_PREC_FP16)
+        k_fill_compact<HF_PREC_FP16><<<blocks, 256, 0, cudaStream_t(stream)>>>(a, cv);
+    else
+        k_fill_compact<HF_PREC_BF16><<<blocks, 256, 0, cudaStream_t(stream)>>>(a, cv);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Visible rows (Section 3 mask) and texel coordinates of every cascade, FP64.
 // Row j of cascade c sees columns [spans.x, spans.y]: the texel centres inside
@@ -248,8 +317,11 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
 }
 
 // ---------------------------------------------------------------------------
-// RBF discretization (Eq. 1, Eq. 2): one thread per texel, a warp per 32
-// consecutive texels of a row.  Each visible texel walks its bucket's list:
+// RBF discretization (Eq. 1, Eq. 2): one thread per texel; a warp covers an
+// 8 x 4 texel patch and a CTA a 32 x 8 tile, so that the lanes of a warp
+// share buckets and their list and record loads coincide (the kernel is
+// bound by the L1 data pipe's wavefronts from these per-lane gathers).
+// Each visible texel walks its bucket's list:
 //   w_i = max(2^(k_i d_i^2) - K, 0),  k_i = -log2(e) / (2 sigma^2 c_i^2)
 //   v   = sum w_i v_i / sum w_i.
 // Invisible texels are written as -inf so the texture is fully defined.
@@ -258,8 +330,9 @@ __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ 
                                                         const __grid_constant__ LookupTables lt,
                                                         const ListsView lv, DevStatus* status) {
     const DiscCascade& q = p.cas[blockIdx.z];
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
+    const int j = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
     if (i >= q.N || j >= q.N) return;
     const int2 sp = __ldg(q.spans + j);
     float* out = q.tex + size_t(j) * q.N + i;
@@ -290,11 +363,136 @@ __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ 
     *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
 }
 
+// Reduced-precision discretization: the same texel mapping, bucket lookup and
+// Eq. 2, but distances, scales and the exponential are evaluated two
+// candidates at a time in FP16x2 or BF16x2 arithmetic (ex2.approx on packed
+// pairs); weights are widened to FP32 for the sums.
+__device__ __forceinline__ int64_t lookup_bucket_at(const LookupTables& lt, float px, float py,
+                                                    int& Lb, int& bx, int& by) {
+    const Bitmaps& bk = lt.buckets;
+    int fx = int(floorf(px * lt.inv_c_fin));
+    int fy = int(floorf(py * lt.inv_c_fin));
+    fx = min(max(fx, 0), lt.nx_fin - 1);
+    fy = min(max(fy, 0), lt.ny_fin - 1);
+    const int M = bk.max_level;
+    int64_t found = -1;
+#pragma unroll
+    for (int L = 0; L < kMaxLevels; ++L) {
+        if (L >= lt.bucket_level && L <= M) {
+            const int sh = M - L;
+            const int64_t b = int64_t(fy >> sh) * bk.nx[L] + (fx >> sh);
+            const int64_t w = bk.word_off[L] + (b >> 6);
+            const uint64_t word = __ldg(reinterpret_cast<const unsigned long long*>(bk.bits) + w);
+            if ((word >> (b & 63)) & 1ull) {
+                found = bk.base[L] + __ldg(bk.prefix + w) + __popcll(word & ((1ull << (b & 63)) - 1ull));
+                Lb = L;
+                bx = fx >> sh;
+                by = fy >> sh;
+            }
+        }
+    }
+    return found;
+}
+
+struct F16Ops {
+    typedef __half2 T;
+    static __device__ __forceinline__ T make(float a) { return __float2half2_rn(a); }
+    static __device__ __forceinline__ T bits(uint32_t u) {
+        T r;
+        memcpy(&r, &u, 4);
+        return r;
+    }
+    static __device__ __forceinline__ T exp2(T x) {
+        uint32_t u, r;
+        memcpy(&u, &x, 4);
+        asm("ex2.approx.f16x2 %0, %1;" : "=r"(r) : "r"(u));
+        return bits(r);
+    }
+    static __device__ __forceinline__ float2 widen(T x) { return __half22float2(x); }
+};
+
+struct BF16Ops {
+    typedef __nv_bfloat162 T;
+    static __device__ __forceinline__ T make(float a) { return __float2bfloat162_rn(a); }
+    static __device__ __forceinline__ T bits(uint32_t u) {
+        T r;
+        memcpy(&r, &u, 4);
+        return r;
+    }
+    static __device__ __forceinline__ T exp2(T x) {
+        uint32_t u, r;
+        memcpy(&u, &x, 4);
+        asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(r) : "r"(u));
+        return bits(r);
+    }
+    static __device__ __forceinline__ float2 widen(T x) { return __bfloat1622float2(x); }
+};
+
+template <class Ops>
+__global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant__ DiscParams p,
+                                                          const __grid_constant__ LookupTables lt,
+                                                          const CompactView cv, DevStatus* status) {
+    typedef typename Ops::T T;
+    const DiscCascade& q = p.cas[blockIdx.z];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
+    const int j = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
+    if (i >= q.N || j >= q.N) return;
+    const int2 sp = __ldg(q.spans + j);
+    float* out = q.tex + size_t(j) * q.N + i;
+    if (i < sp.x || i > sp.y) {
+        *out = -INFINITY;
+        return;
+    }
+    const float px = __ldg(q.xs + i), py = __ldg(q.ys + j);
+    int Lb = 0, bx = 0, by = 0;
+    const int64_t bucket = lookup_bucket_at(lt, px, py, Lb, bx, by);
+    if (bucket < 0) {
+        report(status, kStatusData, 0xFFFFFFFFu);
+        *out = __int_as_float(0x7fc00000);
+        return;
+    }
+    const int sh = lt.buckets.max_level - Lb + 1;
+    const T PX = Ops::make(fmaf(px, cv.inv_q, -float(bx << sh)));
+    const T PY = Ops::make(fmaf(py, cv.inv_q, -float(by << sh)));
+    const T NK = Ops::make(-p.K);
+    const T ONE = Ops::make(1.f);
+    const int64_t pb = __ldg(cv.pair_offsets + bucket);
+    const int np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
+    const uint4* cc = cv.coords + pb;
+    const float2* vv = cv.values + pb;
+    float sw = 0.f, swv = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < np; ++k) {
+        const uint4 c = __ldg(cc + k);
+        const float2 v = __ldg(vv + k);
+        const T dx = __hsub2(Ops::bits(c.x), PX);
+        const T dy = __hsub2(Ops::bits(c.y), PY);
+        const T d2 = __hfma2(dx, dx, __hmul2(dy, dy));
+        const T e = Ops::exp2(__hmul2(Ops::bits(c.z), d2));
+        const float2 w = Ops::widen(__hfma2_relu(e, ONE, NK));
+        sw += w.x + w.y;
+        swv = fmaf(w.x, v.x, fmaf(w.y, v.y, swv));
+    }
+    *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
+                            DevStatus* status, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
+    if (p.precision == HF_PREC_FP16)
+        k_discretize_mixed<F16Ops><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, cv, status);
+    else
+        k_discretize_mixed<BF16Ops><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, cv, status);
+    return cudaGetLastError();
+}
+
 int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
-    k_discretize_f32<<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    k_discretize_f32<<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
     return cudaGetLastError();
 }
 

@@ -211,3 +211,20 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
                 checked += 1
     assert checked > 300
     hfmod.hf_destroy(ctx)
+
+
+def test_reduced_precision_offset_limits(hfmod, tiny):
+    """FP16/BF16 lists need candidate offsets that are exact small integers:
+    a grid whose coarse cells reach too far is rejected, FP32 accepts it."""
+    t = tiny.tree
+    lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    for prec in (0, 1, 2):
+        ctx = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, prec, -1))
+        hfmod.hf_destroy(ctx)
+    # radius 40 cells: reach 40 x 10 m = 320 half-cells of 1.25 m > 256 (BF16), < 1024 (FP16)
+    ctx = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(1.5, 40.0, 1, -1))
+    hfmod.hf_destroy(ctx)
+    with pytest.raises(hfmod.HFError) as e:
+        hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(1.5, 40.0, 2, -1))
+    assert e.value.code == hfmod.HF_ERR_ARG and "BF16" in str(e.value)

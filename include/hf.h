@@ -230,6 +230,47 @@ int hf_ray_stats(hf_ctx* ctx, int32_t view_slot, int64_t* visits, int64_t* patch
 int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_out,
                           hf_cascade_info* info_out, void* stream);
 
+/* Batched frames (the paper times one view; serving many views and tiles at
+ * once is this library's extension).  Each item is one view slot of one
+ * context whose camera is set with hf_set_camera; t_dev / hit_dev receive its
+ * ray cast as in hf_raycast.  hf_batch_prepare writes descriptors of all items
+ * into a caller-provided host buffer (pinned, so that hf_batch_launch can be
+ * captured in a CUDA graph); hf_batch_launch copies them to a caller-provided
+ * device buffer and runs the whole batch: one persistent launch drains a work
+ * queue of visible rows, discretization tiles and max-mip blocks of every
+ * cascade of every item (bounded waits on per-cascade completion counters),
+ * then the ray tiles of every item (in a second launch, or in the same one
+ * with HF_BATCH_RAYS_INSIDE).  The launch sizes depend only on the items'
+ * cascade counts, texture and image sizes, so a captured graph stays valid
+ * while those are unchanged and hf_batch_prepare refreshes the pinned
+ * descriptors before each replay.  Results equal those of the per-view calls.
+ * flags select work-unit shapes: HF_BATCH_RAY_TILE_32x8 / _8x32 (default
+ * 16x16 pixels per ray unit), HF_BATCH_WARP_16x2 (default 8x4 texels per
+ * warp), HF_BATCH_RAYS_INSIDE.  Errors surface through hf_sync of the items'
+ * contexts. */
+typedef struct {
+    hf_ctx* ctx;
+    int32_t view_slot;
+    int32_t reserved;
+    float* t_dev;
+    uint8_t* hit_dev;
+} hf_batch_item;
+
+enum {
+    HF_BATCH_RAYS_INSIDE = 1,
+    HF_BATCH_RAY_TILE_32x8 = 2,
+    HF_BATCH_RAY_TILE_8x32 = 4,
+    HF_BATCH_WARP_16x2 = 8
+};
+
+int hf_batch_query_bytes(const hf_batch_item* items, int32_t n, int32_t flags, size_t* device_bytes,
+                         size_t* host_bytes);
+int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf,
+                     size_t host_bytes);
+int hf_batch_launch(const void* host_buf, void* dev_buf, size_t dev_bytes, void* stream);
+int hf_frame_batch(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf,
+                   size_t host_bytes, void* dev_buf, size_t dev_bytes, void* stream);
+
 /* Waits for `stream` and reports errors recorded on the device since the
  * last hf_sync (HF_ERR_TIMEOUT, HF_ERR_DATA) or by the CUDA runtime. */
 int hf_sync(hf_ctx* ctx, void* stream);

@@ -8,5 +8,6 @@ owns the device buffers of one heightfield.  Importing the package loads
 
 from . import hf
 from .renderer import Renderer, camera_struct
+from .batch import Batch, autotune
 
-__all__ = ["hf", "Renderer", "camera_struct"]
+__all__ = ["hf", "Renderer", "camera_struct", "Batch", "autotune"]

@@ -1,0 +1,127 @@
+"""Batched frames: many views of many heightfields in one persistent launch.
+
+``Batch`` holds the descriptor buffers of a fixed set of (renderer, view
+slot) pairs: a pinned host buffer that ``hf_batch_prepare`` fills from the
+views' current cameras, and a device buffer that ``hf_batch_launch`` copies
+it into before running the batch.  Because launch sizes depend only on the
+items' cascade counts and texture / image sizes, the launch can be captured
+once in a CUDA graph and replayed each frame after ``prepare``.
+
+``autotune`` times the work-unit shapes (ray tile, discretization warp patch,
+ray tiles inside or after the persistent launch) on the actual batch and
+keeps the fastest.
+"""
+
+from __future__ import annotations
+
+import itertools
+
+from . import hf
+
+SHAPE_FLAGS = {
+    "ray16x16": 0, "ray32x8": hf.HF_BATCH_RAY_TILE_32x8, "ray8x32": hf.HF_BATCH_RAY_TILE_8x32,
+}
+
+
+def flag_candidates():
+    out = []
+    for ray, warp, inside in itertools.product(SHAPE_FLAGS.values(), (0, hf.HF_BATCH_WARP_16x2),
+                                               (0, hf.HF_BATCH_RAYS_INSIDE)):
+        out.append(ray | warp | inside)
+    return out
+
+
+def describe(flags: int) -> str:
+    ray = {0: "16x16", hf.HF_BATCH_RAY_TILE_32x8: "32x8", hf.HF_BATCH_RAY_TILE_8x32: "8x32"}[
+        flags & (hf.HF_BATCH_RAY_TILE_32x8 | hf.HF_BATCH_RAY_TILE_8x32)]
+    warp = "16x2" if flags & hf.HF_BATCH_WARP_16x2 else "8x4"
+    inside = "rays in persistent launch" if flags & hf.HF_BATCH_RAYS_INSIDE else "rays in second launch"
+    return f"ray tile {ray}, texel warp {warp}, {inside}"
+
+
+class Batch:
+    """A fixed set of views rendered together.  ``views`` is a list of
+    (Renderer, view_slot); their cameras are set with Renderer.set_camera."""
+
+    def __init__(self, views, flags: int = 0):
+        import torch
+        self.torch = torch
+        self.views = list(views)
+        self.flags = flags
+        self.items = (hf.hf_batch_item * len(self.views))()
+        self._bind_items()
+        dev_bytes, host_bytes = hf.hf_batch_query_bytes(self.items, flags)
+        device = self.views[0][0].device
+        self.dev_buf = torch.empty(dev_bytes, dtype=torch.uint8, device=device)
+        self.host_buf = torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True)
+        self.graph = None
+
+    def _bind_items(self):
+        for k, (r, slot) in enumerate(self.views):
+            v = r.views[slot]
+            self.items[k] = hf.hf_batch_item(r.ctx.value, slot, 0, v["t"].data_ptr(), v["hit"].data_ptr())
+
+    def prepare(self, flags: int | None = None):
+        if flags is not None and flags != self.flags:
+            self.flags = flags
+            self.graph = None
+        hf.hf_batch_prepare(self.items, self.flags, self.host_buf)
+
+    def launch(self, stream=None):
+        hf.hf_batch_launch(self.host_buf, self.dev_buf, stream)
+
+    def run(self, stream=None):
+        """Prepare from the current cameras and run (graph replay if captured)."""
+        self.prepare()
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.launch(stream)
+
+    def capture(self):
+        """Capture the launch (descriptor copy, counter reset, kernels) in a
+        CUDA graph; later ``run`` calls replay it."""
+        torch = self.torch
+        self.prepare()
+        self.launch()  # warm-up outside capture (first-use initialisation)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                hf.hf_batch_launch(self.host_buf, self.dev_buf, s)
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def outputs(self, k: int):
+        r, slot = self.views[k]
+        v = r.views[slot]
+        return v["t"].view(v["shape"]), v["hit"].view(v["shape"])
+
+
+def autotune(batch: Batch, candidates=None, reps: int = 3):
+    """Time each flag combination (prepare + launch, CUDA events, best of
+    `reps`) and leave the batch set to the fastest.  Returns (best flags,
+    {flags: ms})."""
+    torch = batch.torch
+    results = {}
+    for flags in candidates or flag_candidates():
+        batch.prepare(flags)
+        batch.launch()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            batch.prepare(flags)
+            a.record()
+            batch.launch()
+            b.record()
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        results[flags] = best
+    best_flags = min(results, key=results.get)
+    batch.prepare(best_flags)
+    return best_flags, results

@@ -610,6 +610,35 @@ DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
 
 }  // namespace
 
+namespace {
+
+// Grown-polygon edge constraints and buffers of cascade k for the row kernel.
+void fill_prep_cascade(const ViewSlot* v, int k, PrepCascade& q) {
+    const hf_cascade_info& ci = v->fit.cas[k];
+    q.ox = ci.ox;
+    q.oy = ci.oy;
+    q.h = ci.texel;
+    q.inv_h = 1.0 / ci.texel;
+    q.N = v->cam.cascade_size;
+    q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
+    const double delta = std::sqrt(2.0) * ci.texel;  // one texel diagonal
+    for (int e = 0; e < q.n_edges; ++e) {
+        const double ax = ci.poly[e][0], ay = ci.poly[e][1];
+        const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
+        const double len = std::hypot(bx - ax, by - ay);
+        const double nx = (by - ay) / len, ny = -(bx - ax) / len;
+        q.ny[e] = ny;
+        q.c[e] = nx * ax + ny * ay + delta;
+        q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
+        q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
+    }
+    q.spans = v->spans[k];
+    q.xs = v->xs[k];
+    q.ys = v->ys[k];
+}
+
+}  // namespace
+
 int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
@@ -617,36 +646,13 @@ int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
     const int C = v->cam.n_cascades, N = v->cam.cascade_size;
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
+    (void)N;
     pp.C = C;
     pp.max_N = N;
     pp.dom_w = ctx->width;
     pp.dom_h = ctx->height;
     pp.eps_frac = 1e-6;
-    for (int k = 0; k < C; ++k) {
-        const hf_cascade_info& ci = v->fit.cas[k];
-        PrepCascade& q = pp.cas[k];
-        q.ox = ci.ox;
-        q.oy = ci.oy;
-        q.h = ci.texel;
-        q.inv_h = 1.0 / ci.texel;
-        q.N = N;
-        q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
-        // polygon grown by one texel diagonal: n.p <= n.a + sqrt(2) h per edge
-        const double delta = std::sqrt(2.0) * ci.texel;
-        for (int e = 0; e < q.n_edges; ++e) {
-            const double ax = ci.poly[e][0], ay = ci.poly[e][1];
-            const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
-            const double len = std::hypot(bx - ax, by - ay);
-            const double nx = (by - ay) / len, ny = -(bx - ax) / len;
-            q.ny[e] = ny;
-            q.c[e] = nx * ax + ny * ay + delta;
-            q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
-            q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
-        }
-        q.spans = v->spans[k];
-        q.xs = v->xs[k];
-        q.ys = v->ys[k];
-    }
+    for (int k = 0; k < C; ++k) fill_prep_cascade(v, k, pp.cas[k]);
     int e = launch_prep(pp, stream);
     if (e) return cuda_fail(e, "visible-row kernel launch");
     if (ctx->rbf.precision == HF_PREC_FP32)
@@ -779,6 +785,167 @@ int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream)
         out->influencers[k] = int64_t(c[2 * HF_MAX_CASCADES + k]);
     }
     return HF_OK;
+}
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct BatchPlan {
+    int n_cascades = 0;
+    size_t items_off = 0, cascades_off = 0, counters_off = 0, total = 0;
+};
+
+int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
+    if (!items || n < 1) return fail(HF_ERR_ARG, "empty batch");
+    int nc = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const hf_batch_item& it = items[i];
+        ViewSlot* v = get_view(it.ctx, it.view_slot);
+        if (!v || v->stage < 1) return fail(HF_ERR_STATE, "batch item %d: view slot %d has no camera", i, it.view_slot);
+        if (!it.ctx->dev) return fail(HF_ERR_STATE, "batch item %d: persistent buffer not bound", i);
+        if (!it.t_dev || !it.hit_dev) return fail(HF_ERR_ARG, "batch item %d: null output buffer", i);
+        nc += v->cam.n_cascades;
+    }
+    plan->n_cascades = nc;
+    plan->items_off = align_up(sizeof(BatchHeader), 256);
+    plan->cascades_off = align_up(plan->items_off + size_t(n) * sizeof(BatchItem), 256);
+    plan->counters_off = align_up(plan->cascades_off + size_t(nc) * sizeof(BatchCascade), 256);
+    plan->total = align_up(plan->counters_off + (size_t(nc) * 4 + 4) * 4, 256);
+    return HF_OK;
+}
+
+int g_persistent_blocks[64] = {};
+
+}  // namespace
+
+int hf_batch_query_bytes(const hf_batch_item* items, int32_t n, int32_t flags, size_t* device_bytes,
+                         size_t* host_bytes) {
+    (void)flags;
+    BatchPlan plan;
+    int rc = plan_batch(items, n, &plan);
+    if (rc) return rc;
+    if (device_bytes) *device_bytes = plan.total;
+    if (host_bytes) *host_bytes = plan.counters_off;
+    return HF_OK;
+}
+
+int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes) {
+    BatchPlan plan;
+    int rc = plan_batch(items, n, &plan);
+    if (rc) return rc;
+    if (!host_buf) return fail(HF_ERR_ARG, "null host buffer");
+    if (host_bytes < plan.counters_off)
+        return fail(HF_ERR_NOMEM, "batch host buffer has %zu bytes, %zu needed", host_bytes, plan.counters_off);
+    if (flags & ~int32_t(kBatchRaysInside | kBatchRayTileMask | kBatchWarp16x2)) return fail(HF_ERR_ARG, "unknown batch flags");
+    if (((flags & kBatchRayTileMask) >> 1) == 3) return fail(HF_ERR_ARG, "choose one ray tile shape");
+    int dev = 0;
+    int e = cudaGetDevice(&dev);
+    if (e) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HF_ERR_ARG, "device index %d", dev);
+    if (!g_persistent_blocks[dev]) {
+        e = batch_persistent_blocks(&g_persistent_blocks[dev]);
+        if (e) return cuda_fail(e, "occupancy query");
+    }
+    char* hb = static_cast<char*>(host_buf);
+    std::memset(hb, 0, plan.counters_off);
+    BatchHeader& h = *reinterpret_cast<BatchHeader*>(hb);
+    BatchItem* bi = reinterpret_cast<BatchItem*>(hb + plan.items_off);
+    BatchCascade* bc = reinterpret_cast<BatchCascade*>(hb + plan.cascades_off);
+    h.n_items = n;
+    h.n_cascades = plan.n_cascades;
+    h.flags = flags;
+    const int shape = (flags & kBatchRayTileMask) >> 1;
+    h.ray_tile_w = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
+    h.ray_tile_h = 256 / h.ray_tile_w;
+    h.persistent_blocks = g_persistent_blocks[dev];
+    h.items_off = int64_t(plan.items_off);
+    h.cascades_off = int64_t(plan.cascades_off);
+    h.counters_off = int64_t(plan.counters_off);
+    h.desc_bytes = int64_t(plan.counters_off);
+    h.total_bytes = int64_t(plan.total);
+    int kc = 0, units[kPhases] = {0, 0, 0, 0, 0};
+    for (int32_t i = 0; i < n; ++i) {
+        hf_ctx* ctx = items[i].ctx;
+        ViewSlot* v = get_view(ctx, items[i].view_slot);
+        const int C = v->cam.n_cascades, N = v->cam.cascade_size, P = mip_pow2(N);
+        BatchItem& I = bi[i];
+        I.ray = ray_params(v);
+        I.ray.t_out = items[i].t_dev;
+        I.ray.hit_out = items[i].hit_dev;
+        I.lt = ctx->lookup_tables(true);
+        I.lv = ctx->lists();
+        if (ctx->rbf.precision != HF_PREC_FP32) I.cv = ctx->compact();
+        I.status = ctx->d_status();
+        I.dom_w = ctx->width;
+        I.dom_h = ctx->height;
+        I.eps_frac = 1e-6;
+        const DiscParams dp = disc_params(ctx, v);
+        I.K = dp.K;
+        I.precision = ctx->rbf.precision;
+        I.first_cascade = kc;
+        I.n_cascades = C;
+        I.ray_tiles_x = (v->cam.width + h.ray_tile_w - 1) / h.ray_tile_w;
+        I.ray_units = I.ray_tiles_x * ((v->cam.height + h.ray_tile_h - 1) / h.ray_tile_h);
+        I.ray_unit_base = units[kPhaseRays];
+        units[kPhaseRays] += I.ray_units;
+        for (int k = 0; k < C; ++k, ++kc) {
+            BatchCascade& B = bc[kc];
+            fill_prep_cascade(v, k, B.prep);
+            B.disc = dp.cas[k];
+            B.mip.tex = v->tex[k];
+            B.mip.mip = v->mip[k];
+            B.mip.N = N;
+            B.mip.P = P;
+            B.mip.K = mip_levels(P);
+            B.item = i;
+            B.tiles_x = (N + 31) / 32;
+            B.mip_blocks_x = (P + 63) / 64;
+            B.n_units[kPhaseRows] = (N + 255) / 256;
+            B.n_units[kPhaseTexels] = B.tiles_x * ((N + 7) / 8);
+            B.n_units[kPhaseMipLo] = B.mip_blocks_x * B.mip_blocks_x;
+            B.n_units[kPhaseMipHi] = 1;
+            for (int ph = 0; ph < 4; ++ph) {
+                B.unit_base[ph] = units[ph];
+                units[ph] += B.n_units[ph];
+            }
+        }
+        v->stage = 3;
+    }
+    // global unit numbering: phase after phase
+    int base = 0;
+    for (int ph = 0; ph < kPhases; ++ph) {
+        h.phase_base[ph] = base;
+        base += units[ph];
+    }
+    h.phase_base[kPhases] = base;
+    for (int k = 0; k < plan.n_cascades; ++k)
+        for (int ph = 0; ph < 4; ++ph) bc[k].unit_base[ph] += h.phase_base[ph];
+    return HF_OK;
+}
+
+int hf_batch_launch(const void* host_buf, void* dev_buf, size_t dev_bytes, void* stream) {
+    if (!host_buf || !dev_buf) return fail(HF_ERR_ARG, "null buffer");
+    if (reinterpret_cast<uintptr_t>(dev_buf) & 255) return fail(HF_ERR_ARG, "device buffer must be 256-byte aligned");
+    const BatchHeader& h = *static_cast<const BatchHeader*>(host_buf);
+    if (h.n_items < 1 || h.total_bytes <= 0) return fail(HF_ERR_ARG, "host buffer holds no prepared batch");
+    if (dev_bytes < size_t(h.total_bytes))
+        return fail(HF_ERR_NOMEM, "batch device buffer has %zu bytes, %lld needed", dev_bytes, (long long)h.total_bytes);
+    cudaStream_t s = cudaStream_t(stream);
+    char* db = static_cast<char*>(dev_buf);
+    int e = cudaMemcpyAsync(db, host_buf, size_t(h.desc_bytes), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(db + h.counters_off, 0, size_t(h.total_bytes - h.counters_off), s);
+    if (e) return cuda_fail(e, "batch descriptor upload");
+    e = launch_batch(h, dev_buf, stream);
+    if (e) return cuda_fail(e, "batch kernel launch");
+    return HF_OK;
+}
+
+int hf_frame_batch(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes,
+                   void* dev_buf, size_t dev_bytes, void* stream) {
+    int rc = hf_batch_prepare(items, n, flags, host_buf, host_bytes);
+    if (rc) return rc;
+    return hf_batch_launch(host_buf, dev_buf, dev_bytes, stream);
 }
 
 int hf_get_cascade(const hf_ctx* ctx, int32_t slot, int32_t c, hf_cascade_info* out) {

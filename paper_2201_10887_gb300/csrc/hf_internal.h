@@ -151,6 +151,51 @@ struct RayParams {
     uint8_t* hit_out;
 };
 
+// Batched frames (hf_frame_batch).  The host writes a header, one BatchItem
+// per (context, view) and one BatchCascade per cascade into a pinned buffer;
+// the same bytes are copied to the device and drive one persistent launch
+// that drains an ordered work queue (visible rows -> discretization tiles ->
+// level-0..6 mip blocks -> mip tops), then a batched ray-cast launch.
+enum { kPhaseRows = 0, kPhaseTexels = 1, kPhaseMipLo = 2, kPhaseMipHi = 3, kPhaseRays = 4, kPhases = 5 };
+enum : int32_t {
+    kBatchRaysInside = 1,   // ray tiles drained by the persistent launch too
+    kBatchRayTileMask = 6,  // (flags >> 1) & 3: 0 = 16x16, 1 = 32x8, 2 = 8x32 pixels per ray unit
+    kBatchWarp16x2 = 8      // discretization warps cover 16 x 2 texels (else 8 x 4)
+};
+
+struct BatchCascade {
+    PrepCascade prep;
+    DiscCascade disc;
+    MipCascade mip;
+    int32_t item;
+    int32_t tiles_x;        // discretization tiles (32 x 8 texels) per row
+    int32_t mip_blocks_x;   // 64 x 64 level-0 blocks per row
+    int32_t unit_base[4];   // first unit of this cascade in phases 0..3
+    int32_t n_units[4];
+};
+
+struct BatchItem {
+    RayParams ray;
+    LookupTables lt;
+    ListsView lv;
+    CompactView cv;
+    DevStatus* status;
+    double dom_w, dom_h, eps_frac;
+    float K;
+    int32_t precision;
+    int32_t first_cascade, n_cascades;
+    int32_t ray_unit_base, ray_tiles_x, ray_units;
+};
+
+struct BatchHeader {
+    int32_t n_items, n_cascades;
+    int32_t phase_base[kPhases + 1];  // unit ranges per phase; phase_base[kPhases] = all units
+    int32_t ray_tile_w, ray_tile_h;
+    int32_t flags;
+    int32_t persistent_blocks;
+    int64_t items_off, cascades_off, counters_off, desc_bytes, total_bytes;
+};
+
 // Kernel launchers (hf_kernels.cu); they return a cudaError_t value.
 int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
@@ -166,6 +211,8 @@ int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& l
                  DevStatus* status, void* stream);
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
 int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream);
+int batch_persistent_blocks(int* blocks);
+int launch_batch(const BatchHeader& h, void* dev_buf, void* stream);
 
 // Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the
 // prep / discretize parameters for output textures `tex` and the scratch

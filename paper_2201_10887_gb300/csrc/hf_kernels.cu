@@ -32,6 +32,15 @@ __device__ __forceinline__ void report(DevStatus* st, uint32_t flag, uint32_t de
     if (atomicOr(&st->flags, flag) == 0) st->detail = detail;
 }
 
+// Loads of data written earlier in the same launch (batched path) go through
+// L2 (ld.global.cg), which is coherent across SMs; everything else may use the
+// read-only path.
+template <bool COH, class T>
+__device__ __forceinline__ T ldc(const T* p) {
+    if (COH) return __ldcg(p);
+    return __ldg(p);
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -249,19 +258,16 @@ int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const List
 // Row j of cascade c sees columns [spans.x, spans.y]: the texel centres inside
 // the cascade polygon grown by one texel diagonal and inside the domain.
 
-__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams p) {
-    const int c = blockIdx.y;
-    const PrepCascade& q = p.cas[c];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= q.N) return;
+__device__ __forceinline__ void prep_row(const PrepCascade& q, double dom_w, double dom_h,
+                                         double eps_frac, int t) {
     const double h = q.h;
     q.xs[t] = float(q.ox + double(t) * h);
     const double y = q.oy + double(t) * h;
     q.ys[t] = float(y);
-    const double eps = p.eps_frac * h;
+    const double eps = eps_frac * h;
     int lo = 0, hi = -1;
-    if (q.n_edges >= 3 && y >= -eps && y <= p.dom_h + eps) {
-        double xlo = -eps, xhi = p.dom_w + eps;
+    if (q.n_edges >= 3 && y >= -eps && y <= dom_h + eps) {
+        double xlo = -eps, xhi = dom_w + eps;
         bool empty = false;
         for (int e = 0; e < q.n_edges; ++e) {
             const double rhs = q.c[e] - q.ny[e] * y;
@@ -280,6 +286,12 @@ __global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams
         }
     }
     q.spans[t] = make_int2(lo, hi);
+}
+
+__global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams p) {
+    const PrepCascade& q = p.cas[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < q.N) prep_row(q, p.dom_w, p.dom_h, p.eps_frac, t);
 }
 
 int launch_prep(const PrepParams& p, void* stream) {
@@ -326,21 +338,17 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
 //   v   = sum w_i v_i / sum w_i.
 // Invisible texels are written as -inf so the texture is fully defined.
 
-__global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
-                                                        const __grid_constant__ LookupTables lt,
-                                                        const ListsView lv, DevStatus* status) {
-    const DiscCascade& q = p.cas[blockIdx.z];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
-    const int j = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
+template <bool COH>
+__device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, const LookupTables& lt,
+                                                 const ListsView& lv, DevStatus* status, int i, int j) {
     if (i >= q.N || j >= q.N) return;
-    const int2 sp = __ldg(q.spans + j);
+    const int2 sp = ldc<COH>(q.spans + j);
     float* out = q.tex + size_t(j) * q.N + i;
     if (i < sp.x || i > sp.y) {
         *out = -INFINITY;
         return;
     }
-    const float px = __ldg(q.xs + i), py = __ldg(q.ys + j);
+    const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
     const int64_t bucket = lookup_bucket(lt, px, py);
     if (bucket < 0) {
         report(status, kStatusData, 0xFFFFFFFFu);
@@ -350,7 +358,6 @@ __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ 
     const int64_t beg = __ldg(lv.offsets + bucket);
     const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
     const int32_t* ids = lv.idx + beg;
-    const float K = p.K;
     float sw = 0.f, swv = 0.f;
 #pragma unroll 4
     for (int k = 0; k < n; ++k) {
@@ -361,6 +368,21 @@ __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ 
         swv = fmaf(w, r.w, swv);
     }
     *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+// texel of thread t (0..255) in a 32 x 8 tile: warp = 8 x 4 patch
+__device__ __forceinline__ void tile_texel(int t, int& di, int& dj) {
+    const int lane = t & 31, warp = t >> 5;
+    di = (warp & 3) * 8 + (lane & 7);
+    dj = (warp >> 2) * 4 + (lane >> 3);
+}
+
+__global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
+                                                        const __grid_constant__ LookupTables lt,
+                                                        const ListsView lv, DevStatus* status) {
+    int di, dj;
+    tile_texel(threadIdx.x, di, dj);
+    discretize_texel<false>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di, blockIdx.y * 8 + dj);
 }
 
 // Reduced-precision discretization: the same texel mapping, bucket lookup and
@@ -428,23 +450,18 @@ struct BF16Ops {
     static __device__ __forceinline__ float2 widen(T x) { return __bfloat1622float2(x); }
 };
 
-template <class Ops>
-__global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant__ DiscParams p,
-                                                          const __grid_constant__ LookupTables lt,
-                                                          const CompactView cv, DevStatus* status) {
+template <class Ops, bool COH>
+__device__ __forceinline__ void discretize_texel_mixed(const DiscCascade& q, float K, const LookupTables& lt,
+                                                       const CompactView& cv, DevStatus* status, int i, int j) {
     typedef typename Ops::T T;
-    const DiscCascade& q = p.cas[blockIdx.z];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
-    const int j = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
     if (i >= q.N || j >= q.N) return;
-    const int2 sp = __ldg(q.spans + j);
+    const int2 sp = ldc<COH>(q.spans + j);
     float* out = q.tex + size_t(j) * q.N + i;
     if (i < sp.x || i > sp.y) {
         *out = -INFINITY;
         return;
     }
-    const float px = __ldg(q.xs + i), py = __ldg(q.ys + j);
+    const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
     int Lb = 0, bx = 0, by = 0;
     const int64_t bucket = lookup_bucket_at(lt, px, py, Lb, bx, by);
     if (bucket < 0) {
@@ -455,7 +472,7 @@ __global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant_
     const int sh = lt.buckets.max_level - Lb + 1;
     const T PX = Ops::make(fmaf(px, cv.inv_q, -float(bx << sh)));
     const T PY = Ops::make(fmaf(py, cv.inv_q, -float(by << sh)));
-    const T NK = Ops::make(-p.K);
+    const T NK = Ops::make(-K);
     const T ONE = Ops::make(1.f);
     const int64_t pb = __ldg(cv.pair_offsets + bucket);
     const int np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
@@ -475,6 +492,16 @@ __global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant_
         swv = fmaf(w.x, v.x, fmaf(w.y, v.y, swv));
     }
     *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+template <class Ops>
+__global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant__ DiscParams p,
+                                                          const __grid_constant__ LookupTables lt,
+                                                          const CompactView cv, DevStatus* status) {
+    int di, dj;
+    tile_texel(threadIdx.x, di, dj);
+    discretize_texel_mixed<Ops, false>(p.cas[blockIdx.z], p.K, lt, cv, status, blockIdx.x * 32 + di,
+                                       blockIdx.y * 8 + dj);
 }
 
 int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
@@ -557,19 +584,20 @@ __device__ __forceinline__ int64_t mip_off(int P, int k) {
     return (a - b) * 4 / 3;
 }
 
-__global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParams p) {
-    const MipCascade& c = p.cas[blockIdx.z];
+// Levels 0..6 of the 64 x 64 level-0 block (bx, by); 256 threads.
+template <bool COH>
+__device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int byi, float (*sm)[17]) {
     const int P = c.P, N = c.N, K = c.K;
-    if (int(blockIdx.x) * 64 >= P || int(blockIdx.y) * 64 >= P) return;
+    if (bxi * 64 >= P || byi * 64 >= P) return;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int pi0 = blockIdx.x * 64 + tx * 4, pj0 = blockIdx.y * 64 + ty * 4;
+    const int pi0 = bxi * 64 + tx * 4, pj0 = byi * 64 + ty * 4;
     float t[5][5];
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
             const int ii = pi0 + s, jj = pj0 + r;
-            t[r][s] = (ii < N && jj < N) ? __ldg(c.tex + size_t(jj) * N + ii) : -INFINITY;
+            t[r][s] = (ii < N && jj < N) ? ldc<COH>(c.tex + size_t(jj) * N + ii) : -INFINITY;
         }
     float m0[4][4];
 #pragma unroll
@@ -613,7 +641,6 @@ __global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParam
         const int P2 = P >> 2, pi2 = pi0 >> 2, pj2 = pj0 >> 2;
         if (pi2 < P2 && pj2 < P2) c.mip[mip_off(P, 2) + size_t(pj2) * P2 + pi2] = m2;
     }
-    __shared__ float sm[16][17];
     sm[ty][tx] = m2;
     __syncthreads();
     int n = 8;
@@ -627,43 +654,57 @@ __global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParam
         __syncthreads();
         if (act) {
             sm[y][x] = v;
-            const int Pk = P >> k, gx = blockIdx.x * n + x, gy = blockIdx.y * n + y;
+            const int Pk = P >> k, gx = bxi * n + x, gy = byi * n + y;
             if (gx < Pk && gy < Pk) c.mip[mip_off(P, k) + size_t(gy) * Pk + gx] = v;
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipParams p) {
-    const MipCascade& c = p.cas[blockIdx.x];
+__global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParams p) {
+    __shared__ float sm[16][17];
+    mip_lo_block<false>(p.cas[blockIdx.z], blockIdx.x, blockIdx.y, sm);
+}
+
+// Levels 7..K of one cascade from level 6 (any block size; s0, s1 hold 4096 floats each).
+template <bool COH>
+__device__ __forceinline__ void mip_hi_levels(const MipCascade& c, float* s0, float* s1) {
     const int P = c.P, K = c.K;
     if (K < 7) return;
-    __shared__ float sm[2][4096];
-    // level 7 from level 6 in global memory
     const int n6 = P >> 6, n7 = P >> 7;
     const float* l6 = c.mip + mip_off(P, 6);
     for (int e = threadIdx.x; e < n7 * n7; e += blockDim.x) {
         const int x = e % n7, y = e / n7;
-        const float v = fmaxf(fmaxf(l6[size_t(2 * y) * n6 + 2 * x], l6[size_t(2 * y) * n6 + 2 * x + 1]),
-                              fmaxf(l6[size_t(2 * y + 1) * n6 + 2 * x], l6[size_t(2 * y + 1) * n6 + 2 * x + 1]));
-        sm[0][e] = v;
+        const float v = fmaxf(fmaxf(ldc<COH>(l6 + size_t(2 * y) * n6 + 2 * x), ldc<COH>(l6 + size_t(2 * y) * n6 + 2 * x + 1)),
+                              fmaxf(ldc<COH>(l6 + size_t(2 * y + 1) * n6 + 2 * x),
+                                    ldc<COH>(l6 + size_t(2 * y + 1) * n6 + 2 * x + 1)));
+        s0[e] = v;
         c.mip[mip_off(P, 7) + e] = v;
     }
     __syncthreads();
-    int cur = 0, n = n7;
+    float* cur = s0;
+    float* nxt = s1;
+    int n = n7;
     for (int k = 8; k <= K; ++k) {
         const int m = n >> 1;
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
             const int x = e % m, y = e / m;
-            const float v = fmaxf(fmaxf(sm[cur][(2 * y) * n + 2 * x], sm[cur][(2 * y) * n + 2 * x + 1]),
-                                  fmaxf(sm[cur][(2 * y + 1) * n + 2 * x], sm[cur][(2 * y + 1) * n + 2 * x + 1]));
-            sm[cur ^ 1][e] = v;
+            const float v = fmaxf(fmaxf(cur[(2 * y) * n + 2 * x], cur[(2 * y) * n + 2 * x + 1]),
+                                  fmaxf(cur[(2 * y + 1) * n + 2 * x], cur[(2 * y + 1) * n + 2 * x + 1]));
+            nxt[e] = v;
             c.mip[mip_off(P, k) + e] = v;
         }
         __syncthreads();
-        cur ^= 1;
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
         n = m;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipParams p) {
+    __shared__ float sm[2][4096];
+    mip_hi_levels<false>(p.cas[blockIdx.x], sm[0], sm[1]);
 }
 
 int launch_maxmip(const MipParams& p, void* stream) {
@@ -704,10 +745,11 @@ struct Ray {
     float du, dv, dz;  // per metre of t
 };
 
+template <bool COH>
 __device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, int ci, int cj,
                                           const Ray& r, float t0, float t1, float& t_hit) {
     const float* p = tex + size_t(cj) * N + ci;
-    const float h00 = __ldg(p), h10 = __ldg(p + 1), h01 = __ldg(p + N), h11 = __ldg(p + N + 1);
+    const float h00 = ldc<COH>(p), h10 = ldc<COH>(p + 1), h01 = ldc<COH>(p + N), h11 = ldc<COH>(p + N + 1);
     const float a0 = fmaf(t0, r.du, r.eu) - float(ci);
     const float b0 = fmaf(t0, r.dv, r.ev) - float(cj);
     const float z0 = fmaf(t0, r.dz, r.ez);
@@ -750,12 +792,12 @@ struct RayDir {
     float tmin, tmax;
 };
 
-template <bool COUNT>
+template <bool COUNT, bool COH>
 __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
                               float ez, float ta, float tb, float& t_hit, DevStatus* status,
                               uint32_t pixel, unsigned& visits, unsigned& tests) {
     const int N = c.N, P = c.P, K = c.K;
-    const float top = __ldg(c.mip + off[K]);
+    const float top = ldc<COH>(c.mip + off[K]);
     if (!(top > -INFINITY)) return false;  // nothing visible in this cascade
     Ray r;
     r.eu = c.eu;
@@ -788,7 +830,7 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
         const float ty = fmaf(exact_float((nj + bv) << k), idv, ov);
         const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
         const float zmin = fmaf(zneg ? te : t, r.dz, ez);
-        const float mx = __ldg(c.mip + off[k] + nj * (P >> k) + ni);
+        const float mx = ldc<COH>(c.mip + off[k] + nj * (P >> k) + ni);
         if (COUNT) ++visits;
         if (zmin <= mx + slack) {
             if (k > 0) {
@@ -797,7 +839,7 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
             }
             if (ci <= N - 2 && cj <= N - 2) {
                 if (COUNT) ++tests;
-                if (patch_hit(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
+                if (patch_hit<COH>(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
             }
         }
         if (te >= tb) return false;
@@ -866,63 +908,70 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayD
     return lo <= hi;
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
-    __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
-    for (int e = threadIdx.y * 16 + threadIdx.x; e < p.C * kMaxLevels; e += 128)
-        s_off[e / kMaxLevels][e % kMaxLevels] = p.cas[e / kMaxLevels].lvl_off[e % kMaxLevels];
-    __syncthreads();
-    const int x = blockIdx.x * 16 + threadIdx.x;
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    unsigned visits = 0, tests = 0;
-    if (x < p.W && y < p.H) {
-        const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
-        const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
-        float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
-        float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
-        float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
-        const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        RayDir d;
-        d.dx = dx * il;
-        d.dy = dy * il;
-        d.dz = dz * il;
-        d.rdx = d.dx != 0.f ? __frcp_rn(d.dx) : 0.f;
-        d.rdy = d.dy != 0.f ? __frcp_rn(d.dy) : 0.f;
-        d.rdz = d.dz != 0.f ? __frcp_rn(d.dz) : 0.f;
-        const float rfd = __frcp_rn(fmaf(d.dx, p.F[0], fmaf(d.dy, p.F[1], d.dz * p.F[2])));
-        d.tmin = p.znear * rfd;
-        d.tmax = p.zfar * rfd;
-        d.ks = fmaf(d.dx, p.dir2x, d.dy * p.dir2y);
-        d.rks = d.ks != 0.f ? __frcp_rn(d.ks) : 0.f;
-        const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
-        int hit = 0;
-        float t = __int_as_float(0x7fc00000);
-        for (int c = 0; c < p.C && !hit; ++c) {
-            const RayCascade& cc = p.cas[c];
-            float ta, tb, tc;
-            if (!cascade_interval(cc, d, ta, tb)) continue;
-            if (!trace_cascade<COUNT>(cc, s_off[c], d, p.ez, ta, tb, tc, status, pix, visits, tests)) continue;
-            hit = 1 + c;
-            t = tc;
-            const float s = tc * d.ks;
-            if (c + 1 < p.C) {
-                const RayCascade& cn = p.cas[c + 1];
-                if (s >= cn.near_d && cc.far_ext > cn.near_d) {
-                    float ta2, tb2, t2;
-                    if (cascade_interval(cn, d, ta2, tb2) &&
-                        trace_cascade<COUNT>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, status, pix, visits,
-                                             tests)) {
-                        const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
-                        t = fmaf(al, t2 - tc, tc);
-                    }
+template <bool COUNT, bool COH>
+__device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_off)[kMaxLevels], DevStatus* status,
+                                              int x, int y, unsigned& visits, unsigned& tests) {
+    if (x >= p.W || y >= p.H) return;
+    const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
+    const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
+    float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
+    float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
+    float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
+    const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    RayDir d;
+    d.dx = dx * il;
+    d.dy = dy * il;
+    d.dz = dz * il;
+    d.rdx = d.dx != 0.f ? __frcp_rn(d.dx) : 0.f;
+    d.rdy = d.dy != 0.f ? __frcp_rn(d.dy) : 0.f;
+    d.rdz = d.dz != 0.f ? __frcp_rn(d.dz) : 0.f;
+    const float rfd = __frcp_rn(fmaf(d.dx, p.F[0], fmaf(d.dy, p.F[1], d.dz * p.F[2])));
+    d.tmin = p.znear * rfd;
+    d.tmax = p.zfar * rfd;
+    d.ks = fmaf(d.dx, p.dir2x, d.dy * p.dir2y);
+    d.rks = d.ks != 0.f ? __frcp_rn(d.ks) : 0.f;
+    const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
+    int hit = 0;
+    float t = __int_as_float(0x7fc00000);
+    for (int c = 0; c < p.C && !hit; ++c) {
+        const RayCascade& cc = p.cas[c];
+        float ta, tb, tc;
+        if (!cascade_interval(cc, d, ta, tb)) continue;
+        if (!trace_cascade<COUNT, COH>(cc, s_off[c], d, p.ez, ta, tb, tc, status, pix, visits, tests)) continue;
+        hit = 1 + c;
+        t = tc;
+        const float s = tc * d.ks;
+        if (c + 1 < p.C) {
+            const RayCascade& cn = p.cas[c + 1];
+            if (s >= cn.near_d && cc.far_ext > cn.near_d) {
+                float ta2, tb2, t2;
+                if (cascade_interval(cn, d, ta2, tb2) &&
+                    trace_cascade<COUNT, COH>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, status, pix, visits, tests)) {
+                    const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
+                    t = fmaf(al, t2 - tc, tc);
                 }
             }
         }
-        if (!COUNT) {
-            p.t_out[pix] = t;
-            p.hit_out[pix] = uint8_t(hit);
-        }
     }
+    if (!COUNT) {
+        p.t_out[pix] = t;
+        p.hit_out[pix] = uint8_t(hit);
+    }
+}
+
+__device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_off)[kMaxLevels], int tid, int nthreads) {
+    for (int e = tid; e < p.C * kMaxLevels; e += nthreads)
+        s_off[e / kMaxLevels][e % kMaxLevels] = p.cas[e / kMaxLevels].lvl_off[e % kMaxLevels];
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
+    __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
+    load_level_offsets(p, s_off, threadIdx.y * 16 + threadIdx.x, 128);
+    __syncthreads();
+    unsigned visits = 0, tests = 0;
+    raycast_pixel<COUNT, false>(p, s_off, status, blockIdx.x * 16 + threadIdx.x, blockIdx.y * 8 + threadIdx.y,
+                                visits, tests);
     if (COUNT) {
         visits = __reduce_add_sync(0xffffffffu, visits);
         tests = __reduce_add_sync(0xffffffffu, tests);
@@ -943,6 +992,198 @@ int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream) {
     dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
     k_raycast<true><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched frames: one persistent launch drains an ordered queue of work units
+// (all visible-row units, then all discretization tiles, then all level-0..6
+// mip blocks, then all mip tops, and optionally all ray tiles).  A unit waits
+// only for units earlier in the queue (per-cascade completion counters), and
+// units are taken only by running CTAs, so every wait ends; each wait is still
+// bounded and reports HF_ERR_TIMEOUT instead of hanging.  Data written in the
+// same launch is read through L2 (ld.global.cg).
+
+constexpr int kWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void wait_count(const uint32_t* ctr, uint32_t target, DevStatus* status,
+                                           uint32_t detail) {
+    if (threadIdx.x == 0) {
+        int it = 0;
+        while (ld_acquire(ctr) < target) {
+            if (++it > kWaitLimit) {
+                report(status, kStatusTimeout, detail);
+                break;
+            }
+            __nanosleep(128);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void signal_done(uint32_t* ctr) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(ctr, 1u);
+}
+
+__device__ __forceinline__ int find_cascade(const BatchCascade* cas, int n, int phase, int u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cas[mid].unit_base[phase] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_item(const BatchItem* items, int n, int u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].ray_unit_base <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+union BatchShared {
+    float mlo[16][17];
+    float mhi[2][4096];
+    int off[HF_MAX_CASCADES][kMaxLevels];
+};
+
+template <bool COH>
+__device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const BatchItem* items, const BatchCascade* cas,
+                                               const uint32_t* done, int u, int (*off)[kMaxLevels]) {
+    const int it = find_item(items, h->n_items, u - h->phase_base[kPhaseRays]);
+    const BatchItem& I = items[it];
+    if (COH) {
+        for (int c = 0; c < I.n_cascades; ++c)
+            wait_count(done + 4 * (I.first_cascade + c) + kPhaseMipHi, 1u, I.status, uint32_t(u));
+    }
+    load_level_offsets(I.ray, off, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int local = u - h->phase_base[kPhaseRays] - I.ray_unit_base;
+    const int tw = h->ray_tile_w, th = h->ray_tile_h;
+    const int x = (local % I.ray_tiles_x) * tw + int(threadIdx.x) % tw;
+    const int y = (local / I.ray_tiles_x) * th + int(threadIdx.x) / tw;
+    unsigned visits = 0, tests = 0;
+    raycast_pixel<false, COH>(I.ray, off, I.status, x, y, visits, tests);
+}
+
+template <bool RAYS_INSIDE>
+__global__ void __launch_bounds__(256) k_batch(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    uint32_t* done = reinterpret_cast<uint32_t*>(const_cast<uint8_t*>(buf) + h->counters_off);
+    uint32_t* queue = done + 4 * h->n_cascades;
+    __shared__ BatchShared sm;
+    __shared__ LookupTables s_lt;
+    __shared__ int s_unit, s_lt_item;
+    if (threadIdx.x == 0) s_lt_item = -1;
+    const int end = RAYS_INSIDE ? h->phase_base[kPhases] : h->phase_base[kPhaseRays];
+    const bool warp16 = (h->flags & kBatchWarp16x2) != 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = int(atomicAdd(queue, 1u));
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= end) break;
+        if (u >= h->phase_base[kPhaseRays]) {
+            batch_ray_unit<true>(h, items, cas, done, u, sm.off);
+            __syncthreads();
+            continue;
+        }
+        int phase = 0;
+        while (phase < kPhaseMipHi && u >= h->phase_base[phase + 1]) ++phase;
+        const int k = find_cascade(cas, h->n_cascades, phase, u);
+        const BatchCascade& C = cas[k];
+        const BatchItem& I = items[C.item];
+        const int local = u - C.unit_base[phase];
+        if (phase > kPhaseRows)
+            wait_count(done + 4 * k + (phase - 1), uint32_t(C.n_units[phase - 1]), I.status, uint32_t(u));
+        if (phase == kPhaseRows) {
+            const int t = local * 256 + threadIdx.x;
+            if (t < C.prep.N) prep_row(C.prep, I.dom_w, I.dom_h, I.eps_frac, t);
+        } else if (phase == kPhaseTexels) {
+            if (s_lt_item != C.item) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    s_lt = I.lt;
+                    s_lt_item = C.item;
+                }
+                __syncthreads();
+            }
+            int di, dj;
+            if (warp16) {
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                di = (warp & 1) * 16 + (lane & 15);
+                dj = (warp >> 1) * 2 + (lane >> 4);
+            } else {
+                tile_texel(threadIdx.x, di, dj);
+            }
+            const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
+            if (I.precision == HF_PREC_FP32)
+                discretize_texel<true>(C.disc, I.K, s_lt, I.lv, I.status, i, j);
+            else if (I.precision == HF_PREC_FP16)
+                discretize_texel_mixed<F16Ops, true>(C.disc, I.K, s_lt, I.cv, I.status, i, j);
+            else
+                discretize_texel_mixed<BF16Ops, true>(C.disc, I.K, s_lt, I.cv, I.status, i, j);
+        } else if (phase == kPhaseMipLo) {
+            mip_lo_block<true>(C.mip, local % C.mip_blocks_x, local / C.mip_blocks_x, sm.mlo);
+        } else {
+            mip_hi_levels<true>(C.mip, sm.mhi[0], sm.mhi[1]);
+        }
+        signal_done(done + 4 * k + phase);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_rays(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    __shared__ int off[HF_MAX_CASCADES][kMaxLevels];
+    batch_ray_unit<false>(h, items, cas, nullptr, h->phase_base[kPhaseRays] + int(blockIdx.x), off);
+}
+
+int batch_persistent_blocks(int* blocks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>, 256, 0);
+    if (e) return e;
+    int per_sm2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_batch<false>, 256, 0);
+    if (e) return e;
+    *blocks = sms * (per_sm < per_sm2 ? per_sm : per_sm2);
+    return cudaSuccess;
+}
+
+int launch_batch(const BatchHeader& h, void* dev_buf, void* stream) {
+    cudaStream_t s = cudaStream_t(stream);
+    const uint8_t* buf = static_cast<const uint8_t*>(dev_buf);
+    const bool inside = (h.flags & kBatchRaysInside) != 0;
+    const int units = inside ? h.phase_base[kPhases] : h.phase_base[kPhaseRays];
+    const int grid = units < h.persistent_blocks ? units : h.persistent_blocks;
+    if (grid > 0) {
+        if (inside) k_batch<true><<<grid, 256, 0, s>>>(buf);
+        else k_batch<false><<<grid, 256, 0, s>>>(buf);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    const int rays = h.phase_base[kPhases] - h.phase_base[kPhaseRays];
+    if (!inside && rays > 0) {
+        k_batch_rays<<<rays, 256, 0, s>>>(buf);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 }  // namespace hfi

@@ -27,7 +27,9 @@ LEAF_DTYPE = np.dtype([("level", "<i4"), ("ix", "<i4"), ("iy", "<i4"), ("value",
 EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_update_values",
             "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
-            "hf_discretize_noalloc", "hf_ray_stats"]
+            "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
+            "hf_batch_launch", "hf_frame_batch"]
+HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 
@@ -82,6 +84,11 @@ class hf_view_stats_t(ct.Structure):
                 ("influencers", ct.c_int64 * HF_MAX_CASCADES)]
 
 
+class hf_batch_item(ct.Structure):
+    _fields_ = [("ctx", ct.c_void_p), ("view_slot", ct.c_int32), ("reserved", ct.c_int32),
+                ("t_dev", ct.c_void_p), ("hit_dev", ct.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
@@ -102,6 +109,10 @@ def _load():
         "hf_sync": [vp, vp],
         "hf_discretize_noalloc": [vp, P(hf_camera), P(vp), P(hf_cascade_info), vp],
         "hf_ray_stats": [vp, i32, P(i64), P(i64), vp],
+        "hf_batch_query_bytes": [P(hf_batch_item), i32, i32, P(sz), P(sz)],
+        "hf_batch_prepare": [P(hf_batch_item), i32, i32, vp, sz],
+        "hf_batch_launch": [vp, vp, sz, vp],
+        "hf_frame_batch": [P(hf_batch_item), i32, i32, vp, sz, vp, sz, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -220,6 +231,28 @@ def hf_ray_stats(ctx, slot: int, stream=None) -> dict:
     v, t = ct.c_int64(), ct.c_int64()
     _check(_lib.hf_ray_stats(ctx, slot, ct.byref(v), ct.byref(t), _stream(stream)))
     return {"visits": v.value, "patch_tests": t.value}
+
+
+def hf_batch_query_bytes(items, flags: int = 0):
+    d, h = ct.c_size_t(), ct.c_size_t()
+    _check(_lib.hf_batch_query_bytes(items, len(items), flags, ct.byref(d), ct.byref(h)))
+    return d.value, h.value
+
+
+def hf_batch_prepare(items, flags: int, host_buf):
+    _check(_lib.hf_batch_prepare(items, len(items), flags, ct.c_void_p(host_buf.data_ptr()),
+                                 host_buf.numel() * host_buf.element_size()))
+
+
+def hf_batch_launch(host_buf, dev_buf, stream=None):
+    _check(_lib.hf_batch_launch(ct.c_void_p(host_buf.data_ptr()), _dptr(dev_buf),
+                                dev_buf.numel() * dev_buf.element_size(), _stream(stream)))
+
+
+def hf_frame_batch(items, flags: int, host_buf, dev_buf, stream=None):
+    _check(_lib.hf_frame_batch(items, len(items), flags, ct.c_void_p(host_buf.data_ptr()),
+                               host_buf.numel() * host_buf.element_size(), _dptr(dev_buf),
+                               dev_buf.numel() * dev_buf.element_size(), _stream(stream)))
 
 
 def hf_sync(ctx, stream=None):

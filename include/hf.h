@@ -243,7 +243,10 @@ int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_o
  * with HF_BATCH_RAYS_INSIDE).  The launch sizes depend only on the items'
  * cascade counts, texture and image sizes, so a captured graph stays valid
  * while those are unchanged and hf_batch_prepare refreshes the pinned
- * descriptors before each replay.  Results equal those of the per-view calls.
+ * descriptors before each replay.  The launch copies host_buf asynchronously:
+ * do not prepare into the same host buffer again until that copy has run
+ * (e.g. alternate two buffers, or wait on an event recorded after the
+ * launch).  Results equal those of the per-view calls.
  * flags select work-unit shapes: HF_BATCH_RAY_TILE_32x8 / _8x32 (default
  * 16x16 pixels per ray unit), HF_BATCH_WARP_16x2 (default 8x4 texels per
  * warp), HF_BATCH_RAYS_INSIDE.  Errors surface through hf_sync of the items'

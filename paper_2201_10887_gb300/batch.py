@@ -41,7 +41,12 @@ def describe(flags: int) -> str:
 
 class Batch:
     """A fixed set of views rendered together.  ``views`` is a list of
-    (Renderer, view_slot); their cameras are set with Renderer.set_camera."""
+    (Renderer, view_slot); their cameras are set with Renderer.set_camera.
+
+    Two pinned descriptor buffers alternate between frames so that the host
+    can prepare frame k+1 while the copy of frame k is still pending; before
+    a buffer is refilled, the event recorded after its last launch is
+    awaited."""
 
     def __init__(self, views, flags: int = 0):
         import torch
@@ -52,9 +57,19 @@ class Batch:
         self._bind_items()
         dev_bytes, host_bytes = hf.hf_batch_query_bytes(self.items, flags)
         device = self.views[0][0].device
-        self.dev_buf = torch.empty(dev_bytes, dtype=torch.uint8, device=device)
-        self.host_buf = torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True)
-        self.graph = None
+        self.dev_bufs = [torch.empty(dev_bytes, dtype=torch.uint8, device=device) for _ in range(2)]
+        self.host_bufs = [torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        self.events = [None, None]
+        self.graphs = None
+        self.cur = 0
+
+    @property
+    def host_buf(self):
+        return self.host_bufs[self.cur]
+
+    @property
+    def dev_buf(self):
+        return self.dev_bufs[self.cur]
 
     def _bind_items(self):
         for k, (r, slot) in enumerate(self.views):
@@ -62,38 +77,53 @@ class Batch:
             self.items[k] = hf.hf_batch_item(r.ctx.value, slot, 0, v["t"].data_ptr(), v["hit"].data_ptr())
 
     def prepare(self, flags: int | None = None):
+        """Fill the next descriptor buffer from the views' current cameras."""
         if flags is not None and flags != self.flags:
             self.flags = flags
-            self.graph = None
-        hf.hf_batch_prepare(self.items, self.flags, self.host_buf)
+            self.graphs = None
+        self.cur ^= 1
+        if self.events[self.cur] is not None:
+            self.events[self.cur].synchronize()
+        hf.hf_batch_prepare(self.items, self.flags, self.host_bufs[self.cur])
 
     def launch(self, stream=None):
-        hf.hf_batch_launch(self.host_buf, self.dev_buf, stream)
+        torch = self.torch
+        if self.graphs is not None:
+            self.graphs[self.cur].replay()
+        else:
+            hf.hf_batch_launch(self.host_bufs[self.cur], self.dev_bufs[self.cur], stream)
+        ev = torch.cuda.Event()
+        ev.record(stream if stream is not None else torch.cuda.current_stream())
+        self.events[self.cur] = ev
 
     def run(self, stream=None):
         """Prepare from the current cameras and run (graph replay if captured)."""
         self.prepare()
-        if self.graph is not None:
-            self.graph.replay()
-        else:
-            self.launch(stream)
+        self.launch(stream)
 
     def capture(self):
-        """Capture the launch (descriptor copy, counter reset, kernels) in a
-        CUDA graph; later ``run`` calls replay it."""
+        """Capture the launch of each descriptor buffer (copy, counter reset,
+        kernels) in a CUDA graph; later ``launch`` / ``run`` calls replay."""
         torch = self.torch
-        self.prepare()
-        self.launch()  # warm-up outside capture (first-use initialisation)
+        self.graphs = None
+        graphs = []
+        for b in range(2):
+            self.prepare()
+            hf.hf_batch_launch(self.host_bufs[self.cur], self.dev_bufs[self.cur])  # warm-up
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    hf.hf_batch_launch(self.host_bufs[self.cur], self.dev_bufs[self.cur], s)
+            torch.cuda.current_stream().wait_stream(s)
+            graphs.append((self.cur, g))
+        self.graphs = [None, None]
+        for b, g in graphs:
+            self.graphs[b] = g
         torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(g, stream=s):
-                hf.hf_batch_launch(self.host_buf, self.dev_buf, s)
-        torch.cuda.current_stream().wait_stream(s)
-        self.graph = g
-        return g
+        return self.graphs
 
     def outputs(self, k: int):
         r, slot = self.views[k]

@@ -93,9 +93,9 @@ def test_batch_equals_per_view_calls_for_every_shape(torch_cuda):
 def test_batch_graph_replay_with_new_cameras(torch_cuda):
     from paper_2201_10887_gb300 import Batch
     views, cams = _setup(torch_cuda)
-    batch = Batch(views)
     for r_slot, cam in zip(views, cams):
         r_slot[0].set_camera(cam, r_slot[1])
+    batch = Batch(views)
     batch.capture()
     for step in range(3):
         moved = [c.with_(eye=(c.eye[0] + 17.0 * step, c.eye[1] - 9.0 * step, c.eye[2] + 5.0 * step))

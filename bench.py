@@ -443,6 +443,77 @@ def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream):
     return out
 
 
+def run_batch_workload(args):
+    """64 independent tiles (finest side log-uniform in [256, 4096], 1-4
+    cascades of 512^2-2048^2, one 960x540 view each), rendered per view, as
+    one batched launch (autotuned shapes), and as a replayed CUDA graph."""
+    import torch
+    import workloads
+    from paper_2201_10887_gb300 import Batch, Renderer, autotune
+    from paper_2201_10887_gb300.batch import describe
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    scenes = workloads.batch_config(seed=4, n_tiles=args.tiles)
+    t_gen = time.perf_counter() - t0
+    rs, views, cams = [], [], []
+    for sc in scenes:
+        r = Renderer(sc.tree, sc.sigma, sc.radius)
+        r.set_camera(sc.cameras[0])
+        rs.append(r)
+        views.append((r, 0))
+        cams.append(sc.cameras[0])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        out = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    def per_view():
+        for r, cam in zip(rs, cams):
+            r.set_camera(cam)
+            r.discretize()
+            r.build_maxmip()
+            r.raycast()
+
+    for _ in range(args.warmup):
+        per_view()
+    single = timed(per_view, args.steps)
+    batch = Batch(views)
+    best, tune = autotune(batch, reps=2)
+    for _ in range(args.warmup):
+        batch.run()
+    batched = timed(batch.run, args.steps)
+    batch.capture()
+    for _ in range(args.warmup):
+        batch.run()
+    graphed = timed(batch.run, args.steps)
+    for r in rs:
+        r.sync()
+    texels = sum(c.n_cascades * c.cascade_size ** 2 for c in cams)
+    rays = sum(c.width * c.height for c in cams)
+    line = {"metric": f"batched frame ms ({len(cams)} tiles, one 960x540 view each)",
+            "value": statistics.median(graphed), "unit": "ms", "higher_is_better": False,
+            "per_view_calls_ms": statistics.median(single), "batched_launch_ms": statistics.median(batched),
+            "graph_replay_ms": statistics.median(graphed), "p99_graph_ms": _pct(graphed, 99),
+            "autotuned": describe(best), "autotune_ms": {describe(k): v for k, v in tune.items()},
+            "tiles": len(cams), "cascade_texels": texels, "rays": rays,
+            "grays_per_s_graph": rays / (statistics.median(graphed) * 1e-3) / 1e9,
+            "leaves": sum(sc.tree.n_leaves for sc in scenes), "generation_s": t_gen,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch: 64 tiles, finest side log-uniform 256-4096, 1-4 cascades of "
+                                   "512^2-2048^2, 960x540 per tile", "l2": "flushed between steps"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,6 +525,8 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=15.0, help="CPU seconds of the baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 timing")
+    ap.add_argument("--workload", default="dem", choices=["dem", "batch", "serve"])
+    ap.add_argument("--tiles", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -469,6 +542,10 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        import __graft_entry__
+        __graft_entry__.build_library()
+        run_batch_workload(args)
     else:
         import __graft_entry__
         __graft_entry__.build_library()

@@ -143,6 +143,8 @@ def curvature_quadtree(root_nx: int, root_ny: int, root_cell: float, max_level: 
         n = sum(int(m.sum()) for m in leaves)
         if best is None or abs(n - target_leaves) < abs(best[0] - target_leaves):
             best = (n, leaves)
+        if abs(n - target_leaves) <= 0.002 * target_leaves:
+            break
         if n > target_leaves:
             lo = mid
         else:

@@ -815,7 +815,7 @@ int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
     return HF_OK;
 }
 
-int g_persistent_blocks[64] = {};
+int g_persistent_blocks[64][2] = {};
 
 }  // namespace
 
@@ -843,8 +843,8 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
     int e = cudaGetDevice(&dev);
     if (e) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(HF_ERR_ARG, "device index %d", dev);
-    if (!g_persistent_blocks[dev]) {
-        e = batch_persistent_blocks(&g_persistent_blocks[dev]);
+    if (!g_persistent_blocks[dev][0]) {
+        e = batch_persistent_blocks(&g_persistent_blocks[dev][0], &g_persistent_blocks[dev][1]);
         if (e) return cuda_fail(e, "occupancy query");
     }
     char* hb = static_cast<char*>(host_buf);
@@ -858,7 +858,8 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
     const int shape = (flags & kBatchRayTileMask) >> 1;
     h.ray_tile_w = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
     h.ray_tile_h = 256 / h.ray_tile_w;
-    h.persistent_blocks = g_persistent_blocks[dev];
+    h.persistent_blocks = g_persistent_blocks[dev][0];
+    h.persistent_blocks_rays = g_persistent_blocks[dev][1];
     h.items_off = int64_t(plan.items_off);
     h.cascades_off = int64_t(plan.cascades_off);
     h.counters_off = int64_t(plan.counters_off);

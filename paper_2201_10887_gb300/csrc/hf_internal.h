@@ -192,7 +192,8 @@ struct BatchHeader {
     int32_t phase_base[kPhases + 1];  // unit ranges per phase; phase_base[kPhases] = all units
     int32_t ray_tile_w, ray_tile_h;
     int32_t flags;
-    int32_t persistent_blocks;
+    int32_t persistent_blocks, persistent_blocks_rays;
+    int32_t pad;
     int64_t items_off, cascades_off, counters_off, desc_bytes, total_bytes;
 };
 
@@ -211,7 +212,7 @@ int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& l
                  DevStatus* status, void* stream);
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
 int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream);
-int batch_persistent_blocks(int* blocks);
+int batch_persistent_blocks(int* blocks_plain, int* blocks_rays);
 int launch_batch(const BatchHeader& h, void* dev_buf, void* stream);
 
 // Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the

@@ -1077,8 +1077,14 @@ __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const Batch
     raycast_pixel<false, COH>(I.ray, off, I.status, x, y, visits, tests);
 }
 
+// Units are taken in chunks of kChunk; completions of consecutive units of
+// the same cascade and phase are released with one counter increment, and
+// pending releases are always flushed before the CTA waits on anything, so a
+// CTA never waits on its own unreleased work.
+constexpr int kChunk = 4;
+
 template <bool RAYS_INSIDE>
-__global__ void __launch_bounds__(256) k_batch(const uint8_t* __restrict__ buf) {
+__global__ void __launch_bounds__(256, RAYS_INSIDE ? 3 : 5) k_batch(const uint8_t* __restrict__ buf) {
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
@@ -1086,63 +1092,111 @@ __global__ void __launch_bounds__(256) k_batch(const uint8_t* __restrict__ buf) 
     uint32_t* queue = done + 4 * h->n_cascades;
     __shared__ BatchShared sm;
     __shared__ LookupTables s_lt;
-    __shared__ int s_unit, s_lt_item;
-    if (threadIdx.x == 0) s_lt_item = -1;
+    __shared__ DiscCascade s_disc;
+    __shared__ int s_base, s_lt_item, s_disc_k;
+    if (threadIdx.x == 0) {
+        s_lt_item = -1;
+        s_disc_k = -1;
+    }
+    const int n_cas = h->n_cascades;
     const int end = RAYS_INSIDE ? h->phase_base[kPhases] : h->phase_base[kPhaseRays];
+    const int ray_base = h->phase_base[kPhaseRays];
     const bool warp16 = (h->flags & kBatchWarp16x2) != 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = int(atomicAdd(queue, 1u));
-        __syncthreads();
-        const int u = s_unit;
-        __syncthreads();
-        if (u >= end) break;
-        if (u >= h->phase_base[kPhaseRays]) {
-            batch_ray_unit<true>(h, items, cas, done, u, sm.off);
+    int kc = 0, kc_phase = -1;          // cached cascade of the last unit (uniform)
+    int run_k = -1, run_phase = -1;     // pending completions (uniform)
+    uint32_t run_n = 0;
+    auto flush = [&]() {
+        if (run_n) {
+            __threadfence();
             __syncthreads();
-            continue;
+            if (threadIdx.x == 0) atomicAdd(done + 4 * run_k + run_phase, run_n);
+            run_n = 0;
         }
-        int phase = 0;
-        while (phase < kPhaseMipHi && u >= h->phase_base[phase + 1]) ++phase;
-        const int k = find_cascade(cas, h->n_cascades, phase, u);
-        const BatchCascade& C = cas[k];
-        const BatchItem& I = items[C.item];
-        const int local = u - C.unit_base[phase];
-        if (phase > kPhaseRows)
-            wait_count(done + 4 * k + (phase - 1), uint32_t(C.n_units[phase - 1]), I.status, uint32_t(u));
-        if (phase == kPhaseRows) {
-            const int t = local * 256 + threadIdx.x;
-            if (t < C.prep.N) prep_row(C.prep, I.dom_w, I.dom_h, I.eps_frac, t);
-        } else if (phase == kPhaseTexels) {
-            if (s_lt_item != C.item) {
+    };
+    for (;;) {
+        if (threadIdx.x == 0) s_base = int(atomicAdd(queue, unsigned(kChunk)));
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();
+        if (base >= end) break;
+        for (int u = base; u < base + kChunk && u < end; ++u) {
+            if (RAYS_INSIDE && u >= ray_base) {
+                flush();
+                batch_ray_unit<true>(h, items, cas, done, u, sm.off);
                 __syncthreads();
+                continue;
+            }
+            int phase = 0;
+            while (phase < kPhaseMipHi && u >= h->phase_base[phase + 1]) ++phase;
+            if (phase != kc_phase) {
+                kc = find_cascade(cas, n_cas, phase, u);
+                kc_phase = phase;
+            } else {
+                while (kc + 1 < n_cas && cas[kc + 1].unit_base[phase] <= u) ++kc;
+            }
+            const int k = kc;
+            const BatchCascade& C = cas[k];
+            if (run_n && (k != run_k || phase != run_phase)) flush();
+            if (phase > kPhaseRows) {
+                flush();
+                const uint32_t need = uint32_t(C.n_units[phase - 1]);
                 if (threadIdx.x == 0) {
-                    s_lt = I.lt;
-                    s_lt_item = C.item;
+                    int it = 0;
+                    while (ld_acquire(done + 4 * k + (phase - 1)) < need) {
+                        if (++it > kWaitLimit) {
+                            report(items[C.item].status, kStatusTimeout, uint32_t(u));
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
                 }
                 __syncthreads();
             }
-            int di, dj;
-            if (warp16) {
-                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                di = (warp & 1) * 16 + (lane & 15);
-                dj = (warp >> 1) * 2 + (lane >> 4);
+            const int local = u - C.unit_base[phase];
+            if (phase == kPhaseRows) {
+                const BatchItem& I = items[C.item];
+                const int t = local * 256 + threadIdx.x;
+                if (t < C.prep.N) prep_row(C.prep, I.dom_w, I.dom_h, I.eps_frac, t);
+            } else if (phase == kPhaseTexels) {
+                if (s_lt_item != C.item || s_disc_k != k) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        if (s_lt_item != C.item) s_lt = items[C.item].lt;
+                        s_disc = C.disc;
+                        s_lt_item = C.item;
+                        s_disc_k = k;
+                    }
+                    __syncthreads();
+                }
+                const BatchItem& I = items[C.item];
+                int di, dj;
+                if (warp16) {
+                    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                    di = (warp & 1) * 16 + (lane & 15);
+                    dj = (warp >> 1) * 2 + (lane >> 4);
+                } else {
+                    tile_texel(threadIdx.x, di, dj);
+                }
+                const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
+                if (I.precision == HF_PREC_FP32)
+                    discretize_texel<true>(s_disc, I.K, s_lt, I.lv, I.status, i, j);
+                else if (I.precision == HF_PREC_FP16)
+                    discretize_texel_mixed<F16Ops, true>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+                else
+                    discretize_texel_mixed<BF16Ops, true>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+            } else if (phase == kPhaseMipLo) {
+                mip_lo_block<true>(C.mip, local % C.mip_blocks_x, local / C.mip_blocks_x, sm.mlo);
             } else {
-                tile_texel(threadIdx.x, di, dj);
+                mip_hi_levels<true>(C.mip, sm.mhi[0], sm.mhi[1]);
             }
-            const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
-            if (I.precision == HF_PREC_FP32)
-                discretize_texel<true>(C.disc, I.K, s_lt, I.lv, I.status, i, j);
-            else if (I.precision == HF_PREC_FP16)
-                discretize_texel_mixed<F16Ops, true>(C.disc, I.K, s_lt, I.cv, I.status, i, j);
-            else
-                discretize_texel_mixed<BF16Ops, true>(C.disc, I.K, s_lt, I.cv, I.status, i, j);
-        } else if (phase == kPhaseMipLo) {
-            mip_lo_block<true>(C.mip, local % C.mip_blocks_x, local / C.mip_blocks_x, sm.mlo);
-        } else {
-            mip_hi_levels<true>(C.mip, sm.mhi[0], sm.mhi[1]);
+            __syncthreads();
+            run_k = k;
+            run_phase = phase;
+            ++run_n;
         }
-        signal_done(done + 4 * k + phase);
+        flush();
     }
+    flush();
 }
 
 __global__ void __launch_bounds__(256) k_batch_rays(const uint8_t* __restrict__ buf) {
@@ -1153,16 +1207,15 @@ __global__ void __launch_bounds__(256) k_batch_rays(const uint8_t* __restrict__ 
     batch_ray_unit<false>(h, items, cas, nullptr, h->phase_base[kPhaseRays] + int(blockIdx.x), off);
 }
 
-int batch_persistent_blocks(int* blocks) {
-    int dev = 0, sms = 0, per_sm = 0;
+int batch_persistent_blocks(int* blocks_plain, int* blocks_rays) {
+    int dev = 0, sms = 0, a = 0, b = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<true>, 256, 0);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_batch<false>, 256, 0);
+    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch<true>, 256, 0);
     if (e) return e;
-    int per_sm2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_batch<false>, 256, 0);
-    if (e) return e;
-    *blocks = sms * (per_sm < per_sm2 ? per_sm : per_sm2);
+    *blocks_plain = sms * a;
+    *blocks_rays = sms * b;
     return cudaSuccess;
 }
 
@@ -1171,7 +1224,9 @@ int launch_batch(const BatchHeader& h, void* dev_buf, void* stream) {
     const uint8_t* buf = static_cast<const uint8_t*>(dev_buf);
     const bool inside = (h.flags & kBatchRaysInside) != 0;
     const int units = inside ? h.phase_base[kPhases] : h.phase_base[kPhaseRays];
-    const int grid = units < h.persistent_blocks ? units : h.persistent_blocks;
+    const int cap = inside ? h.persistent_blocks_rays : h.persistent_blocks;
+    const int chunks = (units + kChunk - 1) / kChunk;
+    const int grid = chunks < cap ? chunks : cap;
     if (grid > 0) {
         if (inside) k_batch<true><<<grid, 256, 0, s>>>(buf);
         else k_batch<false><<<grid, 256, 0, s>>>(buf);

@@ -240,7 +240,9 @@ int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_o
  * queue of visible rows, discretization tiles and max-mip blocks of every
  * cascade of every item (bounded waits on per-cascade completion counters),
  * then the ray tiles of every item (in a second launch, or in the same one
- * with HF_BATCH_RAYS_INSIDE).  The launch sizes depend only on the items'
+ * with HF_BATCH_RAYS_INSIDE) -- that is HF_BATCH_PERSISTENT; without it, one
+ * launch per phase covers all cascades of all items (five launches in all,
+ * meant to be captured in one CUDA graph).  The launch sizes depend only on the items'
  * cascade counts, texture and image sizes, so a captured graph stays valid
  * while those are unchanged and hf_batch_prepare refreshes the pinned
  * descriptors before each replay.  The launch copies host_buf asynchronously:
@@ -249,8 +251,8 @@ int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_o
  * launch).  Results equal those of the per-view calls.
  * flags select work-unit shapes: HF_BATCH_RAY_TILE_32x8 / _8x32 (default
  * 16x16 pixels per ray unit), HF_BATCH_WARP_16x2 (default 8x4 texels per
- * warp), HF_BATCH_RAYS_INSIDE.  Errors surface through hf_sync of the items'
- * contexts. */
+ * warp), HF_BATCH_PERSISTENT, HF_BATCH_RAYS_INSIDE (with PERSISTENT only).
+ * Errors surface through hf_sync of the items' contexts. */
 typedef struct {
     hf_ctx* ctx;
     int32_t view_slot;
@@ -263,7 +265,8 @@ enum {
     HF_BATCH_RAYS_INSIDE = 1,
     HF_BATCH_RAY_TILE_32x8 = 2,
     HF_BATCH_RAY_TILE_8x32 = 4,
-    HF_BATCH_WARP_16x2 = 8
+    HF_BATCH_WARP_16x2 = 8,
+    HF_BATCH_PERSISTENT = 16
 };
 
 int hf_batch_query_bytes(const hf_batch_item* items, int32_t n, int32_t flags, size_t* device_bytes,

@@ -23,11 +23,18 @@ SHAPE_FLAGS = {
 }
 
 
+MODES = {
+    "per-phase launches": 0,
+    "persistent launch + ray launch": hf.HF_BATCH_PERSISTENT,
+    "one persistent launch": hf.HF_BATCH_PERSISTENT | hf.HF_BATCH_RAYS_INSIDE,
+}
+
+
 def flag_candidates():
     out = []
-    for ray, warp, inside in itertools.product(SHAPE_FLAGS.values(), (0, hf.HF_BATCH_WARP_16x2),
-                                               (0, hf.HF_BATCH_RAYS_INSIDE)):
-        out.append(ray | warp | inside)
+    for ray, warp, mode in itertools.product(SHAPE_FLAGS.values(), (0, hf.HF_BATCH_WARP_16x2),
+                                             MODES.values()):
+        out.append(ray | warp | mode)
     return out
 
 
@@ -35,8 +42,8 @@ def describe(flags: int) -> str:
     ray = {0: "16x16", hf.HF_BATCH_RAY_TILE_32x8: "32x8", hf.HF_BATCH_RAY_TILE_8x32: "8x32"}[
         flags & (hf.HF_BATCH_RAY_TILE_32x8 | hf.HF_BATCH_RAY_TILE_8x32)]
     warp = "16x2" if flags & hf.HF_BATCH_WARP_16x2 else "8x4"
-    inside = "rays in persistent launch" if flags & hf.HF_BATCH_RAYS_INSIDE else "rays in second launch"
-    return f"ray tile {ray}, texel warp {warp}, {inside}"
+    mode = [k for k, v in MODES.items() if v == flags & (hf.HF_BATCH_PERSISTENT | hf.HF_BATCH_RAYS_INSIDE)][0]
+    return f"{mode}, ray tile {ray}, texel warp {warp}"
 
 
 class Batch:

@@ -837,7 +837,10 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
     if (!host_buf) return fail(HF_ERR_ARG, "null host buffer");
     if (host_bytes < plan.counters_off)
         return fail(HF_ERR_NOMEM, "batch host buffer has %zu bytes, %zu needed", host_bytes, plan.counters_off);
-    if (flags & ~int32_t(kBatchRaysInside | kBatchRayTileMask | kBatchWarp16x2)) return fail(HF_ERR_ARG, "unknown batch flags");
+    if (flags & ~int32_t(kBatchRaysInside | kBatchRayTileMask | kBatchWarp16x2 | kBatchPersistent))
+        return fail(HF_ERR_ARG, "unknown batch flags");
+    if ((flags & kBatchRaysInside) && !(flags & kBatchPersistent))
+        return fail(HF_ERR_ARG, "HF_BATCH_RAYS_INSIDE needs HF_BATCH_PERSISTENT");
     if (((flags & kBatchRayTileMask) >> 1) == 3) return fail(HF_ERR_ARG, "choose one ray tile shape");
     int dev = 0;
     int e = cudaGetDevice(&dev);
@@ -903,6 +906,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             B.tiles_x = (N + 31) / 32;
             B.mip_blocks_x = (P + 63) / 64;
             B.n_units[kPhaseRows] = (N + 255) / 256;
+            h.max_rows_units = std::max(h.max_rows_units, B.n_units[kPhaseRows]);
             B.n_units[kPhaseTexels] = B.tiles_x * ((N + 7) / 8);
             B.n_units[kPhaseMipLo] = B.mip_blocks_x * B.mip_blocks_x;
             B.n_units[kPhaseMipHi] = 1;

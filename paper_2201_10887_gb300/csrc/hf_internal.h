@@ -160,7 +160,8 @@ enum { kPhaseRows = 0, kPhaseTexels = 1, kPhaseMipLo = 2, kPhaseMipHi = 3, kPhas
 enum : int32_t {
     kBatchRaysInside = 1,   // ray tiles drained by the persistent launch too
     kBatchRayTileMask = 6,  // (flags >> 1) & 3: 0 = 16x16, 1 = 32x8, 2 = 8x32 pixels per ray unit
-    kBatchWarp16x2 = 8      // discretization warps cover 16 x 2 texels (else 8 x 4)
+    kBatchWarp16x2 = 8,     // discretization warps cover 16 x 2 texels (else 8 x 4)
+    kBatchPersistent = 16   // rows / texels / mips in one persistent launch (else one launch per phase)
 };
 
 struct BatchCascade {
@@ -193,7 +194,7 @@ struct BatchHeader {
     int32_t ray_tile_w, ray_tile_h;
     int32_t flags;
     int32_t persistent_blocks, persistent_blocks_rays;
-    int32_t pad;
+    int32_t max_rows_units;
     int64_t items_off, cascades_off, counters_off, desc_bytes, total_bytes;
 };
 

@@ -1219,19 +1219,104 @@ int batch_persistent_blocks(int* blocks_plain, int* blocks_rays) {
     return cudaSuccess;
 }
 
+// One launch per phase over all cascades of all items: each CTA finds its
+// cascade by binary search over the phase's unit bases; kernel boundaries
+// order the phases, so the per-view code paths (and read-only loads) apply.
+__global__ void __launch_bounds__(128) k_bat_rows(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    const BatchCascade& C = cas[blockIdx.y];
+    const BatchItem& I = items[C.item];
+    const int t = blockIdx.x * 128 + threadIdx.x;
+    if (t < C.prep.N) prep_row(C.prep, I.dom_w, I.dom_h, I.eps_frac, t);
+}
+
+__global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    __shared__ LookupTables s_lt;
+    __shared__ DiscCascade s_disc;
+    const int u = h->phase_base[kPhaseTexels] + int(blockIdx.x);
+    const int k = find_cascade(cas, h->n_cascades, kPhaseTexels, u);
+    const BatchCascade& C = cas[k];
+    const BatchItem& I = items[C.item];
+    if (threadIdx.x == 0) {
+        s_lt = I.lt;
+        s_disc = C.disc;
+    }
+    __syncthreads();
+    const int local = u - C.unit_base[kPhaseTexels];
+    int di, dj;
+    if (h->flags & kBatchWarp16x2) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        di = (warp & 1) * 16 + (lane & 15);
+        dj = (warp >> 1) * 2 + (lane >> 4);
+    } else {
+        tile_texel(threadIdx.x, di, dj);
+    }
+    const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
+    if (I.precision == HF_PREC_FP32)
+        discretize_texel<false>(s_disc, I.K, s_lt, I.lv, I.status, i, j);
+    else if (I.precision == HF_PREC_FP16)
+        discretize_texel_mixed<F16Ops, false>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+    else
+        discretize_texel_mixed<BF16Ops, false>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+}
+
+__global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    __shared__ float sm[16][17];
+    const int u = h->phase_base[kPhaseMipLo] + int(blockIdx.x);
+    const int k = find_cascade(cas, h->n_cascades, kPhaseMipLo, u);
+    const BatchCascade& C = cas[k];
+    const int local = u - C.unit_base[kPhaseMipLo];
+    mip_lo_block<false>(C.mip, local % C.mip_blocks_x, local / C.mip_blocks_x, sm);
+}
+
+__global__ void __launch_bounds__(1024) k_bat_miphi(const uint8_t* __restrict__ buf) {
+    const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
+    const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
+    __shared__ float sm[2][4096];
+    mip_hi_levels<false>(cas[blockIdx.x].mip, sm[0], sm[1]);
+}
+
 int launch_batch(const BatchHeader& h, void* dev_buf, void* stream) {
     cudaStream_t s = cudaStream_t(stream);
     const uint8_t* buf = static_cast<const uint8_t*>(dev_buf);
-    const bool inside = (h.flags & kBatchRaysInside) != 0;
-    const int units = inside ? h.phase_base[kPhases] : h.phase_base[kPhaseRays];
-    const int cap = inside ? h.persistent_blocks_rays : h.persistent_blocks;
-    const int chunks = (units + kChunk - 1) / kChunk;
-    const int grid = chunks < cap ? chunks : cap;
-    if (grid > 0) {
-        if (inside) k_batch<true><<<grid, 256, 0, s>>>(buf);
-        else k_batch<false><<<grid, 256, 0, s>>>(buf);
-        cudaError_t e = cudaGetLastError();
-        if (e) return e;
+    const bool persistent = (h.flags & kBatchPersistent) != 0;
+    const bool inside = persistent && (h.flags & kBatchRaysInside) != 0;
+    cudaError_t e;
+    if (persistent) {
+        const int units = inside ? h.phase_base[kPhases] : h.phase_base[kPhaseRays];
+        const int cap = inside ? h.persistent_blocks_rays : h.persistent_blocks;
+        const int chunks = (units + kChunk - 1) / kChunk;
+        const int grid = chunks < cap ? chunks : cap;
+        if (grid > 0) {
+            if (inside) k_batch<true><<<grid, 256, 0, s>>>(buf);
+            else k_batch<false><<<grid, 256, 0, s>>>(buf);
+            if ((e = cudaGetLastError())) return e;
+        }
+    } else {
+        const int nrow = h.phase_base[kPhaseTexels] - h.phase_base[kPhaseRows];
+        const int ntex = h.phase_base[kPhaseMipLo] - h.phase_base[kPhaseTexels];
+        const int nmip = h.phase_base[kPhaseMipHi] - h.phase_base[kPhaseMipLo];
+        if (nrow > 0) {
+            k_bat_rows<<<dim3(2 * h.max_rows_units, h.n_cascades), 128, 0, s>>>(buf);
+            if ((e = cudaGetLastError())) return e;
+        }
+        if (ntex > 0) {
+            k_bat_texels<<<ntex, 256, 0, s>>>(buf);
+            if ((e = cudaGetLastError())) return e;
+        }
+        if (nmip > 0) {
+            k_bat_miplo<<<nmip, 256, 0, s>>>(buf);
+            if ((e = cudaGetLastError())) return e;
+        }
+        k_bat_miphi<<<h.n_cascades, 1024, 0, s>>>(buf);
+        if ((e = cudaGetLastError())) return e;
     }
     const int rays = h.phase_base[kPhases] - h.phase_base[kPhaseRays];
     if (!inside && rays > 0) {

@@ -30,6 +30,7 @@ EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_up
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
             "hf_batch_launch", "hf_frame_batch"]
 HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
+HF_BATCH_PERSISTENT = 16
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
 
 

@@ -9,5 +9,6 @@ owns the device buffers of one heightfield.  Importing the package loads
 from . import hf
 from .renderer import Renderer, camera_struct
 from .batch import Batch, autotune
+from .serving import Arena, Server
 
-__all__ = ["hf", "Renderer", "camera_struct", "Batch", "autotune"]
+__all__ = ["hf", "Renderer", "camera_struct", "Batch", "autotune", "Arena", "Server"]

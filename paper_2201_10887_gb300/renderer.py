@@ -64,6 +64,18 @@ class Renderer:
         v["C"] = cam.n_cascades
         return v
 
+    def bind_view(self, slot: int, cam, view_buf, t_out, hit_out):
+        """Use caller-provided buffers for a view slot (uint8 view buffer of
+        at least view_bytes(), float32 t and uint8 hit of width*height)."""
+        need = self.view_bytes(cam.n_cascades, cam.cascade_size)
+        npx = cam.width * cam.height
+        if view_buf.numel() < need or t_out.numel() < npx or hit_out.numel() < npx:
+            raise ValueError("view buffers too small")
+        self.views[slot] = {"buf": view_buf, "t": t_out, "hit": hit_out, "npx": npx,
+                            "shape": (cam.height, cam.width), "C": cam.n_cascades, "external": True}
+        hf.hf_set_camera(self.ctx, slot, camera_struct(cam), view_buf)
+        return self.views[slot]
+
     # -- per-frame steps ------------------------------------------------------
     def set_camera(self, cam, slot: int = 0):
         v = self._slot_buffers(slot, cam)

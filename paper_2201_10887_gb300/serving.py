@@ -1,0 +1,200 @@
+"""Continuous-batching view server over one resident heightfield.
+
+Requests (a camera each, with its own image size and cascade count) arrive
+over time.  The server keeps the quadtree resident, admits waiting requests
+first come first served while a view slot is free and their device memory
+(cascade textures, max mipmaps, outputs) fits the budget, launches each
+admitted group as one batched frame (``hf_frame_batch``) on the next of a few
+streams -- so groups admitted while others are still running overlap on the
+device -- and copies each view's ray-cast result to pinned host memory.  A
+request's latency runs from its arrival to its result being on the host.
+Slots and memory are returned as soon as a group's event has completed.
+"""
+
+from __future__ import annotations
+
+import collections
+import statistics
+import time
+
+from . import hf
+from .renderer import Renderer
+
+
+class Arena:
+    """First-fit allocator over one device buffer (256-byte aligned blocks)."""
+
+    def __init__(self, nbytes: int):
+        self.size = int(nbytes)
+        self.free = [(0, self.size)]
+
+    @staticmethod
+    def _round(n):
+        return (int(n) + 255) & ~255
+
+    def alloc(self, n: int):
+        n = self._round(n)
+        for k, (off, sz) in enumerate(self.free):
+            if sz >= n:
+                if sz == n:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (off + n, sz - n)
+                return off
+        return None
+
+    def release(self, off: int, n: int):
+        n = self._round(n)
+        self.free.append((off, n))
+        self.free.sort()
+        merged = []
+        for o, z in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == o:
+                merged[-1] = (merged[-1][0], merged[-1][1] + z)
+            else:
+                merged.append((o, z))
+        self.free = merged
+
+    def used(self) -> int:
+        return self.size - sum(z for _, z in self.free)
+
+
+class Server:
+    def __init__(self, renderer: Renderer, memory_budget: int, max_slots: int = 32,
+                 n_streams: int = 3, max_group: int = 16, flags: int = 0, keep_results=False):
+        import torch
+        self.torch = torch
+        self.r = renderer
+        self.budget = int(memory_budget)
+        self.max_slots = max_slots
+        self.max_group = max_group
+        self.flags = flags
+        self.keep_results = keep_results
+        self.streams = [torch.cuda.Stream(device=renderer.device) for _ in range(n_streams)]
+        self.stream_event = [None] * n_streams
+        desc = 1 << 22  # descriptor buffers per stream, checked against hf_batch_query_bytes
+        self.host_desc = [torch.empty(desc, dtype=torch.uint8, pin_memory=True) for _ in self.streams]
+        self.dev_desc = [torch.empty(desc, dtype=torch.uint8, device=renderer.device) for _ in self.streams]
+        self.host_out = {}
+        self.free_slots = list(range(max_slots))
+        self.pool = torch.empty(self.budget, dtype=torch.uint8, device=renderer.device)
+        self.arena = Arena(self.budget)
+        self.max_used = 0
+
+    def request_bytes(self, cam) -> int:
+        """Device memory of one view: per-view buffer plus t and hit."""
+        r = Arena._round
+        npx = cam.width * cam.height
+        return r(self.r.view_bytes(cam.n_cascades, cam.cascade_size)) + r(4 * npx) + r(npx)
+
+    def _bind(self, req, slot, off):
+        cam = req.camera
+        r = Arena._round
+        vb = r(self.r.view_bytes(cam.n_cascades, cam.cascade_size))
+        npx = cam.width * cam.height
+        buf = self.pool[off: off + vb]
+        t = self.pool[off + vb: off + vb + 4 * npx].view(self.torch.float32)
+        h = self.pool[off + vb + r(4 * npx): off + vb + r(4 * npx) + npx]
+        self.r.bind_view(slot, cam, buf, t, h)
+
+    def _host_outputs(self, slot, cam):
+        n = cam.width * cam.height
+        cur = self.host_out.get(slot)
+        if cur is None or cur[0].numel() < n:
+            t = self.torch.empty(n, dtype=self.torch.float32, pin_memory=True)
+            h = self.torch.empty(n, dtype=self.torch.uint8, pin_memory=True)
+            cur = (t, h)
+            self.host_out[slot] = cur
+        return cur
+
+    def _launch(self, group, k):
+        torch = self.torch
+        s = self.streams[k]
+        if self.stream_event[k] is not None:      # descriptor buffers of stream k are free again
+            self.stream_event[k].synchronize()
+        items = (hf.hf_batch_item * len(group))()
+        for n, (req, slot) in enumerate(group):
+            v = self.r.views[slot]
+            items[n] = hf.hf_batch_item(self.r.ctx.value, slot, 0, v["t"].data_ptr(), v["hit"].data_ptr())
+        dev_bytes, host_bytes = hf.hf_batch_query_bytes(items, self.flags)
+        if dev_bytes > self.dev_desc[k].numel() or host_bytes > self.host_desc[k].numel():
+            self.host_desc[k] = torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True)
+            self.dev_desc[k] = torch.empty(dev_bytes, dtype=torch.uint8, device=self.r.device)
+        hf.hf_frame_batch(items, self.flags, self.host_desc[k], self.dev_desc[k], s)
+        with torch.cuda.stream(s):
+            for req, slot in group:
+                v = self.r.views[slot]
+                n = req.camera.width * req.camera.height
+                ht, hh = self._host_outputs(slot, req.camera)
+                ht[:n].copy_(v["t"][:n], non_blocking=True)
+                hh[:n].copy_(v["hit"][:n], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(s)
+        self.stream_event[k] = ev
+        return ev
+
+    def run(self, requests, realtime: bool = True, idle_sleep: float = 5e-5) -> dict:
+        """Serve `requests` (sorted by arrival).  With realtime=False all
+        requests are available at once (a throughput run)."""
+        waiting = collections.deque()
+        inflight = []
+        lat, admitted_at, mem = {}, {}, {}
+        results = {}
+        nxt, k_stream, groups = 0, 0, 0
+        sizes = []
+        t0 = time.perf_counter()
+        n = len(requests)
+        while len(lat) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and (not realtime or requests[nxt].arrival <= now):
+                waiting.append(requests[nxt])
+                nxt += 1
+            still = []
+            for ev, group in inflight:
+                if ev.query():
+                    done = time.perf_counter() - t0
+                    for req, slot in group:
+                        lat[req.rid] = done - (req.arrival if realtime else 0.0)
+                        if self.keep_results:
+                            c = req.camera
+                            ht, hh = self.host_out[slot]
+                            results[req.rid] = (ht[:c.width * c.height].numpy().copy(),
+                                                hh[:c.width * c.height].numpy().copy())
+                        self.arena.release(mem[req.rid], self.request_bytes(req.camera))
+                        self.free_slots.append(slot)
+                else:
+                    still.append((ev, group))
+            inflight = still
+            group = []
+            while waiting and self.free_slots and len(group) < self.max_group:
+                need = self.request_bytes(waiting[0].camera)
+                if need > self.budget:
+                    raise ValueError(f"request {waiting[0].rid} needs {need} bytes, over the budget")
+                off = self.arena.alloc(need)
+                if off is None:
+                    break
+                req = waiting.popleft()
+                slot = self.free_slots.pop()
+                mem[req.rid] = off
+                self.max_used = max(self.max_used, self.arena.used())
+                self._bind(req, slot, off)
+                admitted_at[req.rid] = time.perf_counter() - t0
+                group.append((req, slot))
+            if group:
+                inflight.append((self._launch(group, k_stream), group))
+                k_stream = (k_stream + 1) % len(self.streams)
+                groups += 1
+                sizes.append(len(group))
+            elif inflight or nxt < n:
+                time.sleep(idle_sleep)
+        wall = time.perf_counter() - t0
+        self.r.sync()
+        vals = sorted(lat.values())
+        out = {"requests": n, "wall_s": wall, "frames_per_s": n / wall,
+               "p50_ms": 1e3 * statistics.median(vals), "p99_ms": 1e3 * vals[min(n - 1, int(0.99 * n))],
+               "mean_ms": 1e3 * statistics.mean(vals), "groups": groups,
+               "mean_group": statistics.mean(sizes) if sizes else 0.0,
+               "max_memory_used": self.max_used, "memory_budget": self.budget}
+        if self.keep_results:
+            out["results"] = results
+        return out

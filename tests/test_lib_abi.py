@@ -228,3 +228,15 @@ def test_reduced_precision_offset_limits(hfmod, tiny):
     with pytest.raises(hfmod.HFError) as e:
         hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(1.5, 40.0, 2, -1))
     assert e.value.code == hfmod.HF_ERR_ARG and "BF16" in str(e.value)
+
+
+def test_arena_first_fit_and_merge():
+    from paper_2201_10887_gb300.serving import Arena
+    a = Arena(10_000)
+    x, y = a.alloc(1000), a.alloc(3000)
+    assert (x, y) == (0, 1024) and a.alloc(6000) is None
+    a.release(y, 3000)
+    assert a.alloc(2000) == 1024
+    a.release(x, 1000)
+    a.release(1024, 2000)
+    assert a.free == [(0, 10_000)] and a.used() == 0

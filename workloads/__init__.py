@@ -16,10 +16,11 @@ several levels as in Table 1.
 from .fbm import FBm
 from .quadtree import Quadtree, random_split_quadtree, curvature_quadtree
 from .cameras import Camera, fixed_camera, flight_path
-from .configs import tiny_config, dem_config, precision_config, batch_config
+from .configs import (tiny_config, dem_config, precision_config, batch_config, serve_config,
+                      Request)
 
 __all__ = [
     "FBm", "Quadtree", "random_split_quadtree", "curvature_quadtree",
     "Camera", "fixed_camera", "flight_path",
-    "tiny_config", "dem_config", "precision_config", "batch_config",
+    "tiny_config", "dem_config", "precision_config", "batch_config", "serve_config", "Request",
 ]

@@ -13,6 +13,10 @@
   origin of (5e6, 5e6) m, which FP32 cannot hold to centimetres.
 * ``batch_config``: independent tiles of uneven finest size with 1-4
   cascades each and a 960 x 540 view per tile.
+* ``serve_config``: a 16384^2-equivalent quadtree (6 levels, 10-320 m cells,
+  fBm amplitude 3000 m, a mosaic of curvature-refined blocks) kept resident,
+  and a Poisson stream of view requests (rate 200/s) of 1280 x 720,
+  1920 x 1080 or 3840 x 2160 with 2-6 cascades of 2048^2.
 
 All use a Gaussian RBF with sigma = 1.5 cell sizes truncated at 3 cell sizes.
 """
@@ -25,7 +29,7 @@ import numpy as np
 
 from .cameras import Camera, fixed_camera, flight_path
 from .fbm import FBm
-from .quadtree import Quadtree, curvature_quadtree, random_split_quadtree
+from .quadtree import Quadtree, curvature_quadtree, random_split_quadtree, tiled_curvature_quadtree
 
 RBF_SIGMA = 1.5
 RBF_RADIUS = 3.0
@@ -89,3 +93,32 @@ def batch_config(seed: int = 4, n_tiles: int = 64, min_side: int = 256,
                           split_lambda=0.5)[0]
         scenes.append(Scene(f"tile{t}", tree, fbm, RBF_SIGMA, RBF_RADIUS, [cam]))
     return scenes
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float        # seconds from the start of the stream
+    camera: Camera
+
+
+def serve_config(seed: int = 5, blocks: int = 4, leaves_per_block: int = 2_500_000,
+                 block_root: int = 128, rate: float = 200.0, duration: float = 2.0,
+                 cascade_size: int = 2048) -> tuple:
+    """(Scene, requests): the resident quadtree and the request stream."""
+    span = blocks * block_root * 320.0
+    fbm = FBm(seed, amplitude=3000.0, wavelength=span / 8)
+    tree = tiled_curvature_quadtree(blocks, block_root, 320.0, 5, fbm, leaves_per_block, seed)
+    rng = np.random.default_rng(seed)
+    n = int(rng.poisson(rate * duration))
+    arrivals = np.sort(rng.uniform(0.0, duration, n))
+    resolutions = [(1280, 720), (1920, 1080), (3840, 2160)]
+    path = flight_path(tree, fbm, seed, max(n, 2), 16, 16, 2, cascade_size, split_lambda=0.5,
+                       n_waypoints=12)
+    reqs = []
+    for k in range(n):
+        w, h = resolutions[int(rng.integers(0, 3))]
+        cam = path[int(rng.integers(0, len(path)))].with_(width=w, height=h,
+                                                          n_cascades=int(rng.integers(2, 7)))
+        reqs.append(Request(k, float(arrivals[k]), cam))
+    return Scene("serve", tree, fbm, RBF_SIGMA, RBF_RADIUS, []), reqs

@@ -110,15 +110,16 @@ def _block_max(a: np.ndarray, b: int) -> np.ndarray:
 
 def curvature_quadtree(root_nx: int, root_ny: int, root_cell: float, max_level: int,
                        fbm: FBm, target_leaves: int, seed: int,
-                       origin=(0.0, 0.0), shuffle=False) -> Quadtree:
+                       origin=(0.0, 0.0), shuffle=False, fbm_offset=(0.0, 0.0)) -> Quadtree:
     """Refine a node wherever the largest |Laplacian| of the terrain over its
     footprint exceeds one threshold; the threshold is bisected so that the
-    leaf count is close to ``target_leaves``."""
+    leaf count is close to ``target_leaves``.  The terrain is sampled at
+    ``fbm_offset`` + domain-local coordinates."""
     fine = 1 << max_level
     fnx, fny = root_nx * fine, root_ny * fine
     cf = root_cell / fine
-    xs = (np.arange(fnx) + 0.5) * cf
-    ys = (np.arange(fny) + 0.5) * cf
+    xs = fbm_offset[0] + (np.arange(fnx) + 0.5) * cf
+    ys = fbm_offset[1] + (np.arange(fny) + 0.5) * cf
     h = fbm.grid(xs, ys)
     hp = np.pad(h, 1, mode="edge")
     lap = np.abs(hp[1:-1, 2:] + hp[1:-1, :-2] + hp[2:, 1:-1] + hp[:-2, 1:-1]
@@ -160,7 +161,30 @@ def curvature_quadtree(root_nx: int, root_ny: int, root_cell: float, max_level: 
             val_out.append(h[iy, ix].astype(np.float32))
         else:
             c = root_cell / (1 << L)
-            val_out.append(fbm((ix + 0.5) * c, (iy + 0.5) * c).astype(np.float32))
+            val_out.append(fbm(fbm_offset[0] + (ix + 0.5) * c,
+                               fbm_offset[1] + (iy + 0.5) * c).astype(np.float32))
     return _finish(origin, root_cell, root_nx, root_ny, max_level,
                    np.concatenate(lv_out), np.concatenate(ix_out),
                    np.concatenate(iy_out), np.concatenate(val_out), seed, shuffle)
+
+
+def tiled_curvature_quadtree(blocks: int, block_root: int, root_cell: float, max_level: int,
+                             fbm: FBm, leaves_per_block: int, seed: int) -> Quadtree:
+    """A blocks x blocks mosaic of curvature-refined blocks of one continuous
+    terrain (each block refined with its own threshold), for domains too
+    large to sample at the finest level at once."""
+    parts = []
+    span = block_root * root_cell
+    for by in range(blocks):
+        for bx in range(blocks):
+            t = curvature_quadtree(block_root, block_root, root_cell, max_level, fbm,
+                                   leaves_per_block, seed + by * blocks + bx,
+                                   fbm_offset=(bx * span, by * span))
+            shift = (block_root << t.level.astype(np.int64))
+            parts.append((t.level, t.ix + bx * shift, t.iy + by * shift, t.value))
+    level = np.concatenate([p[0] for p in parts])
+    ix = np.concatenate([p[1] for p in parts])
+    iy = np.concatenate([p[2] for p in parts])
+    value = np.concatenate([p[3] for p in parts])
+    return _finish((0.0, 0.0), root_cell, blocks * block_root, blocks * block_root, max_level,
+                   level, ix, iy, value, seed, False)

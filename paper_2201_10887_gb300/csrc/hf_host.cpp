@@ -703,8 +703,14 @@ RayParams ray_params(const ViewSlot* v) {
         rp.R[a] = float(f.R[a]);
         rp.U[a] = float(f.U[a]);
     }
-    rp.tan_v = float(std::tan(0.5 * c.vfov));
-    rp.tan_h = float(std::tan(0.5 * c.vfov) * double(c.width) / double(c.height));
+    {
+        // pixel centre x + 1/2 maps to (2 (x + 1/2) / W - 1) tan_h, y + 1/2 to (1 - 2 (y + 1/2) / H) tan_v
+        const double tv = std::tan(0.5 * c.vfov), th = tv * double(c.width) / double(c.height);
+        rp.px_a = float(2.0 * th / c.width);
+        rp.px_b = float(th * (1.0 / c.width - 1.0));
+        rp.py_a = float(-2.0 * tv / c.height);
+        rp.py_b = float(tv * (1.0 - 1.0 / c.height));
+    }
     rp.dir2x = float(f.dir2[0]);
     rp.dir2y = float(f.dir2[1]);
     rp.znear = float(c.znear);

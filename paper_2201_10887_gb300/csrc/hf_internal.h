@@ -143,7 +143,7 @@ struct RayParams {
     int32_t C, W, H;
     float ez;                // eye height (m)
     float F[3], R[3], U[3];  // camera basis
-    float tan_h, tan_v;
+    float px_a, px_b, py_a, py_b;  // screen coordinates: s = fma(pixel, a, b), s in [-tan, tan]
     float dir2x, dir2y;      // normalised ground projection of the view
     float znear, zfar;
     RayCascade cas[HF_MAX_CASCADES];

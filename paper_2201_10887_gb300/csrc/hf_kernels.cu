@@ -729,12 +729,40 @@ int launch_maxmip(const MipParams& p, void* stream) {
 // current level-0 patch is tracked in integers, so rounding can never move
 // the walk backwards; after a step the walk climbs one level when it has left
 // its parent node.  The segment above the cascade's global maximum (the top
-// mip entry) is skipped before the walk starts.
+// mip entry) is skipped before the walk starts, and the walk starts at level
+// kRayStartLevel (64 x 64 patches) rather than at the single top node: on the
+// flight-path views this removes about a fifth of the node visits (the
+// descent through the top levels) and cannot change the first hit, since the
+// walk still climbs to any level above where it may skip.
 //
 // Per-step arithmetic is kept small: exit times are fma(boundary, 1/d, -e/d)
 // with 1/d = 0, -e/d = +inf for an axis-parallel ray (no branch), integer
 // node boundaries become floats through the exact 2^23 bit trick, level
 // offsets come from shared memory, and all divisions happen once per ray.
+// Screen coordinates are one fma per axis with host-computed scales.  The
+// per-ray reciprocals of the direction and the divisions and square root of
+// the patch root use the hardware approximations (rcp.approx, div.approx,
+// sqrt.approx: a few ulp): the walk only needs its exit times to be
+// consistent with one another, which they are whatever 1/d is, and a root
+// error of a few ulp of t is far inside the ray tolerance.  The reciprocal
+// used to clip the ray at the cascade maximum stays correctly rounded.
+// Sums that carry a tolerance are written with __fadd_rn (and the blend depth
+// with __fmul_rn / __fsub_rn) so that no copy of this code is contracted into
+// an FMA differently from another: per-view and batched launches then agree
+// bit for bit.
+
+constexpr int kRayStartLevel = 6;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 __device__ __forceinline__ float exact_float(int x) {  // 0 <= x < 2^23
     return __int_as_float(x | 0x4B000000) - 8388608.0f;
@@ -766,17 +794,18 @@ __device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, 
     float tau = INFINITY;
     if (A == 0.f) {
         if (B != 0.f) {
-            const float x = -C / B;
-            if (x >= -slack && x <= dt + slack) tau = x;
+            const float x = __fdividef(-C, B);
+            if (x >= -slack && x <= __fadd_rn(dt, slack)) tau = x;
         }
     } else {
         const float disc = fmaf(B, B, -4.f * A * C);
         if (disc >= 0.f) {
-            const float s = sqrtf(disc);
+            const float s = sqrt_approx(disc);
             const float qq = -0.5f * (B + copysignf(s, B));
-            const float x1 = qq / A, x2 = (qq != 0.f) ? C / qq : x1;
-            if (x1 >= -slack && x1 <= dt + slack) tau = x1;
-            if (x2 >= -slack && x2 <= dt + slack) tau = fminf(tau, x2);
+            const float x1 = __fdividef(qq, A), x2 = (qq != 0.f) ? __fdividef(C, qq) : x1;
+            const float hi = __fadd_rn(dt, slack);
+            if (x1 >= -slack && x1 <= hi) tau = x1;
+            if (x2 >= -slack && x2 <= hi) tau = fminf(tau, x2);
         }
     }
     if (tau == INFINITY) return false;
@@ -821,7 +850,7 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
     const float slack = 2e-6f * fabsf(top);
     int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
-    int k = K;
+    int k = min(K, kRayStartLevel);
     float t = ta;
     const int budget = 8 * (2 * N + 8) * (K + 2);
     for (int it = 0; it < budget; ++it) {
@@ -832,7 +861,7 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
         const float zmin = fmaf(zneg ? te : t, r.dz, ez);
         const float mx = ldc<COH>(c.mip + off[k] + nj * (P >> k) + ni);
         if (COUNT) ++visits;
-        if (zmin <= mx + slack) {
+        if (zmin <= __fadd_rn(mx, slack)) {
             if (k > 0) {
                 --k;
                 continue;
@@ -912,24 +941,24 @@ template <bool COUNT, bool COH>
 __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_off)[kMaxLevels], DevStatus* status,
                                               int x, int y, unsigned& visits, unsigned& tests) {
     if (x >= p.W || y >= p.H) return;
-    const float sx = (2.f * (float(x) + 0.5f) / float(p.W) - 1.f) * p.tan_h;
-    const float sy = (1.f - 2.f * (float(y) + 0.5f) / float(p.H)) * p.tan_v;
-    float dx = p.F[0] + sx * p.R[0] + sy * p.U[0];
-    float dy = p.F[1] + sx * p.R[1] + sy * p.U[1];
-    float dz = p.F[2] + sx * p.R[2] + sy * p.U[2];
+    const float sx = fmaf(float(x), p.px_a, p.px_b);
+    const float sy = fmaf(float(y), p.py_a, p.py_b);
+    float dx = fmaf(sy, p.U[0], fmaf(sx, p.R[0], p.F[0]));
+    float dy = fmaf(sy, p.U[1], fmaf(sx, p.R[1], p.F[1]));
+    float dz = fmaf(sy, p.U[2], fmaf(sx, p.R[2], p.F[2]));
     const float il = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     RayDir d;
     d.dx = dx * il;
     d.dy = dy * il;
     d.dz = dz * il;
-    d.rdx = d.dx != 0.f ? __frcp_rn(d.dx) : 0.f;
-    d.rdy = d.dy != 0.f ? __frcp_rn(d.dy) : 0.f;
+    d.rdx = d.dx != 0.f ? rcp_approx(d.dx) : 0.f;
+    d.rdy = d.dy != 0.f ? rcp_approx(d.dy) : 0.f;
     d.rdz = d.dz != 0.f ? __frcp_rn(d.dz) : 0.f;
-    const float rfd = __frcp_rn(fmaf(d.dx, p.F[0], fmaf(d.dy, p.F[1], d.dz * p.F[2])));
+    const float rfd = rcp_approx(fmaf(d.dx, p.F[0], fmaf(d.dy, p.F[1], d.dz * p.F[2])));
     d.tmin = p.znear * rfd;
     d.tmax = p.zfar * rfd;
     d.ks = fmaf(d.dx, p.dir2x, d.dy * p.dir2y);
-    d.rks = d.ks != 0.f ? __frcp_rn(d.ks) : 0.f;
+    d.rks = d.ks != 0.f ? rcp_approx(d.ks) : 0.f;
     const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
     int hit = 0;
     float t = __int_as_float(0x7fc00000);
@@ -940,14 +969,14 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
         if (!trace_cascade<COUNT, COH>(cc, s_off[c], d, p.ez, ta, tb, tc, status, pix, visits, tests)) continue;
         hit = 1 + c;
         t = tc;
-        const float s = tc * d.ks;
+        const float s = __fmul_rn(tc, d.ks);
         if (c + 1 < p.C) {
             const RayCascade& cn = p.cas[c + 1];
             if (s >= cn.near_d && cc.far_ext > cn.near_d) {
                 float ta2, tb2, t2;
                 if (cascade_interval(cn, d, ta2, tb2) &&
                     trace_cascade<COUNT, COH>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, status, pix, visits, tests)) {
-                    const float al = fminf(fmaxf((s - cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
+                    const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
                     t = fmaf(al, t2 - tc, tc);
                 }
             }

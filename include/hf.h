@@ -90,12 +90,21 @@ typedef struct {
  * square "bucket": every leaf at or below level bucket_level is a bucket,
  * coarser leaves are split into their level-bucket_level descendants so a
  * list never covers more than one level-bucket_level cell.  bucket_level
- * = -1 selects max(0, max_level - 2). */
+ * = -1 selects max(0, max_level - 2).
+ * water = 1 adds the water layer (Section 2: the input is a terrain model
+ * plus relative water depths at the cells of the same adaptive grid; Table 1
+ * times the approximation of both): every leaf also carries a depth >= 0
+ * (hf_update_water, initially 0), each cascade gets a second texture holding
+ * the water surface, and rays stop at whichever surface they meet first.  The
+ * water layer needs precision HF_PREC_FP32 and is not available in batched
+ * frames; hf_discretize_noalloc ignores it.  reserved must be 0. */
 typedef struct {
     double sigma;
     double radius;
     int32_t precision;
     int32_t bucket_level;
+    int32_t water;
+    int32_t reserved;
 } hf_rbf_params;
 
 /* A view (Section 3, Section 5).  eye is in world coordinates; forward and
@@ -127,6 +136,7 @@ typedef struct {
     float* mip;                                  /* device, max mipmap (see hf_build_maxmip) */
     int32_t* spans;                              /* device, N rows x {first, last} visible column; last < first = none */
     int64_t mip_floats;                          /* number of floats in mip */
+    float* water_tex;                            /* device, N*N FP32 water surface, -inf where dry or invisible; NULL without the water layer */
 } hf_cascade_info;
 
 typedef struct hf_ctx hf_ctx;
@@ -141,9 +151,10 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
                        const hf_rbf_params* rbf, hf_ctx** out);
 
 /* Device bytes the caller must provide: persistent_bytes for
- * hf_bind_persistent (quadtree + influence lists), per_view_bytes for one
- * hf_set_camera with n_cascades textures of cascade_size^2 texels.  Either
- * output pointer may be NULL. */
+ * hf_bind_persistent (quadtree + influence lists, + 4 bytes per leaf for the
+ * water depths), per_view_bytes for one hf_set_camera with n_cascades
+ * textures of cascade_size^2 texels (a second texture per cascade with the
+ * water layer).  Either output pointer may be NULL. */
 int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
                    size_t* persistent_bytes, size_t* per_view_bytes);
 
@@ -158,6 +169,16 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
  * hf_create_quadtree.  Enqueued on `stream`. */
 int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* stream);
 
+/* Water layer only (hf_rbf_params.water = 1): sets the leaves' relative
+ * water depths (Section 2), a host array in the order of the leaves given to
+ * hf_create_quadtree; every depth must be finite and >= 0 (HF_ERR_ARG).  The
+ * same RBF weights that give the terrain height v at a texel give its depth
+ * d = sum w_i d_i / sum w_i; the texel's water surface is v + d where d > 0,
+ * else -inf (dry).  The cascade fit afterwards covers terrain + depth.
+ * HF_ERR_STATE for a context without the water layer.  Uploads on `stream`
+ * and waits for it. */
+int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* stream);
+
 /* Fits the cascades of `cam` (Section 3) on the host in FP64 and binds
  * dev_view (>= per_view_bytes for cam's cascade settings, 256-byte aligned)
  * to view slot `view_slot` (0..HF_MAX_VIEWS-1).  Host work only. */
@@ -166,7 +187,8 @@ int hf_set_camera(hf_ctx* ctx, int32_t view_slot, const hf_camera* cam, void* de
 
 /* Step 1 (Section 3 mask, Section 4 Eq. 2): computes the visible-texel rows
  * of every cascade and evaluates the RBF approximation at every visible
- * texel; invisible texels are set to -infinity. */
+ * texel; invisible texels are set to -infinity.  With the water layer the
+ * same pass also writes the water surface textures (hf_update_water). */
 int hf_discretize_cascades(hf_ctx* ctx, int32_t view_slot, void* stream);
 
 /* Step 2a (Section 5, maximum mipmap of Tevs et al.): level 0 holds, per
@@ -174,7 +196,9 @@ int hf_discretize_cascades(hf_ctx* ctx, int32_t view_slot, void* stream);
  * or -inf if a corner is invisible; patches are padded with -inf to P x P,
  * P the smallest power of two >= N-1; level k (P>>k)^2 entries hold the
  * maximum of 2x2 entries of level k-1; levels are stored one after another,
- * row-major. */
+ * row-major.  With the water layer one mipmap bounds both surfaces: a
+ * level-0 entry is the larger of the terrain patch's maximum and the water
+ * patch's (a water patch exists where its four corners are wet). */
 int hf_build_maxmip(hf_ctx* ctx, int32_t view_slot, void* stream);
 
 /* Step 2b (Section 5): one ray per pixel, nearest cascade first; writes
@@ -182,7 +206,11 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t view_slot, void* stream);
  * miss) and hit_dev[y*width + x] = 0 on a miss, else 1 + the index of the
  * first cascade hit.  Pixel (0, 0) is the top-left corner.  In the overlap
  * of cascades c and c+1 both are intersected and the hit distances are
- * blended linearly across the overlap band. */
+ * blended linearly across the overlap band.  With the water layer a ray
+ * stops, inside each cascade, at whichever surface it meets first (the
+ * water surface on a tie), and that per-cascade hit is what gets blended;
+ * bit 0x80 of hit_dev marks a first-hit cascade whose hit is on the water
+ * surface, the low bits still hold 1 + that cascade's index. */
 int hf_raycast(hf_ctx* ctx, int32_t view_slot, float* t_dev, uint8_t* hit_dev, void* stream);
 
 /* Descriptor and device pointers of cascade c of a view slot. */

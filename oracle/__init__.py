@@ -7,6 +7,7 @@ baseline may import this package; the product library never does.
 
 from __future__ import annotations
 
+import copy
 import ctypes as ct
 import os
 import subprocess
@@ -190,6 +191,27 @@ def texel_heights(cas: CascadeC, cells: Cells, sigma, radius, ii=None, jj=None) 
     return out
 
 
+def depth_cells(cells: Cells, depths) -> Cells:
+    """The same cells carrying the water depths (leaf order) as their values."""
+    c = copy.copy(cells)
+    c.cv = np.ascontiguousarray(np.asarray(depths, np.float32), np.float64)
+    return c
+
+
+def water_heights(cas: CascadeC, cells: Cells, depths, sigma, radius, ii=None, jj=None):
+    """Terrain height v, discretized depth d and water surface at texels.
+
+    Section 2: terrain values and relative water depths live on the same
+    cells, and both are approximated by Eq. 2 (so with the same weights).
+    Reading: the texel's water surface is v + d where d > 0 (some
+    influencing cell is wet), else -inf (dry); invisible texels are -inf."""
+    v = texel_heights(cas, cells, sigma, radius, ii, jj)
+    d = texel_heights(cas, depth_cells(cells, depths), sigma, radius, ii, jj)
+    with np.errstate(invalid="ignore"):
+        w = np.where(np.isfinite(v) & (d > 0), v + d, -np.inf)
+    return v, d, w
+
+
 def maxmip(tex: np.ndarray) -> np.ndarray:
     tex = np.ascontiguousarray(tex, np.float32)
     N = tex.shape[-1]
@@ -225,22 +247,31 @@ def rcascades(cascades) -> "ct.Array":
     return arr
 
 
-def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0):
+def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0, water_textures=None):
     """Cast rays for ``pixels`` (arrays px, py) or the whole image.
 
-    Returns t (world distance), hit (0 miss, 1 + first cascade hit),
-    seg (length of the first-hit cascade's ray segment), visits."""
+    Returns t (world distance), hit (0 miss, 1 + first cascade hit, + 0x80
+    when that hit is on the water surface), seg (length of the first-hit
+    cascade's ray segment), visits.  ``water_textures`` (one per cascade)
+    adds the water surface: inside each cascade the first surface met wins."""
     C = len(cascades)
     rc = rcascades(cascades)
     texs = [np.ascontiguousarray(t, np.float32) for t in textures]
     tp = (ct.POINTER(ct.c_float) * C)(*[_p(t, ct.c_float) for t in texs])
+    if water_textures is not None:
+        if mode != 0:
+            raise ValueError("the water surface is traced by the DDA (mode 0)")
+        wts = [np.ascontiguousarray(t, np.float32) for t in water_textures]
+        wp = (ct.POINTER(ct.c_float) * C)(*[_p(t, ct.c_float) for t in wts])
+    else:
+        wp = None
     if mips is not None:
         ms = [np.ascontiguousarray(m, np.float32) for m in mips]
         mp = (ct.POINTER(ct.c_float) * C)(*[_p(m, ct.c_float) for m in ms])
     else:
         if mode == 1:
             raise ValueError("mip traversal needs the max mipmaps")
-        mp = (ct.POINTER(ct.c_float) * C)()
+        mp = None
     if pixels is None:
         py, px = np.meshgrid(np.arange(cam.height, dtype=np.int32),
                              np.arange(cam.width, dtype=np.int32), indexing="ij")
@@ -254,10 +285,23 @@ def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0):
     seg = np.empty(m)
     visits = np.empty(m, np.int64)
     c = camera_struct(cam, tree)
-    lib().orc_raycast(ct.byref(c), rc, ct.c_int(C), tp, mp, _p(px, ct.c_int), _p(py, ct.c_int),
+    lib().orc_raycast(ct.byref(c), rc, ct.c_int(C), tp, wp, mp, _p(px, ct.c_int), _p(py, ct.c_int),
                       ct.c_long(m), ct.c_int(mode), _p(t, ct.c_double), _p(hit, ct.c_int),
                       _p(seg, ct.c_double), _p(visits, ct.c_longlong))
     return t, hit, seg, visits
+
+
+def raycast_water(cam, tree, cascades, terrain_textures, water_textures, pixels=None):
+    """Terrain and water surface together (t, hit, seg): see ``raycast``."""
+    t, hit, seg, _ = raycast(cam, tree, cascades, terrain_textures, pixels=pixels,
+                             water_textures=water_textures)
+    return t, hit, seg
+
+
+def maxmip_pair(tex: np.ndarray, wtex: np.ndarray) -> np.ndarray:
+    """Max mipmap bounding both surfaces: the entrywise larger of the two
+    surfaces' max mipmaps (max commutes with the 2x2 reductions)."""
+    return np.maximum(maxmip(tex), maxmip(wtex))
 
 
 def threads() -> int:

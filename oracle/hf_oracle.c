@@ -707,16 +707,40 @@ static int cascade_interval(const orc_rcascade* c, const prj_ray* r, double ks, 
     return lo <= hi;
 }
 
+/* First hit on [ta, tb] inside one cascade.  Without a water texture this is
+ * the terrain's first hit.  With one (the water layer: terrain and water
+ * depths on the same cells, Section 2) the ray meets whichever surface comes
+ * first: the nearer of the terrain's and the water surface's first hits, the
+ * water surface on a tie; *on_water says which.  A water patch exists where
+ * its four corners are wet (finite), as a terrain patch needs four visible
+ * corners.                                                                 */
+static int trace_cascade(const float* tex, const float* wtex, const float* mip, int N,
+                         const prj_ray* r, double ta, double tb, int mode, double* t_hit,
+                         int* on_water, long long* visits) {
+    double t1 = 0.0, t2 = 0.0;
+    int h1 = mode == 0 ? trace_dda(tex, N, r, ta, tb, &t1, visits)
+                       : trace_mip(tex, mip, N, r, ta, tb, &t1, visits);
+    int h2 = wtex ? trace_dda(wtex, N, r, ta, tb, &t2, visits) : 0;
+    *on_water = h2 && (!h1 || t2 <= t1);
+    if (*on_water) {
+        *t_hit = t2;
+        return 1;
+    }
+    if (h1) *t_hit = t1;
+    return h1;
+}
+
 /* One ray per pixel through the cascades, nearest first (Section 5).
  * Reading of the blend: if cascade c is hit at projected depth s inside its
  * overlap with cascade c+1, cascade c+1 is traced too and, if it is hit,
  * t = (1 - alpha) t_c + alpha t_{c+1} with alpha rising linearly from 0 to 1
  * across the overlap band; otherwise the single hit is kept.  The result
- * reports the first cascade that was hit.                                 */
+ * reports the first cascade that was hit, with 0x80 added when that
+ * cascade's hit is on the water surface (wtex given).                      */
 void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
-                 const float* const* tex, const float* const* mip, const int* pxs,
-                 const int* pys, long m, int mode, double* t_out, int* hit_out, double* seg_out,
-                 long long* visits_out) {
+                 const float* const* tex, const float* const* wtex, const float* const* mip,
+                 const int* pxs, const int* pys, long m, int mode, double* t_out, int* hit_out,
+                 double* seg_out, long long* visits_out) {
     double F[3], U[3], R[3], dir2[2];
     camera_basis(cam, F, U, R);
     view_dir2(F, U, dir2);
@@ -738,11 +762,12 @@ void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
             prj_ray r = {(cam->eye[0] - cas[c].ox) / cas[c].h, (cam->eye[1] - cas[c].oy) / cas[c].h,
                          cam->eye[2], d[0] / cas[c].h, d[1] / cas[c].h, d[2]};
             double ta, tb, tc;
+            int wet = 0;
             if (!cascade_interval(&cas[c], &r, ks, tmin, tmax, &ta, &tb)) continue;
-            int h = mode == 0 ? trace_dda(tex[c], cas[c].N, &r, ta, tb, &tc, &visits)
-                              : trace_mip(tex[c], mip[c], cas[c].N, &r, ta, tb, &tc, &visits);
-            if (!h) continue;
-            hit = 1 + c;
+            if (!trace_cascade(tex[c], wtex ? wtex[c] : NULL, mip ? mip[c] : NULL, cas[c].N, &r, ta, tb,
+                               mode, &tc, &wet, &visits))
+                continue;
+            hit = (1 + c) | (wet ? 0x80 : 0);
             t = tc;
             seg = tb - ta;
             double s = tc * ks;
@@ -751,9 +776,10 @@ void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
                 prj_ray r2 = {(cam->eye[0] - n2->ox) / n2->h, (cam->eye[1] - n2->oy) / n2->h,
                               cam->eye[2], d[0] / n2->h, d[1] / n2->h, d[2]};
                 double ta2, tb2, t2;
+                int wet2 = 0;
                 if (cascade_interval(n2, &r2, ks, tmin, tmax, &ta2, &tb2)) {
-                    int h2 = mode == 0 ? trace_dda(tex[c + 1], n2->N, &r2, ta2, tb2, &t2, &visits)
-                                       : trace_mip(tex[c + 1], mip[c + 1], n2->N, &r2, ta2, tb2, &t2, &visits);
+                    int h2 = trace_cascade(tex[c + 1], wtex ? wtex[c + 1] : NULL, mip ? mip[c + 1] : NULL,
+                                           n2->N, &r2, ta2, tb2, mode, &t2, &wet2, &visits);
                     if (h2) {
                         double al = (s - n2->near_) / (cas[c].far_ext - n2->near_);
                         al = al < 0.0 ? 0.0 : (al > 1.0 ? 1.0 : al);

@@ -101,13 +101,15 @@ void orc_maxmip(const float* tex, int N, float* mip);
 /* first root of bilinear(a,b) - z along a ray segment inside one patch */
 int orc_ray_patch(double h00, double h10, double h01, double h11, double a0, double b0,
                   double z0, double da, double db, double dz, double dt, double* tau);
-/* mode 0: per-patch DDA; mode 1: max-mip traversal (needs mips); outputs per pixel:
- * t (world distance from the eye), hit (0 = miss, 1 + first cascade hit),
+/* mode 0: per-patch DDA; mode 1: max-mip traversal (needs mips) of the terrain;
+ * wtex (NULL = none): water surface textures, traced by DDA, the first surface met
+ * wins inside each cascade.  Outputs per pixel: t (world distance from the eye),
+ * hit (0 = miss, 1 + first cascade hit, + 0x80 if that hit is on the water surface),
  * seg (length of the first-hit cascade's ray segment), visits (mip nodes tested) */
 void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
-                 const float* const* tex, const float* const* mip, const int* pxs,
-                 const int* pys, long m, int mode, double* t, int* hit, double* seg,
-                 long long* visits);
+                 const float* const* tex, const float* const* wtex, const float* const* mip,
+                 const int* pxs, const int* pys, long m, int mode, double* t, int* hit,
+                 double* seg, long long* visits);
 int orc_threads(void);
 
 #ifdef __cplusplus

@@ -113,6 +113,7 @@ struct ViewSlot {
     size_t bytes = 0;
     float* tex[HF_MAX_CASCADES] = {};
     float* mip[HF_MAX_CASCADES] = {};
+    float* wtex[HF_MAX_CASCADES] = {};  // water surface (water layer only)
     int2* spans[HF_MAX_CASCADES] = {};
     float* xs[HF_MAX_CASCADES] = {};
     float* ys[HF_MAX_CASCADES] = {};
@@ -122,6 +123,7 @@ struct ViewSlot {
 struct PersistentLayout {
     size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx;
     size_t pair_offsets, coords, values;  // reduced-precision lists (0 bytes for FP32)
+    size_t depth;                         // water depths (0 bytes without the water layer)
     size_t total;
 };
 
@@ -141,6 +143,7 @@ struct hf_ctx {
     std::vector<int64_t> pair_offsets;  // n_buckets + 1 (reduced precision only)
     int64_t n_pairs = 0;
     std::vector<float> staged;     // values in sorted order for hf_update_values
+    std::vector<float> depth;      // water depths in sorted order (water layer only)
     char* dev = nullptr;
     size_t dev_bytes = 0;
     PersistentLayout lay{};
@@ -161,6 +164,7 @@ struct hf_ctx {
         l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
         l.coords = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
         l.values = o; o = align256(o + (compact ? size_t(n_pairs) * 8 : 0));
+        l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves) * 4 : 0));
         l.total = o;
         return l;
     }
@@ -200,17 +204,19 @@ struct hf_ctx {
         v.offsets = reinterpret_cast<const int64_t*>(dev + lay.offsets);
         v.idx = reinterpret_cast<int32_t*>(dev + lay.idx);
         v.recs = reinterpret_cast<float4*>(dev + lay.recs);
+        v.depth = rbf.water ? reinterpret_cast<const float*>(dev + lay.depth) : nullptr;
         return v;
     }
 };
 
 namespace {
 
-size_t per_view_bytes(int C, int N) {
+size_t per_view_bytes(int C, int N, bool water) {
     size_t o = 0;
     for (int c = 0; c < C; ++c) {
         o = align256(o + size_t(N) * N * 4);
         o = align256(o + size_t(mip_floats(N)) * 4);
+        if (water) o = align256(o + size_t(N) * N * 4);
         o = align256(o + size_t(N) * 8);
         o = align256(o + size_t(N) * 4);
         o = align256(o + size_t(N) * 4);
@@ -306,6 +312,7 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
             info_out[k].mip = nullptr;
             info_out[k].spans = nullptr;
             info_out[k].mip_floats = mip_floats(N);
+            info_out[k].water_tex = nullptr;
         }
     }
     *lt = ctx->lookup_tables(true);
@@ -340,6 +347,10 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     if (rbf->precision < HF_PREC_FP32 || rbf->precision > HF_PREC_BF16)
         return fail(HF_ERR_ARG, "unknown precision %d", rbf->precision);
     if (rbf->bucket_level > M) return fail(HF_ERR_ARG, "bucket_level %d > max_level %d", rbf->bucket_level, M);
+    if (rbf->water != 0 && rbf->water != 1) return fail(HF_ERR_ARG, "water must be 0 or 1");
+    if (rbf->reserved != 0) return fail(HF_ERR_ARG, "reserved must be 0");
+    if (rbf->water && rbf->precision != HF_PREC_FP32)
+        return fail(HF_ERR_ARG, "the water layer needs FP32 precision");
 
     std::unique_ptr<hf_ctx> ctx(new hf_ctx);
     ctx->desc = d;
@@ -384,6 +395,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     ctx->c_max = d.root_cell / double(int64_t(1) << lmin);
     ctx->zmin = vmin;
     ctx->zmax = vmax;
+    if (rbf->water) ctx->depth.assign(size_t(n_leaves), 0.f);
 
     // records in (level, iy, ix) order: centre, exponent scale, value
     const double log2e = 1.4426950408889634;
@@ -468,7 +480,7 @@ int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
     if (view_bytes) {
         if (n_cascades < 1 || n_cascades > HF_MAX_CASCADES || cascade_size < 2 || cascade_size > kMaxCascadeSize)
             return fail(HF_ERR_ARG, "cascades must be 1..%d of side 2..%d", HF_MAX_CASCADES, kMaxCascadeSize);
-        *view_bytes = per_view_bytes(n_cascades, cascade_size);
+        *view_bytes = per_view_bytes(n_cascades, cascade_size, ctx->rbf.water != 0);
     }
     return HF_OK;
 }
@@ -491,6 +503,8 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
     if (!e && ctx->rbf.precision != HF_PREC_FP32)
         e = cudaMemcpyAsync(dev + l.pair_offsets, ctx->pair_offsets.data(), ctx->pair_offsets.size() * 8,
                             cudaMemcpyHostToDevice, s);
+    if (!e && ctx->rbf.water)
+        e = cudaMemcpyAsync(dev + l.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
     if (e) return cuda_fail(e, "upload of the quadtree");
     ctx->dev = dev;
     ctx->dev_bytes = bytes;
@@ -529,6 +543,8 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
     }
     ctx->zmin = vmin;
     ctx->zmax = vmax;
+    for (size_t k = 0; k < ctx->depth.size(); ++k)
+        if (ctx->depth[k] > 0.f) ctx->zmax = std::max(double(ctx->zmax), double(ctx->recs[k].w) + ctx->depth[k]);
     cudaStream_t s = cudaStream_t(stream);
     int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
                               cudaMemcpyHostToDevice, s);
@@ -537,6 +553,29 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
                                 ctx->rbf.precision, stream);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "value upload");
+    return HF_OK;
+}
+
+int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* stream) {
+    if (!ctx || !depths) return fail(HF_ERR_ARG, "null argument");
+    if (!ctx->rbf.water) return fail(HF_ERR_STATE, "context was created without the water layer");
+    if (n_depths != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld depths", (long long)ctx->n_leaves);
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    for (int64_t k = 0; k < n_depths; ++k)
+        if (!(std::isfinite(depths[k]) && depths[k] >= 0.f))
+            return fail(HF_ERR_ARG, "depth %lld must be finite and >= 0", (long long)k);
+    double zmax = -INFINITY;
+    for (int64_t k = 0; k < n_depths; ++k) {
+        const int64_t s = ctx->perm[size_t(k)];
+        ctx->depth[size_t(s)] = depths[k];
+    }
+    for (int64_t s = 0; s < n_depths; ++s)
+        zmax = std::max(zmax, double(ctx->recs[size_t(s)].w) + (ctx->depth[size_t(s)] > 0.f ? ctx->depth[size_t(s)] : 0.0));
+    ctx->zmax = zmax;
+    cudaStream_t s = cudaStream_t(stream);
+    int e = cudaMemcpyAsync(ctx->dev + ctx->lay.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "depth upload");
     return HF_OK;
 }
 
@@ -555,7 +594,7 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
     if (!(c.split_lambda >= 0.0 && c.split_lambda <= 1.0)) return fail(HF_ERR_ARG, "split_lambda must be in [0, 1]");
     if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
     if (reinterpret_cast<uintptr_t>(dev_view) & 255) return fail(HF_ERR_ARG, "view buffer must be 256-byte aligned");
-    const size_t need = per_view_bytes(c.n_cascades, c.cascade_size);
+    const size_t need = per_view_bytes(c.n_cascades, c.cascade_size, ctx->rbf.water != 0);
     if (bytes < need) return fail(HF_ERR_NOMEM, "view buffer has %zu bytes, %zu needed", bytes, need);
     if (!ctx->views[slot]) ctx->views[slot].reset(new ViewSlot);
     ViewSlot& v = *ctx->views[slot];
@@ -574,6 +613,11 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
     for (int k = 0; k < c.n_cascades; ++k) {
         v.tex[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * N * 4);
         v.mip[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(mip_floats(N)) * 4);
+        if (ctx->rbf.water) {
+            v.wtex[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * N * 4);
+        } else {
+            v.wtex[k] = nullptr;
+        }
         v.spans[k] = reinterpret_cast<int2*>(v.dev + o); o = align256(o + size_t(N) * 8);
         v.xs[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * 4);
         v.ys[k] = reinterpret_cast<float*>(v.dev + o); o = align256(o + size_t(N) * 4);
@@ -582,6 +626,7 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
         ci.mip = v.mip[k];
         ci.spans = reinterpret_cast<int32_t*>(v.spans[k]);
         ci.mip_floats = mip_floats(N);
+        ci.water_tex = v.wtex[k];
     }
     v.stage = 1;
     return HF_OK;
@@ -596,6 +641,7 @@ DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
     dp.C = C;
     dp.max_N = N;
     dp.precision = ctx->rbf.precision;
+    dp.water = ctx->rbf.water;
     dp.K = float(std::exp(-ctx->rbf.radius * ctx->rbf.radius / (2.0 * ctx->rbf.sigma * ctx->rbf.sigma)));
     for (int k = 0; k < C; ++k) {
         DiscCascade& dc = dp.cas[k];
@@ -604,6 +650,7 @@ DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
         dc.xs = v->xs[k];
         dc.ys = v->ys[k];
         dc.tex = v->tex[k];
+        dc.wtex = v->wtex[k];
     }
     return dp;
 }
@@ -674,8 +721,10 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
     mp.C = C;
     mp.max_P = mip_pow2(N);
     mp.max_K = mip_levels(mp.max_P);
+    mp.two = ctx->rbf.water;
     for (int k = 0; k < C; ++k) {
         mp.cas[k].tex = v->tex[k];
+        mp.cas[k].wtex = v->wtex[k];
         mp.cas[k].mip = v->mip[k];
         mp.cas[k].N = N;
         mp.cas[k].P = mp.max_P;
@@ -689,12 +738,13 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
 
 namespace {
 
-RayParams ray_params(const ViewSlot* v) {
+RayParams ray_params(const ViewSlot* v, bool water) {
     const hf_camera& c = v->cam;
     const FitResult& f = v->fit;
     RayParams rp;
     std::memset(&rp, 0, sizeof(rp));
     rp.C = c.n_cascades;
+    rp.water = water ? 1 : 0;
     rp.W = c.width;
     rp.H = c.height;
     rp.ez = float(v->eye_local[2]);
@@ -721,6 +771,7 @@ RayParams ray_params(const ViewSlot* v) {
         RayCascade& rc = rp.cas[k];
         rc.tex = v->tex[k];
         rc.mip = v->mip[k];
+        rc.wtex = v->wtex[k];
         rc.N = N;
         rc.P = P;
         rc.K = mip_levels(P);
@@ -745,7 +796,7 @@ int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* 
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
     if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
-    RayParams rp = ray_params(v);
+    RayParams rp = ray_params(v, ctx->rbf.water != 0);
     rp.t_out = t_dev;
     rp.hit_out = hit_dev;
     int e = launch_raycast(rp, ctx->d_status(), stream);
@@ -760,7 +811,7 @@ int hf_ray_stats(hf_ctx* ctx, int32_t slot, int64_t* visits, int64_t* patch_test
     cudaStream_t s = cudaStream_t(stream);
     DevStatus* st = ctx->d_status();
     int e = cudaMemsetAsync(st->ray_counters, 0, sizeof(st->ray_counters), s);
-    if (!e) e = launch_raycast_count(ray_params(v), st, stream);
+    if (!e) e = launch_raycast_count(ray_params(v, ctx->rbf.water != 0), st, stream);
     if (e) return cuda_fail(e, "ray counting pass launch");
     unsigned long long c[2];
     e = cudaMemcpyAsync(c, st->ray_counters, sizeof(c), cudaMemcpyDeviceToHost, s);
@@ -810,6 +861,7 @@ int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
         ViewSlot* v = get_view(it.ctx, it.view_slot);
         if (!v || v->stage < 1) return fail(HF_ERR_STATE, "batch item %d: view slot %d has no camera", i, it.view_slot);
         if (!it.ctx->dev) return fail(HF_ERR_STATE, "batch item %d: persistent buffer not bound", i);
+        if (it.ctx->rbf.water) return fail(HF_ERR_ARG, "batch item %d: batched frames do not carry the water layer", i);
         if (!it.t_dev || !it.hit_dev) return fail(HF_ERR_ARG, "batch item %d: null output buffer", i);
         nc += v->cam.n_cascades;
     }
@@ -880,7 +932,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
         ViewSlot* v = get_view(ctx, items[i].view_slot);
         const int C = v->cam.n_cascades, N = v->cam.cascade_size, P = mip_pow2(N);
         BatchItem& I = bi[i];
-        I.ray = ray_params(v);
+        I.ray = ray_params(v, false);
         I.ray.t_out = items[i].t_dev;
         I.ray.hit_out = items[i].hit_dev;
         I.lt = ctx->lookup_tables(true);

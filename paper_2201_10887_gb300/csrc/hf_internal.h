@@ -62,6 +62,7 @@ struct ListsView {
     const int64_t* offsets;  // n_buckets + 1
     int32_t* idx;            // candidate leaf indices, ascending within a bucket
     float4* recs;            // per leaf: centre x, y (domain-local), -log2(e)/(2 sigma^2 c^2), value
+    const float* depth;      // per leaf water depth (water layer only, else null)
 };
 
 // Compact candidate lists of the reduced-precision discretization: per bucket
@@ -106,18 +107,21 @@ struct DiscCascade {
     const float* xs;
     const float* ys;
     float* tex;
+    float* wtex;  // water surface texture (water layer only)
 };
 
 struct DiscParams {
     int32_t C;
     int32_t max_N;
     int32_t precision;
-    float K;  // exp(-R^2 / (2 sigma^2))
+    int32_t water;  // 1: also discretize the depths and write the water surface
+    float K;        // exp(-R^2 / (2 sigma^2))
     DiscCascade cas[HF_MAX_CASCADES];
 };
 
 struct MipCascade {
     const float* tex;
+    const float* wtex;  // water surface: level 0 bounds both patches (two = 1 only)
     float* mip;
     int32_t N, P, K;
 };
@@ -126,12 +130,14 @@ struct MipParams {
     int32_t C;
     int32_t max_P;
     int32_t max_K;
+    int32_t two;  // 1: bound the terrain and the water surface together
     MipCascade cas[HF_MAX_CASCADES];
 };
 
 struct RayCascade {
     const float* tex;
     const float* mip;
+    const float* wtex;  // water surface (water layer only; mip then bounds both surfaces)
     int32_t N, P, K;
     float eu, ev;  // eye in this cascade's patch units
     float h, inv_h;
@@ -141,6 +147,7 @@ struct RayCascade {
 
 struct RayParams {
     int32_t C, W, H;
+    int32_t water;           // 1: rays meet the terrain or the water surface, whichever comes first
     float ez;                // eye height (m)
     float F[3], R[3], U[3];  // camera basis
     float px_a, px_b, py_a, py_b;  // screen coordinates: s = fma(pixel, a, b), s in [-tan, tan]

@@ -337,15 +337,20 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
 //   w_i = max(2^(k_i d_i^2) - K, 0),  k_i = -log2(e) / (2 sigma^2 c_i^2)
 //   v   = sum w_i v_i / sum w_i.
 // Invisible texels are written as -inf so the texture is fully defined.
+// With the water layer the same weights also sum the cells' water depths d_i
+// (terrain and depths live on the same cells, Section 2): the water surface
+// texel is v + sum w_i d_i / sum w_i where that depth is positive, else -inf.
 
-template <bool COH>
+template <bool COH, bool WATER = false>
 __device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, const LookupTables& lt,
                                                  const ListsView& lv, DevStatus* status, int i, int j) {
     if (i >= q.N || j >= q.N) return;
     const int2 sp = ldc<COH>(q.spans + j);
-    float* out = q.tex + size_t(j) * q.N + i;
+    const size_t o = size_t(j) * q.N + i;
+    float* out = q.tex + o;
     if (i < sp.x || i > sp.y) {
         *out = -INFINITY;
+        if (WATER) q.wtex[o] = -INFINITY;
         return;
     }
     const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
@@ -353,21 +358,26 @@ __device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, 
     if (bucket < 0) {
         report(status, kStatusData, 0xFFFFFFFFu);
         *out = __int_as_float(0x7fc00000);
+        if (WATER) q.wtex[o] = __int_as_float(0x7fc00000);
         return;
     }
     const int64_t beg = __ldg(lv.offsets + bucket);
     const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
     const int32_t* ids = lv.idx + beg;
-    float sw = 0.f, swv = 0.f;
+    float sw = 0.f, swv = 0.f, swd = 0.f;
 #pragma unroll 4
     for (int k = 0; k < n; ++k) {
-        const float4 r = __ldg(lv.recs + __ldg(ids + k));
+        const int id = __ldg(ids + k);
+        const float4 r = __ldg(lv.recs + id);
         const float dx = r.x - px, dy = r.y - py;
         const float w = fmaxf(ex2_approx(r.z * fmaf(dx, dx, dy * dy)) - K, 0.f);
         sw += w;
         swv = fmaf(w, r.w, swv);
+        if (WATER) swd = fmaf(w, __ldg(lv.depth + id), swd);
     }
-    *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+    const float v = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+    *out = v;
+    if (WATER) q.wtex[o] = swd > 0.f ? v + swd / sw : -INFINITY;
 }
 
 // texel of thread t (0..255) in a 32 x 8 tile: warp = 8 x 4 patch
@@ -377,12 +387,14 @@ __device__ __forceinline__ void tile_texel(int t, int& di, int& dj) {
     dj = (warp >> 2) * 4 + (lane >> 3);
 }
 
+template <bool WATER>
 __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
                                                         const __grid_constant__ LookupTables lt,
                                                         const ListsView lv, DevStatus* status) {
     int di, dj;
     tile_texel(threadIdx.x, di, dj);
-    discretize_texel<false>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di, blockIdx.y * 8 + dj);
+    discretize_texel<false, WATER>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di,
+                                   blockIdx.y * 8 + dj);
 }
 
 // Reduced-precision discretization: the same texel mapping, bucket lookup and
@@ -519,7 +531,10 @@ int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsVi
                       DevStatus* status, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
-    k_discretize_f32<<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    if (p.water)
+        k_discretize_f32<true><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    else
+        k_discretize_f32<false><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
     return cudaGetLastError();
 }
 
@@ -585,7 +600,7 @@ __device__ __forceinline__ int64_t mip_off(int P, int k) {
 }
 
 // Levels 0..6 of the 64 x 64 level-0 block (bx, by); 256 threads.
-template <bool COH>
+template <bool COH, bool TWO = false>
 __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int byi, float (*sm)[17]) {
     const int P = c.P, N = c.N, K = c.K;
     if (bxi * 64 >= P || byi * 64 >= P) return;
@@ -609,6 +624,24 @@ __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int b
                             isfinite(d) && isfinite(e);
             m0[r][s] = ok ? fmaxf(fmaxf(a, b), fmaxf(d, e)) : -INFINITY;
         }
+    if (TWO) {  // water layer: the entry bounds the water patch too, where it exists
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int ii = pi0 + s, jj = pj0 + r;
+                t[r][s] = (ii < N && jj < N) ? ldc<COH>(c.wtex + size_t(jj) * N + ii) : -INFINITY;
+            }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const float a = t[r][s], b = t[r][s + 1], d = t[r + 1][s], e = t[r + 1][s + 1];
+                const bool ok = (pi0 + s < N - 1) && (pj0 + r < N - 1) && isfinite(a) && isfinite(b) &&
+                                isfinite(d) && isfinite(e);
+                if (ok) m0[r][s] = fmaxf(m0[r][s], fmaxf(fmaxf(a, b), fmaxf(d, e)));
+            }
+    }
     if (pi0 < P && pj0 < P) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -661,9 +694,10 @@ __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int b
     }
 }
 
+template <bool TWO>
 __global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParams p) {
     __shared__ float sm[16][17];
-    mip_lo_block<false>(p.cas[blockIdx.z], blockIdx.x, blockIdx.y, sm);
+    mip_lo_block<false, TWO>(p.cas[blockIdx.z], blockIdx.x, blockIdx.y, sm);
 }
 
 // Levels 7..K of one cascade from level 6 (any block size; s0, s1 hold 4096 floats each).
@@ -710,7 +744,10 @@ __global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipPara
 int launch_maxmip(const MipParams& p, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_P + 63) / 64, (p.max_P + 63) / 64, p.C);
-    k_mip_lo<<<grid, 256, 0, cudaStream_t(stream)>>>(p);
+    if (p.two)
+        k_mip_lo<true><<<grid, 256, 0, cudaStream_t(stream)>>>(p);
+    else
+        k_mip_lo<false><<<grid, 256, 0, cudaStream_t(stream)>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.max_K >= 7) {
@@ -773,11 +810,13 @@ struct Ray {
     float du, dv, dz;  // per metre of t
 };
 
-template <bool COH>
+// CHECK: the patch may have an undefined (-inf) corner, then it does not exist.
+template <bool COH, bool CHECK = false>
 __device__ __forceinline__ bool patch_hit(const float* __restrict__ tex, int N, int ci, int cj,
                                           const Ray& r, float t0, float t1, float& t_hit) {
     const float* p = tex + size_t(cj) * N + ci;
     const float h00 = ldc<COH>(p), h10 = ldc<COH>(p + 1), h01 = ldc<COH>(p + N), h11 = ldc<COH>(p + N + 1);
+    if (CHECK && !(fminf(fminf(h00, h10), fminf(h01, h11)) > -INFINITY)) return false;
     const float a0 = fmaf(t0, r.du, r.eu) - float(ci);
     const float b0 = fmaf(t0, r.dv, r.ev) - float(cj);
     const float z0 = fmaf(t0, r.dz, r.ez);
@@ -821,12 +860,19 @@ struct RayDir {
     float tmin, tmax;
 };
 
-template <bool COUNT, bool COH>
-__device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
-                              float ez, float ta, float tb, float& t_hit, DevStatus* status,
-                              uint32_t pixel, unsigned& visits, unsigned& tests) {
+// First hit inside cascade c on [ta, tb].  With the water layer (UNION) the
+// mipmap bounds both surfaces and each patch reached is tested against the
+// terrain and, where its four corners are wet, the water surface: the first
+// patch with any root holds the first hit of either surface, the nearer root
+// of the two (the water surface on a tie; on_water says which).
+template <bool COUNT, bool COH, bool UNION = false>
+__device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
+                                              float ez, float ta, float tb, float& t_hit, bool& on_water,
+                                              DevStatus* status, uint32_t pixel, unsigned& visits, unsigned& tests) {
     const int N = c.N, P = c.P, K = c.K;
-    const float top = ldc<COH>(c.mip + off[K]);
+    const float* __restrict__ mip = c.mip;
+    const float* __restrict__ tex = c.tex;
+    const float top = ldc<COH>(mip + off[K]);
     if (!(top > -INFINITY)) return false;  // nothing visible in this cascade
     Ray r;
     r.eu = c.eu;
@@ -859,7 +905,7 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
         const float ty = fmaf(exact_float((nj + bv) << k), idv, ov);
         const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
         const float zmin = fmaf(zneg ? te : t, r.dz, ez);
-        const float mx = ldc<COH>(c.mip + off[k] + nj * (P >> k) + ni);
+        const float mx = ldc<COH>(mip + off[k] + nj * (P >> k) + ni);
         if (COUNT) ++visits;
         if (zmin <= __fadd_rn(mx, slack)) {
             if (k > 0) {
@@ -868,7 +914,21 @@ __device__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, 
             }
             if (ci <= N - 2 && cj <= N - 2) {
                 if (COUNT) ++tests;
-                if (patch_hit<COH>(c.tex, N, ci, cj, r, t, te, t_hit)) return true;
+                float th;
+                const bool ht = patch_hit<COH>(tex, N, ci, cj, r, t, te, th);
+                if (UNION) {
+                    float tw;
+                    if (patch_hit<COH, true>(c.wtex, N, ci, cj, r, t, te, tw) && (!ht || tw <= th)) {
+                        t_hit = tw;
+                        on_water = true;
+                        return true;
+                    }
+                }
+                if (ht) {
+                    t_hit = th;
+                    on_water = false;
+                    return true;
+                }
             }
         }
         if (te >= tb) return false;
@@ -937,7 +997,43 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayD
     return lo <= hi;
 }
 
-template <bool COUNT, bool COH>
+// Through the cascades, nearest first, blended in the overlaps (reading of
+// Section 5: the blend runs linearly in projected depth across the overlap
+// band of cascades c and c+1 when both are hit); 0x80 marks a first-hit
+// cascade whose hit is on the water surface.
+template <bool COUNT, bool COH, bool UNION>
+__device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_off)[kMaxLevels], const RayDir& d,
+                                              DevStatus* status, uint32_t pix, unsigned& visits, unsigned& tests,
+                                              float& t, int& hit) {
+    hit = 0;
+    t = __int_as_float(0x7fc00000);
+    for (int c = 0; c < p.C && !hit; ++c) {
+        const RayCascade& cc = p.cas[c];
+        float ta, tb, tc;
+        bool wet = false;
+        if (!cascade_interval(cc, d, ta, tb)) continue;
+        if (!trace_cascade<COUNT, COH, UNION>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
+            continue;
+        hit = (1 + c) | (wet ? 0x80 : 0);
+        t = tc;
+        const float s = __fmul_rn(tc, d.ks);
+        if (c + 1 < p.C) {
+            const RayCascade& cn = p.cas[c + 1];
+            if (s >= cn.near_d && cc.far_ext > cn.near_d) {
+                float ta2, tb2, t2;
+                bool wet2 = false;
+                if (cascade_interval(cn, d, ta2, tb2) &&
+                    trace_cascade<COUNT, COH, UNION>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
+                                                     visits, tests)) {
+                    const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
+                    t = fmaf(al, t2 - tc, tc);
+                }
+            }
+        }
+    }
+}
+
+template <bool COUNT, bool COH, bool WATER = false>
 __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_off)[kMaxLevels], DevStatus* status,
                                               int x, int y, unsigned& visits, unsigned& tests) {
     if (x >= p.W || y >= p.H) return;
@@ -960,28 +1056,9 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
     d.ks = fmaf(d.dx, p.dir2x, d.dy * p.dir2y);
     d.rks = d.ks != 0.f ? rcp_approx(d.ks) : 0.f;
     const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
-    int hit = 0;
-    float t = __int_as_float(0x7fc00000);
-    for (int c = 0; c < p.C && !hit; ++c) {
-        const RayCascade& cc = p.cas[c];
-        float ta, tb, tc;
-        if (!cascade_interval(cc, d, ta, tb)) continue;
-        if (!trace_cascade<COUNT, COH>(cc, s_off[c], d, p.ez, ta, tb, tc, status, pix, visits, tests)) continue;
-        hit = 1 + c;
-        t = tc;
-        const float s = __fmul_rn(tc, d.ks);
-        if (c + 1 < p.C) {
-            const RayCascade& cn = p.cas[c + 1];
-            if (s >= cn.near_d && cc.far_ext > cn.near_d) {
-                float ta2, tb2, t2;
-                if (cascade_interval(cn, d, ta2, tb2) &&
-                    trace_cascade<COUNT, COH>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, status, pix, visits, tests)) {
-                    const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
-                    t = fmaf(al, t2 - tc, tc);
-                }
-            }
-        }
-    }
+    int hit;
+    float t;
+    cast_cascades<COUNT, COH, WATER>(p, s_off, d, status, pix, visits, tests, t, hit);
     if (!COUNT) {
         p.t_out[pix] = t;
         p.hit_out[pix] = uint8_t(hit);
@@ -993,14 +1070,16 @@ __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_o
         s_off[e / kMaxLevels][e % kMaxLevels] = p.cas[e / kMaxLevels].lvl_off[e % kMaxLevels];
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
+// 9 CTAs of 128 threads per SM leave the walk its 56 registers without spills
+// (8 and 64 registers for the walk over both surfaces).
+template <bool COUNT, bool WATER>
+__global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
     __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
     load_level_offsets(p, s_off, threadIdx.y * 16 + threadIdx.x, 128);
     __syncthreads();
     unsigned visits = 0, tests = 0;
-    raycast_pixel<COUNT, false>(p, s_off, status, blockIdx.x * 16 + threadIdx.x, blockIdx.y * 8 + threadIdx.y,
-                                visits, tests);
+    raycast_pixel<COUNT, false, WATER>(p, s_off, status, blockIdx.x * 16 + threadIdx.x, blockIdx.y * 8 + threadIdx.y,
+                                       visits, tests);
     if (COUNT) {
         visits = __reduce_add_sync(0xffffffffu, visits);
         tests = __reduce_add_sync(0xffffffffu, tests);
@@ -1011,16 +1090,22 @@ __global__ void __launch_bounds__(128) k_raycast(const __grid_constant__ RayPara
     }
 }
 
-int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
+template <bool COUNT>
+int launch_raycast_t(const RayParams& p, DevStatus* status, void* stream) {
     dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
-    k_raycast<false><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
+    if (p.water)
+        k_raycast<COUNT, true><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
+    else
+        k_raycast<COUNT, false><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
     return cudaGetLastError();
 }
 
+int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
+    return launch_raycast_t<false>(p, status, stream);
+}
+
 int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream) {
-    dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
-    k_raycast<true><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
-    return cudaGetLastError();
+    return launch_raycast_t<true>(p, status, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_up
             "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
-            "hf_batch_launch", "hf_frame_batch"]
+            "hf_batch_launch", "hf_frame_batch", "hf_update_water"]
 HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
 HF_BATCH_PERSISTENT = 16
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
@@ -47,7 +47,7 @@ class hf_quadtree_desc(ct.Structure):
 
 class hf_rbf_params(ct.Structure):
     _fields_ = [("sigma", ct.c_double), ("radius", ct.c_double), ("precision", ct.c_int32),
-                ("bucket_level", ct.c_int32)]
+                ("bucket_level", ct.c_int32), ("water", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class hf_camera(ct.Structure):
@@ -65,7 +65,8 @@ class hf_cascade_info(ct.Structure):
                 ("snap_x", ct.c_int64), ("snap_y", ct.c_int64), ("snap_k", ct.c_int64),
                 ("ox", ct.c_double), ("oy", ct.c_double), ("extent", ct.c_double),
                 ("texel", ct.c_double), ("tex", ct.c_void_p), ("mip", ct.c_void_p),
-                ("spans", ct.c_void_p), ("mip_floats", ct.c_int64)]
+                ("spans", ct.c_void_p), ("mip_floats", ct.c_int64),
+                ("water_tex", ct.c_void_p)]
 
     @property
     def h(self) -> float:
@@ -101,6 +102,7 @@ def _load():
         "hf_query_bytes": [vp, i32, i32, P(sz), P(sz)],
         "hf_bind_persistent": [vp, vp, sz, vp],
         "hf_update_values": [vp, vp, i64, vp],
+        "hf_update_water": [vp, vp, i64, vp],
         "hf_set_camera": [vp, i32, P(hf_camera), vp, sz],
         "hf_discretize_cascades": [vp, i32, vp],
         "hf_build_maxmip": [vp, i32, vp],
@@ -184,6 +186,11 @@ def hf_bind_persistent(ctx, buf, stream=None):
 def hf_update_values(ctx, values: np.ndarray, stream=None):
     v = np.ascontiguousarray(values, np.float32)
     _check(_lib.hf_update_values(ctx, v.ctypes.data_as(ct.c_void_p), ct.c_int64(v.size), _stream(stream)))
+
+
+def hf_update_water(ctx, depths: np.ndarray, stream=None):
+    d = np.ascontiguousarray(depths, np.float32)
+    _check(_lib.hf_update_water(ctx, d.ctypes.data_as(ct.c_void_p), ct.c_int64(d.size), _stream(stream)))
 
 
 def hf_set_camera(ctx, slot: int, cam: hf_camera, view_buf):

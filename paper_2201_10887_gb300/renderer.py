@@ -26,18 +26,22 @@ class Renderer:
     """One quadtree heightfield on one GPU.
 
     ``tree`` is any object with origin_x, origin_y, root_cell, root_nx,
-    root_ny, max_level and leaf arrays level, ix, iy, value.
+    root_ny, max_level and leaf arrays level, ix, iy, value.  With
+    ``water=True`` the leaves also carry water depths (``update_water``) and
+    every view gets a water surface texture per cascade (the max mipmap then
+    bounds both surfaces).
     """
 
     def __init__(self, tree, sigma: float, radius: float, precision: int = hf.HF_PREC_FP32,
-                 bucket_level: int = -1, device=None, stream=None):
+                 bucket_level: int = -1, device=None, stream=None, water: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
         desc = hf.hf_quadtree_desc(tree.origin_x, tree.origin_y, tree.root_cell, tree.root_nx,
                                    tree.root_ny, tree.max_level)
         leaves = hf.leaves_array(tree.level, tree.ix, tree.iy, tree.value)
-        rbf = hf.hf_rbf_params(sigma, radius, precision, bucket_level)
+        rbf = hf.hf_rbf_params(sigma, radius, precision, bucket_level, 1 if water else 0, 0)
+        self.water = bool(water)
         self.ctx = hf.hf_create_quadtree(desc, leaves, rbf)
         self.persistent_bytes, _ = hf.hf_query_bytes(self.ctx, 1, 2)
         self.persistent = torch.empty(self.persistent_bytes, dtype=torch.uint8, device=self.device)
@@ -103,6 +107,9 @@ class Renderer:
     def update_values(self, values, stream=None):
         hf.hf_update_values(self.ctx, values, stream)
 
+    def update_water(self, depths, stream=None):
+        hf.hf_update_water(self.ctx, depths, stream)
+
     def stats(self, slot: int = 0, stream=None) -> dict:
         return hf.hf_view_stats(self.ctx, slot, self.views[slot]["C"], stream)
 
@@ -128,6 +135,10 @@ class Renderer:
     def mip(self, slot: int, c: int):
         info = self.cascade(slot, c)
         return self._sub(slot, info.mip, info.mip_floats * 4).view(self.torch.float32)
+
+    def water_texture(self, slot: int, c: int):
+        info = self.cascade(slot, c)
+        return self._sub(slot, info.water_tex, info.N * info.N * 4).view(self.torch.float32).view(info.N, info.N)
 
     def spans(self, slot: int, c: int):
         info = self.cascade(slot, c)

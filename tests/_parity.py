@@ -8,6 +8,12 @@ Tolerances (FP32 path):
   hit/miss  at most 0.1 % of pixels differ, and only at silhouettes: pixels
             whose 3x3 reference neighbourhood mixes hit and miss, or whose
             reference t jumps by more than 5 % inside it
+  water     the water surface texture: the wet/dry decision (discretized
+            depth > 0) may differ only where the oracle's depth is below 1e-6
+            of the largest depth (a cell at the truncation radius has a
+            weight of order the FP32 exp error there); wet on both sides:
+            the height rule above.  Water flag of a hit: see
+            check_water_flags.
   grazing   a pixel outside the two rules above is still correct if the
             oracle, run on the same surface raised and lowered by
             delta = 2e-6 * (t + A), brackets it (backward error): a ray that
@@ -84,15 +90,21 @@ def silhouettes(hit_ref: np.ndarray, t_ref: np.ndarray) -> np.ndarray:
     return mixed | jump
 
 
-def surface_bracket(orc, cam, tree, rcs, texs, px, py, delta):
-    """Oracle rays at pixels (px, py) on the surface raised and lowered by
-    delta: (t_up, hit_up, t_down, hit_down)."""
+def surface_bracket(orc, cam, tree, rcs, texs, px, py, delta, water_texs=None):
+    """Oracle rays at pixels (px, py) on the surface (both surfaces with the
+    water layer) raised and lowered by delta: (t_up, hit_up, t_down, hit_down)."""
     d = np.float32(delta)
-    up = [np.where(np.isfinite(t), t + d, t).astype(np.float32) for t in texs]
-    dn = [np.where(np.isfinite(t), t - d, t).astype(np.float32) for t in texs]
-    tu, hu, _, _ = orc.raycast(cam, tree, rcs, up, pixels=(px, py))
-    td, hd, _, _ = orc.raycast(cam, tree, rcs, dn, pixels=(px, py))
-    return tu, hu, td, hd
+
+    def shift(ts, s):
+        return [np.where(np.isfinite(t), t + s * d, t).astype(np.float32) for t in ts]
+    out = []
+    for sgn in (1, -1):
+        if water_texs is None:
+            t, h, _, _ = orc.raycast(cam, tree, rcs, shift(texs, sgn), pixels=(px, py))
+        else:
+            t, h, _ = orc.raycast_water(cam, tree, rcs, shift(texs, sgn), shift(water_texs, sgn), pixels=(px, py))
+        out += [t, h]
+    return tuple(out)
 
 
 def bracketed(gt, gh, seg, tu, hu, td, hd):
@@ -104,7 +116,7 @@ def bracketed(gt, gh, seg, tu, hu, td, hd):
     return hit_ok | miss_ok
 
 
-def frame_bracket(orc, cam, tree, rcs, texs, gt, gh, ot, seg, amp):
+def frame_bracket(orc, cam, tree, rcs, texs, gt, gh, ot, seg, amp, water_texs=None):
     """Callable for check_rays: flat pixel indices -> explained by a surface
     perturbation of size GRAZE_REL * (t + A)."""
     def f(idx):
@@ -112,9 +124,27 @@ def frame_bracket(orc, cam, tree, rcs, texs, gt, gh, ot, seg, amp):
         tmax = np.nanmax(np.concatenate([np.where(gh[idx] > 0, gt[idx], np.nan),
                                          np.where(np.isfinite(ot[idx]), ot[idx], np.nan), [0.0]]))
         delta = GRAZE_REL * (tmax + amp)
-        tu, hu, td, hd = surface_bracket(orc, cam, tree, rcs, texs, px, py, delta)
+        tu, hu, td, hd = surface_bracket(orc, cam, tree, rcs, texs, px, py, delta, water_texs)
         return bracketed(gt[idx], gh[idx], seg[idx], tu, hu, td, hd)
     return f
+
+
+def check_water_flags(orc, cam, tree, rcs, texs, water_texs, gh, oh, seg):
+    """Where both sides hit, the water flag (0x80) must agree, except where
+    the oracle's terrain and water hits are closer than the ray tolerance
+    (a water layer thinner than the comparison can resolve, e.g. at a
+    shore where the discretized depth tends to 0).  Returns (mismatches,
+    unexplained mismatches)."""
+    gh, oh, seg = np.asarray(gh).ravel(), np.asarray(oh).ravel(), np.asarray(seg).ravel()
+    both = (gh > 0) & (oh > 0)
+    mis = np.nonzero(both & ((gh & 0x80) != (oh & 0x80)))[0]
+    if mis.size == 0:
+        return 0, 0
+    px, py = (mis % cam.width).astype(np.int32), (mis // cam.width).astype(np.int32)
+    tt, ht, _, _ = orc.raycast(cam, tree, rcs, texs, pixels=(px, py))
+    tw, hw, _, _ = orc.raycast(cam, tree, rcs, water_texs, pixels=(px, py))
+    thin = (ht > 0) & (hw > 0) & (np.abs(tw - tt) <= RAY_REL * seg[mis])
+    return int(mis.size), int((~thin).sum())
 
 
 def check_rays(gt, gh, ot, oh, seg, shape=None, silhouette=None, bracket=None):

@@ -230,6 +230,27 @@ def test_reduced_precision_offset_limits(hfmod, tiny):
     assert e.value.code == hfmod.HF_ERR_ARG and "BF16" in str(e.value)
 
 
+def test_water_layer_flags_and_sizes(hfmod, tiny):
+    """The water layer: FP32 only, flag 0/1, reserved 0; it adds 4 bytes per
+    leaf to the persistent buffer and a second texture per cascade (one
+    mipmap bounds both surfaces)."""
+    t = tiny.tree
+    lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    plain = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 0, 0))
+    wet = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 1, 0))
+    p0, v0 = hfmod.hf_query_bytes(plain, 3, 256)
+    p1, v1 = hfmod.hf_query_bytes(wet, 3, 256)
+    assert p1 - p0 >= 4 * t.n_leaves and p1 - p0 < 4 * t.n_leaves + 256
+    assert v1 - v0 == 3 * 256 * 256 * 4
+    for d in (plain, wet):
+        hfmod.hf_destroy(d)
+    for args in ((0, -1, 2, 0), (1, -1, 1, 0), (2, -1, 1, 0), (0, -1, 0, 7)):
+        with pytest.raises(hfmod.HFError) as e:
+            hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, *args))
+        assert e.value.code == hfmod.HF_ERR_ARG
+
+
 def test_arena_first_fit_and_merge():
     from paper_2201_10887_gb300.serving import Arena
     a = Arena(10_000)

@@ -17,10 +17,11 @@ from .fbm import FBm
 from .quadtree import Quadtree, random_split_quadtree, curvature_quadtree
 from .cameras import Camera, fixed_camera, flight_path
 from .configs import (tiny_config, dem_config, precision_config, batch_config, serve_config,
-                      Request)
+                      tiny_flood_config, flood_config, flood_depths, Request)
 
 __all__ = [
     "FBm", "Quadtree", "random_split_quadtree", "curvature_quadtree",
     "Camera", "fixed_camera", "flight_path",
     "tiny_config", "dem_config", "precision_config", "batch_config", "serve_config", "Request",
+    "tiny_flood_config", "flood_config", "flood_depths",
 ]

@@ -17,6 +17,11 @@
   fBm amplitude 3000 m, a mosaic of curvature-refined blocks) kept resident,
   and a Poisson stream of view requests (rate 200/s) of 1280 x 720,
   1920 x 1080 or 3840 x 2160 with 2-6 cascades of 2048^2.
+* ``flood_config`` / ``tiny_flood_config``: the DEM (or tiny) scene plus
+  relative water depths at the same cells, a "bathtub" flood: every cell
+  below a water level L gets depth L - v (the paper's scenarios carry a flood
+  simulation's depths; a level flood is the simplest such field), with L
+  chosen so that a given fraction of the domain's area is under water.
 
 All use a Gaussian RBF with sigma = 1.5 cell sizes truncated at 3 cell sizes.
 """
@@ -43,6 +48,17 @@ class Scene:
     sigma: float
     radius: float
     cameras: list = field(default_factory=list)
+    depth: np.ndarray | None = None   # water depths per leaf (flood scenes)
+
+
+def flood_depths(tree: Quadtree, wet_area: float) -> tuple:
+    """(depths, level): depth = max(L - v, 0) per leaf, L the value below which
+    ``wet_area`` of the domain's area lies."""
+    area = tree.cell_sizes() ** 2
+    order = np.argsort(tree.value, kind="stable")
+    cum = np.cumsum(area[order]) / area.sum()
+    L = float(tree.value[order][min(int(np.searchsorted(cum, wet_area)), order.size - 1)])
+    return np.maximum(np.float32(L) - tree.value, np.float32(0)).astype(np.float32), L
 
 
 def tiny_config(seed: int = 1, origin=(0.0, 0.0), shuffle=True) -> Scene:
@@ -68,6 +84,20 @@ def dem_config(seed: int = 2, n_frames: int = 120, target_leaves: int = 4_500_00
     cams = flight_path(tree, fbm, seed, n_frames, width, height, n_cascades=4,
                        cascade_size=cascade_size, split_lambda=0.5)
     return Scene("dem", tree, fbm, RBF_SIGMA, RBF_RADIUS, cams)
+
+
+def tiny_flood_config(seed: int = 1, wet_area: float = 0.3) -> Scene:
+    s = tiny_config(seed)
+    s.name = "tiny_flood"
+    s.depth, _ = flood_depths(s.tree, wet_area)
+    return s
+
+
+def flood_config(seed: int = 2, n_frames: int = 120, wet_area: float = 0.2, **kw) -> Scene:
+    s = dem_config(seed, n_frames, **kw)
+    s.name = "flood"
+    s.depth, _ = flood_depths(s.tree, wet_area)
+    return s
 
 
 def batch_config(seed: int = 4, n_tiles: int = 64, min_side: int = 256,

@@ -400,6 +400,9 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_variants:
         line["precision_variants"] = time_precision_variants(scene, cams, sched[:min(len(sched), 240)],
                                                              args.warmup, dev, flush, stream)
+        line["interpolant_variants"] = time_precision_variants(
+            scene, cams, sched[:min(len(sched), 240)], args.warmup, dev, flush, stream,
+            variants=(("wendland_c2", {"kernel": 1}),))
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
@@ -414,14 +417,16 @@ def run_ours(args, rank, world, local_rank):
     r.close()
 
 
-def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream):
-    """Frame and discretization time of the FP16x2 / BF16x2 discretization on
-    the same frames (same timing method as the main line)."""
+def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream,
+                            variants=(("fp16", {"precision": 1}), ("bf16", {"precision": 2}))):
+    """Frame and discretization time of variants of the discretization (by
+    default the FP16x2 / BF16x2 paths) on the same frames (same timing method
+    as the main line)."""
     import torch
     from paper_2201_10887_gb300 import Renderer
     out = {}
-    for name, prec in (("fp16", 1), ("bf16", 2)):
-        r = Renderer(scene.tree, scene.sigma, scene.radius, precision=prec, device=dev)
+    for name, kw in variants:
+        r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev, **kw)
         for f in sched[:warmup]:
             r.render(cams[f])
         r.sync()

@@ -54,6 +54,7 @@ enum {
 };
 
 enum { HF_PREC_FP32 = 0, HF_PREC_FP16 = 1, HF_PREC_BF16 = 2 };
+enum { HF_RBF_GAUSSIAN = 0, HF_RBF_WENDLAND_C2 = 1 };
 
 #define HF_MAX_LEVEL 15
 #define HF_MAX_CASCADES 8
@@ -91,20 +92,26 @@ typedef struct {
  * coarser leaves are split into their level-bucket_level descendants so a
  * list never covers more than one level-bucket_level cell.  bucket_level
  * = -1 selects max(0, max_level - 2).
+ * kernel selects the weight function of Eq. 2: HF_RBF_GAUSSIAN is Eq. 1;
+ * HF_RBF_WENDLAND_C2 is Wendland's compactly supported C2 function
+ * (1 - r)^4 (4 r + 1) of r = |p_i - p| / (radius c_i), zero for r >= 1 (sigma
+ * unused) -- another interpolant in the same slot: lists, normalisation,
+ * mipmap and ray cast stay as they are.  Non-Gaussian kernels need FP32
+ * precision and are not available in batched frames.
  * water = 1 adds the water layer (Section 2: the input is a terrain model
  * plus relative water depths at the cells of the same adaptive grid; Table 1
  * times the approximation of both): every leaf also carries a depth >= 0
  * (hf_update_water, initially 0), each cascade gets a second texture holding
  * the water surface, and rays stop at whichever surface they meet first.  The
  * water layer needs precision HF_PREC_FP32 and is not available in batched
- * frames; hf_discretize_noalloc ignores it.  reserved must be 0. */
+ * frames; hf_discretize_noalloc ignores it. */
 typedef struct {
     double sigma;
     double radius;
     int32_t precision;
     int32_t bucket_level;
     int32_t water;
-    int32_t reserved;
+    int32_t kernel;
 } hf_rbf_params;
 
 /* A view (Section 3, Section 5).  eye is in world coordinates; forward and

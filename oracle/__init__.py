@@ -82,7 +82,7 @@ def lib():
         d, i, f, L = ct.c_double, ct.c_int, ct.c_float, ct.c_long
         P = ct.POINTER
         _lib.orc_rbf_weight.restype = d
-        _lib.orc_rbf_weight.argtypes = [d, d, d, d]
+        _lib.orc_rbf_weight.argtypes = [d, d, d, d, i]
         _lib.orc_ray_patch.restype = i
         _lib.orc_ray_patch.argtypes = [d] * 11 + [P(d)]
         _lib.orc_fit.restype = i
@@ -121,11 +121,14 @@ class Cells:
                              float(self.cs.min()), float(self.cs.max()))
 
 
-def rbf_weight(dist, c, sigma, radius) -> float:
-    return lib().orc_rbf_weight(float(dist), float(c), float(sigma), float(radius))
+GAUSSIAN, WENDLAND_C2 = 0, 1   # weight functions (kernel argument)
 
 
-def rbf_points(cells: Cells, sigma, radius, px, py, mode=1, with_counts=False):
+def rbf_weight(dist, c, sigma, radius, kernel=GAUSSIAN) -> float:
+    return lib().orc_rbf_weight(float(dist), float(c), float(sigma), float(radius), int(kernel))
+
+
+def rbf_points(cells: Cells, sigma, radius, px, py, mode=1, with_counts=False, kernel=GAUSSIAN):
     px = np.ascontiguousarray(px, np.float64).ravel()
     py = np.ascontiguousarray(py, np.float64).ravel()
     m = px.size
@@ -133,7 +136,7 @@ def rbf_points(cells: Cells, sigma, radius, px, py, mode=1, with_counts=False):
     cnt = np.empty(m, np.int32)
     lib().orc_rbf_points(_p(cells.cx, ct.c_double), _p(cells.cy, ct.c_double),
                          _p(cells.cs, ct.c_double), _p(cells.cv, ct.c_double), ct.c_long(cells.n),
-                         ct.c_double(sigma), ct.c_double(radius),
+                         ct.c_double(sigma), ct.c_double(radius), ct.c_int(kernel),
                          ct.c_double(cells.domain.width), ct.c_double(cells.domain.height),
                          _p(px, ct.c_double), _p(py, ct.c_double), ct.c_long(m), ct.c_int(mode),
                          _p(out, ct.c_double), _p(cnt, ct.c_int))
@@ -180,13 +183,13 @@ def mask(cas: CascadeC, cells: Cells, ii=None, jj=None):
     return vis, mg
 
 
-def texel_heights(cas: CascadeC, cells: Cells, sigma, radius, ii=None, jj=None) -> np.ndarray:
+def texel_heights(cas: CascadeC, cells: Cells, sigma, radius, ii=None, jj=None, kernel=GAUSSIAN) -> np.ndarray:
     ii, jj = _ij(cas.N, ii, jj)
     out = np.empty(ii.size)
     lib().orc_texel_heights(ct.byref(cas), ct.byref(cells.domain), _p(cells.cx, ct.c_double),
                             _p(cells.cy, ct.c_double), _p(cells.cs, ct.c_double),
                             _p(cells.cv, ct.c_double), ct.c_long(cells.n), ct.c_double(sigma),
-                            ct.c_double(radius), _p(ii, ct.c_int), _p(jj, ct.c_int),
+                            ct.c_double(radius), ct.c_int(kernel), _p(ii, ct.c_int), _p(jj, ct.c_int),
                             ct.c_long(ii.size), _p(out, ct.c_double))
     return out
 

@@ -2,7 +2,8 @@
  * CPU FP64 oracle (test infrastructure only; see hf_oracle.h).
  *
  * Every function restates one step of the paper in plain code:
- *   Eq. 1 (truncated Gaussian weight) ........ orc_rbf_weight
+ *   Eq. 1 (truncated Gaussian weight) ........ orc_rbf_weight (kernel 0)
+ *   Wendland C2 weight (another interpolant) .. orc_rbf_weight (kernel 1)
  *   Eq. 2 (normalised weighted sum) ........... orc_rbf_points, orc_texel_heights
  *   Section 3 (cascade fitting) ............... orc_fit, orc_frustum_box_vertices
  *   Section 3 (visible-texel mask) ............ orc_mask
@@ -33,7 +34,16 @@ int orc_threads(void) {
  * The paper truncates at 3.5 sigma (R = 3.5 sigma gives its constant
  * exp(-3.5^2/2)); R is a parameter here.  A cell influences p only if
  * w > 0 (Section 4), so the weight is 0 at and beyond d = R c.            */
-double orc_rbf_weight(double dist, double c, double sigma, double radius) {
+double orc_rbf_weight(double dist, double c, double sigma, double radius, int kernel) {
+    if (kernel == 1) {
+        /* Wendland's compactly supported C2 function psi_{3,1}(r) =
+         * (1 - r)^4 (4 r + 1) for r < 1, 0 beyond, with r = d / (radius c):
+         * the same support as the truncated Gaussian (sigma unused).        */
+        double r = dist / (radius * c);
+        if (r >= 1.0) return 0.0;
+        double t = 1.0 - r;
+        return t * t * t * t * (4.0 * r + 1.0);
+    }
     double r = dist / c;
     double w = exp(-(r * r) / (2.0 * sigma * sigma)) - exp(-(radius * radius) / (2.0 * sigma * sigma));
     return w > 0.0 ? w : 0.0;
@@ -99,11 +109,11 @@ static void bins_free(orc_bins* b) {
 /* Eq. 2 at one point: v = sum_{i in I} w_i v_i / sum_{i in I} w_i.
  * Returns NaN when I is empty (the quotient is undefined).                */
 static double rbf_brute(const double* cx, const double* cy, const double* cs, const double* cv,
-                        long n, double sigma, double radius, double px, double py, int* nI) {
+                        long n, double sigma, double radius, int kernel, double px, double py, int* nI) {
     double sw = 0.0, swv = 0.0;
     int cnt = 0;
     for (long k = 0; k < n; ++k) {
-        double w = orc_rbf_weight(hypot(cx[k] - px, cy[k] - py), cs[k], sigma, radius);
+        double w = orc_rbf_weight(hypot(cx[k] - px, cy[k] - py), cs[k], sigma, radius, kernel);
         if (w > 0.0) {
             sw += w;
             swv += w * cv[k];
@@ -115,8 +125,8 @@ static double rbf_brute(const double* cx, const double* cy, const double* cs, co
 }
 
 static double rbf_binned(const orc_bins* b, const double* cx, const double* cy, const double* cs,
-                         const double* cv, double sigma, double radius, double px, double py,
-                         int* nI) {
+                         const double* cv, double sigma, double radius, int kernel, double px,
+                         double py, int* nI) {
     long bx = (long)floor(px / b->bin), by = (long)floor(py / b->bin);
     double sw = 0.0, swv = 0.0;
     int cnt = 0;
@@ -127,7 +137,7 @@ static double rbf_binned(const orc_bins* b, const double* cx, const double* cy, 
             long q = y * b->nbx + x;
             for (long s = b->start[q]; s < b->start[q + 1]; ++s) {
                 long k = b->items[s];
-                double w = orc_rbf_weight(hypot(cx[k] - px, cy[k] - py), cs[k], sigma, radius);
+                double w = orc_rbf_weight(hypot(cx[k] - px, cy[k] - py), cs[k], sigma, radius, kernel);
                 if (w > 0.0) {
                     sw += w;
                     swv += w * cv[k];
@@ -141,13 +151,13 @@ static double rbf_binned(const orc_bins* b, const double* cx, const double* cy, 
 }
 
 void orc_rbf_points(const double* cx, const double* cy, const double* cs, const double* cv,
-                    long n, double sigma, double radius, double dom_w, double dom_h,
+                    long n, double sigma, double radius, int kernel, double dom_w, double dom_h,
                     const double* px, const double* py, long m, int mode, double* out,
                     int* n_influencers) {
     if (mode == 0) {
 #pragma omp parallel for schedule(dynamic, 16)
         for (long q = 0; q < m; ++q)
-            out[q] = rbf_brute(cx, cy, cs, cv, n, sigma, radius, px[q], py[q],
+            out[q] = rbf_brute(cx, cy, cs, cv, n, sigma, radius, kernel, px[q], py[q],
                                n_influencers ? &n_influencers[q] : NULL);
         return;
     }
@@ -155,7 +165,7 @@ void orc_rbf_points(const double* cx, const double* cy, const double* cs, const 
     bins_build(&b, cx, cy, cs, n, radius, dom_w, dom_h);
 #pragma omp parallel for schedule(dynamic, 64)
     for (long q = 0; q < m; ++q)
-        out[q] = rbf_binned(&b, cx, cy, cs, cv, sigma, radius, px[q], py[q],
+        out[q] = rbf_binned(&b, cx, cy, cs, cv, sigma, radius, kernel, px[q], py[q],
                             n_influencers ? &n_influencers[q] : NULL);
     bins_free(&b);
 }
@@ -469,8 +479,8 @@ void orc_mask(const orc_cascade* cas, const orc_domain* dom, const int* ii, cons
 
 void orc_texel_heights(const orc_cascade* cas, const orc_domain* dom, const double* cx,
                        const double* cy, const double* cs, const double* cv, long n,
-                       double sigma, double radius, const int* ii, const int* jj, long m,
-                       double* out) {
+                       double sigma, double radius, int kernel, const int* ii, const int* jj,
+                       long m, double* out) {
     unsigned char* vis = (unsigned char*)malloc((size_t)(m > 0 ? m : 1));
     orc_mask(cas, dom, ii, jj, m, vis, NULL);
     double* px = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
@@ -479,8 +489,8 @@ void orc_texel_heights(const orc_cascade* cas, const orc_domain* dom, const doub
         px[q] = cas->ox + (double)ii[q] * cas->h;
         py[q] = cas->oy + (double)jj[q] * cas->h;
     }
-    orc_rbf_points(cx, cy, cs, cv, n, sigma, radius, dom->width, dom->height, px, py, m, 1, out,
-                   NULL);
+    orc_rbf_points(cx, cy, cs, cv, n, sigma, radius, kernel, dom->width, dom->height, px, py, m, 1,
+                   out, NULL);
     for (long q = 0; q < m; ++q)
         if (!vis[q]) out[q] = -INFINITY;
     free(vis);

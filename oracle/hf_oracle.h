@@ -71,13 +71,14 @@ typedef struct {
 } orc_rcascade;
 
 /* ---- Eq. 1 / Eq. 2 ---- */
-double orc_rbf_weight(double dist, double c, double sigma, double radius);
+/* kernel 0: truncated Gaussian (Eq. 1); kernel 1: Wendland psi_{3,1} with support radius * c */
+double orc_rbf_weight(double dist, double c, double sigma, double radius, int kernel);
 void orc_cells_from_leaves(double root_cell, const int* level, const int* ix, const int* iy,
                            const float* value, long n, double* cx, double* cy, double* cs,
                            double* cv);
 /* mode 0: brute force over every cell; mode 1: exact binned enumeration */
 void orc_rbf_points(const double* cx, const double* cy, const double* cs, const double* cv,
-                    long n, double sigma, double radius, double dom_w, double dom_h,
+                    long n, double sigma, double radius, int kernel, double dom_w, double dom_h,
                     const double* px, const double* py, long m, int mode, double* out,
                     int* n_influencers);
 
@@ -92,7 +93,7 @@ void orc_mask(const orc_cascade* cas, const orc_domain* dom, const int* ii, cons
 /* heights of texels (i, j): Eq. 2 at visible texels, -inf elsewhere */
 void orc_texel_heights(const orc_cascade* cas, const orc_domain* dom, const double* cx,
                        const double* cy, const double* cs, const double* cv, long n,
-                       double sigma, double radius, const int* ii, const int* jj, long m,
+                       double sigma, double radius, int kernel, const int* ii, const int* jj, long m,
                        double* out);
 
 /* ---- Section 5: maximum mipmap and ray casting ---- */

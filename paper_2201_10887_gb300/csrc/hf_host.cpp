@@ -273,6 +273,7 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
     dp->C = C;
     dp->max_N = N;
     dp->precision = ctx->rbf.precision;
+    dp->kernel = ctx->rbf.kernel;
     dp->K = float(std::exp(-ctx->rbf.radius * ctx->rbf.radius / (2.0 * ctx->rbf.sigma * ctx->rbf.sigma)));
     int2* spans = reinterpret_cast<int2*>(scratch);
     float* xs = reinterpret_cast<float*>(scratch + size_t(C) * N * 8);
@@ -348,7 +349,10 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         return fail(HF_ERR_ARG, "unknown precision %d", rbf->precision);
     if (rbf->bucket_level > M) return fail(HF_ERR_ARG, "bucket_level %d > max_level %d", rbf->bucket_level, M);
     if (rbf->water != 0 && rbf->water != 1) return fail(HF_ERR_ARG, "water must be 0 or 1");
-    if (rbf->reserved != 0) return fail(HF_ERR_ARG, "reserved must be 0");
+    if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->kernel != HF_RBF_WENDLAND_C2)
+        return fail(HF_ERR_ARG, "unknown RBF kernel %d", rbf->kernel);
+    if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->precision != HF_PREC_FP32)
+        return fail(HF_ERR_ARG, "the Wendland kernel needs FP32 precision");
     if (rbf->water && rbf->precision != HF_PREC_FP32)
         return fail(HF_ERR_ARG, "the water layer needs FP32 precision");
 
@@ -397,7 +401,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     ctx->zmax = vmax;
     if (rbf->water) ctx->depth.assign(size_t(n_leaves), 0.f);
 
-    // records in (level, iy, ix) order: centre, exponent scale, value
+    // records in (level, iy, ix) order: centre, weight scale, value
     const double log2e = 1.4426950408889634;
     ctx->perm.resize(size_t(n_leaves));
     ctx->recs.resize(size_t(n_leaves));
@@ -406,9 +410,10 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         const int64_t s = lf.rank(l.level, l.ix, l.iy);
         const double c = d.root_cell / double(int64_t(1) << l.level);
         ctx->perm[size_t(k)] = s;
-        ctx->recs[size_t(s)] = make_float4(float((l.ix + 0.5) * c), float((l.iy + 0.5) * c),
-                                           float(-log2e / (2.0 * rbf->sigma * rbf->sigma * c * c)),
-                                           l.value);
+        // exponent scale of the weight (see rbf_weight in hf_kernels.cu)
+        const double scale = rbf->kernel == HF_RBF_WENDLAND_C2 ? 1.0 / (rbf->radius * c * rbf->radius * c)
+                                                               : -log2e / (2.0 * rbf->sigma * rbf->sigma * c * c);
+        ctx->recs[size_t(s)] = make_float4(float((l.ix + 0.5) * c), float((l.iy + 0.5) * c), float(scale), l.value);
     }
 
     // buckets: leaves at or below level B, coarser leaves split down to B
@@ -642,6 +647,7 @@ DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
     dp.max_N = N;
     dp.precision = ctx->rbf.precision;
     dp.water = ctx->rbf.water;
+    dp.kernel = ctx->rbf.kernel;
     dp.K = float(std::exp(-ctx->rbf.radius * ctx->rbf.radius / (2.0 * ctx->rbf.sigma * ctx->rbf.sigma)));
     for (int k = 0; k < C; ++k) {
         DiscCascade& dc = dp.cas[k];
@@ -862,6 +868,8 @@ int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
         if (!v || v->stage < 1) return fail(HF_ERR_STATE, "batch item %d: view slot %d has no camera", i, it.view_slot);
         if (!it.ctx->dev) return fail(HF_ERR_STATE, "batch item %d: persistent buffer not bound", i);
         if (it.ctx->rbf.water) return fail(HF_ERR_ARG, "batch item %d: batched frames do not carry the water layer", i);
+        if (it.ctx->rbf.kernel != HF_RBF_GAUSSIAN)
+            return fail(HF_ERR_ARG, "batch item %d: batched frames use the Gaussian kernel only", i);
         if (!it.t_dev || !it.hit_dev) return fail(HF_ERR_ARG, "batch item %d: null output buffer", i);
         nc += v->cam.n_cascades;
     }

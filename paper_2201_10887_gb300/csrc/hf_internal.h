@@ -115,6 +115,7 @@ struct DiscParams {
     int32_t max_N;
     int32_t precision;
     int32_t water;  // 1: also discretize the depths and write the water surface
+    int32_t kernel; // HF_RBF_* weight function
     float K;        // exp(-R^2 / (2 sigma^2))
     DiscCascade cas[HF_MAX_CASCADES];
 };

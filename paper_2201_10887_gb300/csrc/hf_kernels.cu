@@ -47,6 +47,27 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Weight of a candidate from q = k * d^2, k taken from its record:
+//   HF_RBF_GAUSSIAN (Eq. 1)   k = -log2(e) / (2 sigma^2 c^2):   w = max(2^q - K, 0)
+//   HF_RBF_WENDLAND_C2        k = 1 / (radius c)^2, r = sqrt(q): w = (1 - r)_+^4 (4 r + 1)
+// (Wendland's compactly supported C2 function psi_{3,1}, the same support
+// radius * c as the truncated Gaussian, so the same candidate lists serve.)
+template <int KERNEL>
+__device__ __forceinline__ float rbf_weight(float q, float K) {
+    if (KERNEL == HF_RBF_WENDLAND_C2) {
+        const float r = sqrt_approx(q);
+        const float t = fmaxf(1.f - r, 0.f), t2 = t * t;
+        return t2 * t2 * fmaf(4.f, r, 1.f);
+    }
+    return fmaxf(ex2_approx(q) - K, 0.f);
+}
+
 // ---------------------------------------------------------------------------
 // Candidate enumeration for one bucket square (Section 4: the cells that can
 // influence any point of the square).  Exact integer geometry in units of
@@ -341,7 +362,7 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
 // (terrain and depths live on the same cells, Section 2): the water surface
 // texel is v + sum w_i d_i / sum w_i where that depth is positive, else -inf.
 
-template <bool COH, bool WATER = false>
+template <bool COH, bool WATER = false, int KERNEL = HF_RBF_GAUSSIAN>
 __device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, const LookupTables& lt,
                                                  const ListsView& lv, DevStatus* status, int i, int j) {
     if (i >= q.N || j >= q.N) return;
@@ -370,7 +391,7 @@ __device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, 
         const int id = __ldg(ids + k);
         const float4 r = __ldg(lv.recs + id);
         const float dx = r.x - px, dy = r.y - py;
-        const float w = fmaxf(ex2_approx(r.z * fmaf(dx, dx, dy * dy)) - K, 0.f);
+        const float w = rbf_weight<KERNEL>(r.z * fmaf(dx, dx, dy * dy), K);
         sw += w;
         swv = fmaf(w, r.w, swv);
         if (WATER) swd = fmaf(w, __ldg(lv.depth + id), swd);
@@ -387,14 +408,14 @@ __device__ __forceinline__ void tile_texel(int t, int& di, int& dj) {
     dj = (warp >> 2) * 4 + (lane >> 3);
 }
 
-template <bool WATER>
+template <bool WATER, int KERNEL>
 __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
                                                         const __grid_constant__ LookupTables lt,
                                                         const ListsView lv, DevStatus* status) {
     int di, dj;
     tile_texel(threadIdx.x, di, dj);
-    discretize_texel<false, WATER>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di,
-                                   blockIdx.y * 8 + dj);
+    discretize_texel<false, WATER, KERNEL>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di,
+                                           blockIdx.y * 8 + dj);
 }
 
 // Reduced-precision discretization: the same texel mapping, bucket lookup and
@@ -531,16 +552,23 @@ int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsVi
                       DevStatus* status, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
-    if (p.water)
-        k_discretize_f32<true><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    cudaStream_t s = cudaStream_t(stream);
+    const bool wend = p.kernel == HF_RBF_WENDLAND_C2;
+    if (p.water && wend)
+        k_discretize_f32<true, HF_RBF_WENDLAND_C2><<<grid, 256, 0, s>>>(p, lt, lv, status);
+    else if (p.water)
+        k_discretize_f32<true, HF_RBF_GAUSSIAN><<<grid, 256, 0, s>>>(p, lt, lv, status);
+    else if (wend)
+        k_discretize_f32<false, HF_RBF_WENDLAND_C2><<<grid, 256, 0, s>>>(p, lt, lv, status);
     else
-        k_discretize_f32<false><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+        k_discretize_f32<false, HF_RBF_GAUSSIAN><<<grid, 256, 0, s>>>(p, lt, lv, status);
     return cudaGetLastError();
 }
 
 // Measurement pass: the discretization's texel mapping and inner loop, but
 // counting visible texels, list entries walked and terms with w > 0 instead
 // of writing heights.  Warp sums, one 64-bit atomic per warp and counter.
+template <int KERNEL>
 __global__ void __launch_bounds__(256) k_stats_f32(const __grid_constant__ DiscParams p,
                                                    const __grid_constant__ LookupTables lt,
                                                    const ListsView lv, DevStatus* status) {
@@ -563,7 +591,7 @@ __global__ void __launch_bounds__(256) k_stats_f32(const __grid_constant__ DiscP
                 for (int k = 0; k < n; ++k) {
                     const float4 r = __ldg(lv.recs + __ldg(ids + k));
                     const float dx = r.x - px, dy = r.y - py;
-                    infl += (ex2_approx(r.z * fmaf(dx, dx, dy * dy)) - p.K) > 0.f ? 1u : 0u;
+                    infl += rbf_weight<KERNEL>(r.z * fmaf(dx, dx, dy * dy), p.K) > 0.f ? 1u : 0u;
                 }
             }
         }
@@ -582,7 +610,10 @@ int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& l
                  DevStatus* status, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
-    k_stats_f32<<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    if (p.kernel == HF_RBF_WENDLAND_C2)
+        k_stats_f32<HF_RBF_WENDLAND_C2><<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
+    else
+        k_stats_f32<HF_RBF_GAUSSIAN><<<grid, dim3(32, 8), 0, cudaStream_t(stream)>>>(p, lt, lv, status);
     return cudaGetLastError();
 }
 
@@ -795,12 +826,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 __device__ __forceinline__ float exact_float(int x) {  // 0 <= x < 2^23
     return __int_as_float(x | 0x4B000000) - 8388608.0f;
 }

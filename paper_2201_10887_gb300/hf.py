@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhf.so")
 
 HF_OK, HF_ERR_ARG, HF_ERR_STATE, HF_ERR_NOMEM, HF_ERR_CUDA, HF_ERR_TIMEOUT, HF_ERR_DATA = 0, -1, -2, -3, -4, -5, -6
 HF_PREC_FP32, HF_PREC_FP16, HF_PREC_BF16 = 0, 1, 2
+HF_RBF_GAUSSIAN, HF_RBF_WENDLAND_C2 = 0, 1
 HF_MAX_LEVEL, HF_MAX_CASCADES, HF_MAX_POLY, HF_MAX_VIEWS = 15, 8, 32, 256
 
 ERROR_NAMES = {HF_ERR_ARG: "HF_ERR_ARG", HF_ERR_STATE: "HF_ERR_STATE", HF_ERR_NOMEM: "HF_ERR_NOMEM",
@@ -47,7 +48,7 @@ class hf_quadtree_desc(ct.Structure):
 
 class hf_rbf_params(ct.Structure):
     _fields_ = [("sigma", ct.c_double), ("radius", ct.c_double), ("precision", ct.c_int32),
-                ("bucket_level", ct.c_int32), ("water", ct.c_int32), ("reserved", ct.c_int32)]
+                ("bucket_level", ct.c_int32), ("water", ct.c_int32), ("kernel", ct.c_int32)]
 
 
 class hf_camera(ct.Structure):

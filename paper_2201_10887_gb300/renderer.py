@@ -29,18 +29,19 @@ class Renderer:
     root_ny, max_level and leaf arrays level, ix, iy, value.  With
     ``water=True`` the leaves also carry water depths (``update_water``) and
     every view gets a water surface texture per cascade (the max mipmap then
-    bounds both surfaces).
+    bounds both surfaces).  ``kernel`` selects the RBF weight (hf.HF_RBF_*).
     """
 
     def __init__(self, tree, sigma: float, radius: float, precision: int = hf.HF_PREC_FP32,
-                 bucket_level: int = -1, device=None, stream=None, water: bool = False):
+                 bucket_level: int = -1, device=None, stream=None, water: bool = False,
+                 kernel: int = hf.HF_RBF_GAUSSIAN):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
         desc = hf.hf_quadtree_desc(tree.origin_x, tree.origin_y, tree.root_cell, tree.root_nx,
                                    tree.root_ny, tree.max_level)
         leaves = hf.leaves_array(tree.level, tree.ix, tree.iy, tree.value)
-        rbf = hf.hf_rbf_params(sigma, radius, precision, bucket_level, 1 if water else 0, 0)
+        rbf = hf.hf_rbf_params(sigma, radius, precision, bucket_level, 1 if water else 0, kernel)
         self.water = bool(water)
         self.ctx = hf.hf_create_quadtree(desc, leaves, rbf)
         self.persistent_bytes, _ = hf.hf_query_bytes(self.ctx, 1, 2)

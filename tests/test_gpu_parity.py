@@ -22,9 +22,9 @@ def torch_cuda():
     return torch
 
 
-def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True):
+def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True, kernel=0):
     from paper_2201_10887_gb300 import Renderer
-    r = Renderer(scene.tree, scene.sigma, scene.radius, bucket_level=bucket_level)
+    r = Renderer(scene.tree, scene.sigma, scene.radius, bucket_level=bucket_level, kernel=kernel)
     t, hit = r.render(cam)
     r.sync()
     cells = orc.Cells(scene.tree)
@@ -39,7 +39,8 @@ def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True):
         bad, vis = check_mask(orc, info, cells, spans)
         assert bad == 0, f"cascade {c}: {bad} mask mismatches"
         tex = r.texture(0, c).cpu().numpy()
-        ref = orc.texel_heights(ocas(orc, info), cells, scene.sigma, scene.radius).reshape(info.N, info.N)
+        ref = orc.texel_heights(ocas(orc, info), cells, scene.sigma, scene.radius,
+                                kernel=kernel).reshape(info.N, info.N)
         assert np.array_equal(np.isfinite(tex), mask_from_spans(spans, info.N))
         both = np.isfinite(tex) & np.isfinite(ref)
         worst = max(worst, height_error(np.where(both, tex, -np.inf), np.where(both, ref, -np.inf), amp))
@@ -73,6 +74,16 @@ def test_ragged_sizes_and_cascades(orc, torch_cuda, tiny, N, W, H, C, lam):
     """Texture sides and image sizes that are not multiples of any tile."""
     cam = tiny.cameras[0].with_(n_cascades=C, cascade_size=N, width=W, height=H, split_lambda=lam)
     _frame_parity(orc, torch_cuda, tiny, cam)
+
+
+@pytest.mark.parametrize("N,C", [(256, 1), (100, 3)])
+def test_wendland_kernel_frame(orc, torch_cuda, tiny, N, C):
+    """Another interpolant in the discretization slot (Wendland's compactly
+    supported C2 function over the same supports): heights, mips and rays
+    against the oracle with the same weights."""
+    cam = tiny.cameras[0].with_(cascade_size=N, n_cascades=C)
+    worst, terr, nhit = _frame_parity(orc, torch_cuda, tiny, cam, kernel=orc.WENDLAND_C2)
+    assert nhit > 1000
 
 
 def test_far_world_origin(orc, torch_cuda):

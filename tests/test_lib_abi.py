@@ -231,9 +231,9 @@ def test_reduced_precision_offset_limits(hfmod, tiny):
 
 
 def test_water_layer_flags_and_sizes(hfmod, tiny):
-    """The water layer: FP32 only, flag 0/1, reserved 0; it adds 4 bytes per
+    """The water layer: FP32 only, flag 0/1; it adds 4 bytes per
     leaf to the persistent buffer and a second texture per cascade (one
-    mipmap bounds both surfaces)."""
+    mipmap bounds both surfaces).  RBF kernels: 0 or 1, FP32 only."""
     t = tiny.tree
     lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
     desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
@@ -245,7 +245,7 @@ def test_water_layer_flags_and_sizes(hfmod, tiny):
     assert v1 - v0 == 3 * 256 * 256 * 4
     for d in (plain, wet):
         hfmod.hf_destroy(d)
-    for args in ((0, -1, 2, 0), (1, -1, 1, 0), (2, -1, 1, 0), (0, -1, 0, 7)):
+    for args in ((0, -1, 2, 0), (1, -1, 1, 0), (2, -1, 1, 0), (0, -1, 0, 7), (1, -1, 0, 1), (2, -1, 0, 1)):
         with pytest.raises(hfmod.HFError) as e:
             hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, *args))
         assert e.value.code == hfmod.HF_ERR_ARG

@@ -157,3 +157,55 @@ def test_convexity_and_influencer_counts(orc, tiny):
     _, cnt = orc.rbf_points(uni, 1.5, 3.0, [7.5], [7.5], mode=0, with_counts=True)
     lattice = sum(1 for m in range(-3, 4) for n in range(-3, 4) if m * m + n * n < 9)
     assert cnt[0] == lattice == 25
+
+
+# ---- Wendland's psi_{3,1}: another interpolant in the discretization slot ----
+
+def test_wendland_values_support_and_smoothness(orc):
+    """psi_{3,1}(r) = (1 - r)_+^4 (4 r + 1) (Wendland, 1995) of r = d / (R c):
+    psi(0) = 1, psi(1/2) = 3/16, zero from the support radius R c on; the
+    function is C2 at the support edge (value, slope and curvature vanish
+    there) and flat at the centre; only d / c matters."""
+    W = orc.WENDLAND_C2
+    for R, c in [(3.0, 10.0), (3.5, 2.0), (1.0, 0.75)]:
+        def w(r):
+            return orc.rbf_weight(r * R * c, c, 1.5, R, W)
+        assert w(0.0) == 1.0
+        assert w(0.5) == pytest.approx(3.0 / 16.0, rel=1e-14)
+        assert w(1.0) == 0.0 and w(1.2) == 0.0 and w(0.999) > 0.0
+        h = 1e-3
+        assert abs((w(1.0) - w(1.0 - h)) / h) < 1e-7                         # slope -> 0
+        assert abs((w(1.0) - 2 * w(1.0 - h) + w(1.0 - 2 * h)) / h ** 2) < 2e-4  # curvature -> 0
+        assert abs((w(h) - w(0.0)) / h) < 1e-2                                # flat peak
+        assert w(0.3) > w(0.6) > w(0.9) > 0.0                                 # decreasing
+    for d in [0.0, 0.3, 1.1, 2.9]:
+        assert orc.rbf_weight(d, 1.0, 1.5, 3.0, W) == pytest.approx(orc.rbf_weight(8 * d, 8.0, 1.5, 3.0, W),
+                                                                 rel=1e-14, abs=1e-16)
+
+
+def test_wendland_constant_linear_and_binned(orc, tiny):
+    """With the Wendland weights Eq. 2 still reproduces a constant field on
+    the adaptive grid, a linear field at lattice-symmetric points of a
+    uniform grid, and the binned search still finds exactly the influencers
+    (the supports equal the Gaussian's truncation radius)."""
+    W = orc.WENDLAND_C2
+    cells = orc.Cells(tiny.tree)
+    cells.cv[:] = -7.5
+    rng = np.random.default_rng(3)
+    px = rng.uniform(0, tiny.tree.width, 1500)
+    py = rng.uniform(0, tiny.tree.height, 1500)
+    assert np.all(np.abs(orc.rbf_points(cells, tiny.sigma, tiny.radius, px, py, kernel=W) + 7.5) < 1e-11)
+    a, b, c0 = 0.37, -1.25, 40.0
+    uni = _uniform(24, c=2.0, values=lambda x, y: a * x + b * y + c0)
+    pts = [((i + ox) * 2.0, (j + oy) * 2.0) for i in range(8, 16) for j in range(8, 16)
+           for ox, oy in [(0.5, 0.5), (0.0, 0.0), (0.5, 0.0), (0.0, 0.5)]]
+    qx, qy = np.array(pts).T
+    v = orc.rbf_points(uni, 1.5, 3.0, qx, qy, mode=1, kernel=W)
+    assert np.max(np.abs(v - (a * qx + b * qy + c0))) < 1e-10
+    cells = orc.Cells(tiny.tree)
+    vb, nb = orc.rbf_points(cells, tiny.sigma, tiny.radius, px, py, mode=0, with_counts=True, kernel=W)
+    vn, nn = orc.rbf_points(cells, tiny.sigma, tiny.radius, px, py, mode=1, with_counts=True, kernel=W)
+    assert np.array_equal(nb, nn) and np.max(np.abs(vb - vn)) < 1e-9
+    # same support as the truncated Gaussian: the same influencing sets
+    _, ng = orc.rbf_points(cells, tiny.sigma, tiny.radius, px, py, mode=1, with_counts=True)
+    assert np.array_equal(nn, ng)

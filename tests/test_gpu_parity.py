@@ -6,8 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from _parity import (HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, check_mask, check_rays, frame_bracket,
-                     height_error, mask_from_spans, ocas)
+from _parity import (GRAZE_REL, HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, bracketed, check_mask, check_rays,
+                     frame_bracket, height_error, mask_from_spans, ocas, surface_bracket)
 
 pytestmark = pytest.mark.gpu
 
@@ -189,6 +189,55 @@ def test_minimal_texture(orc, torch_cuda, tiny):
     r.sync()
     tex = r.texture(0, 0).cpu().numpy()
     assert np.array_equal(r.mip(0, 0).cpu().numpy(), orc.maxmip(tex))
+    r.close()
+
+
+@pytest.mark.slow
+def test_maximum_cascades_and_size(orc, torch_cuda, tiny):
+    """HF_MAX_CASCADES cascades of the largest side (8192^2, a 14-level max
+    mipmap): full masks and mipmaps, sampled texels and rays."""
+    from paper_2201_10887_gb300 import Renderer, hf
+    cam = tiny.cameras[0].with_(n_cascades=hf.HF_MAX_CASCADES, cascade_size=8192, width=320, height=240)
+    r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    t, hit = r.render(cam)
+    r.sync()
+    cells = orc.Cells(tiny.tree)
+    amp = float(np.abs(cells.cv).max())
+    rng = np.random.default_rng(7)
+    texs, rcs = [], []
+    for c in range(cam.n_cascades):
+        info = r.cascade(0, c)
+        assert info.N == 8192
+        spans = r.spans(0, c).cpu().numpy()
+        tex = r.texture(0, c).cpu().numpy()
+        shown = mask_from_spans(spans, info.N)
+        assert np.array_equal(np.isfinite(tex), shown)
+        jj, ii = np.nonzero(shown)
+        if jj.size:
+            pick = rng.choice(jj.size, size=min(1500, jj.size), replace=False)
+            vis, _ = orc.mask(ocas(orc, info), cells, ii[pick], jj[pick])
+            assert vis.all()
+            ref = orc.texel_heights(ocas(orc, info), cells, tiny.sigma, tiny.radius, ii[pick], jj[pick])
+            got = tex[jj[pick], ii[pick]]
+            assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), amp)) <= HEIGHT_REL
+        assert np.array_equal(r.mip(0, c).cpu().numpy(), orc.maxmip(tex))
+        texs.append(tex)
+        rcs.append(RC(info))
+    gt, gh = t.cpu().numpy(), hit.cpu().numpy()
+    py = rng.integers(0, cam.height, 1500)
+    px = rng.integers(0, cam.width, 1500)
+    ot, oh, seg, _ = orc.raycast(cam, tiny.tree, rcs, texs, pixels=(px, py))
+    g_t, g_h = gt[py, px], gh[py, px]
+
+    def bracket(idx):                 # backward-error rule on the sampled pixels
+        tmax = np.nanmax(np.concatenate([np.where(g_h[idx] > 0, g_t[idx], np.nan), ot[idx], [0.0]]))
+        tu, hu, td, hd = surface_bracket(orc, cam, tiny.tree, rcs, texs, px[idx], py[idx],
+                                         GRAZE_REL * (tmax + amp))
+        return bracketed(g_t[idx], g_h[idx], seg[idx], tu, hu, td, hd)
+    frac, off, terr, _ = check_rays(g_t, g_h, ot, oh, seg, silhouette=np.zeros(px.size, bool), bracket=bracket)
+    assert frac <= 2e-3 and off == 0, (frac, off)
+    assert int(((g_h > 0) & (oh > 0)).sum()) > 500
+    assert terr <= RAY_REL, terr
     r.close()
 
 

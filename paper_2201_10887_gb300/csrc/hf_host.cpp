@@ -787,6 +787,7 @@ RayParams ray_params(const ViewSlot* v, bool water) {
         rc.inv_h = float(1.0 / ci.texel);
         rc.near_d = float(ci.near_depth);
         rc.far_ext = float(ci.far_ext_depth);
+        rc.budget = 8 * (2 * N + 8) * (rc.K + 2);
         int64_t off = 0;
         for (int L = 0; L < kMaxLevels; ++L) {
             rc.lvl_off[L] = int32_t(off);

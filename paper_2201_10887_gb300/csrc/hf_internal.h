@@ -143,6 +143,7 @@ struct RayCascade {
     float eu, ev;  // eye in this cascade's patch units
     float h, inv_h;
     float near_d, far_ext;  // projected-depth band
+    int32_t budget;         // bound on walk steps: 8 (2 N + 8) (K + 2)
     int32_t lvl_off[kMaxLevels];  // first float of mip level k
 };
 

@@ -622,30 +622,49 @@ int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& l
 // of the patch's four corner texels, -inf if one is invisible or the patch
 // lies in the padding; level k is the max of 2x2 entries of level k-1.
 // k_mip_lo: one CTA per 64x64 block of level 0 builds levels 0..6 of it
-// (each thread 4x4 level-0 entries from a 5x5 texel window, then 2x2, 1,
-// then shared memory).  k_mip_hi: one CTA per cascade builds levels 7..K.
+// (each thread 4x4 level-0 entries from a 5x5 texel window, then 2x2 and 1 in
+// registers, 3 and 4 across lanes, 5 and 6 in shared memory).  k_mip_hi: one
+// CTA per cascade builds levels 7..K.
 
 __device__ __forceinline__ int64_t mip_off(int P, int k) {
     const int64_t a = int64_t(P) * P, b = int64_t(P >> k) * (P >> k);
     return (a - b) * 4 / 3;
 }
 
-// Levels 0..6 of the 64 x 64 level-0 block (bx, by); 256 threads.
-template <bool COH, bool TWO = false>
-__device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int byi, float (*sm)[17]) {
-    const int P = c.P, N = c.N, K = c.K;
-    if (bxi * 64 >= P || byi * 64 >= P) return;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int pi0 = bxi * 64 + tx * 4, pj0 = byi * 64 + ty * 4;
-    float t[5][5];
+// 5 x 5 texels from (pi0, pj0): -inf outside the texture.  Rows are read as
+// one float4 plus a scalar where the texture's rows are 16-byte aligned
+// (N % 4 == 0) and the window lies inside them, else texel by texel.
+template <bool COH>
+__device__ __forceinline__ void load_window(const float* __restrict__ tex, int N, int pi0, int pj0, float (&t)[5][5]) {
+    const bool vec = (N & 3) == 0 && pi0 + 4 < N;
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
+    for (int r = 0; r < 5; ++r) {
+        const int jj = pj0 + r;
+        const float* row = tex + size_t(jj) * N;
+        if (jj >= N) {
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            const int ii = pi0 + s, jj = pj0 + r;
-            t[r][s] = (ii < N && jj < N) ? ldc<COH>(c.tex + size_t(jj) * N + ii) : -INFINITY;
+            for (int s = 0; s < 5; ++s) t[r][s] = -INFINITY;
+        } else if (vec) {
+            const float4 v = ldc<COH>(reinterpret_cast<const float4*>(row + pi0));
+            t[r][0] = v.x;
+            t[r][1] = v.y;
+            t[r][2] = v.z;
+            t[r][3] = v.w;
+            t[r][4] = ldc<COH>(row + pi0 + 4);
+        } else {
+#pragma unroll
+            for (int s = 0; s < 5; ++s) t[r][s] = pi0 + s < N ? ldc<COH>(row + pi0 + s) : -INFINITY;
         }
-    float m0[4][4];
+    }
+}
+
+// Level-0 entries of the 4 x 4 patches whose lower corners are (pi0 + s, pj0 + r):
+// the maximum of the four corners, -inf for a patch with an undefined corner
+// or beyond the N-1 patches of a row.
+template <bool COH>
+__device__ __forceinline__ void patch_maxima(const float* __restrict__ tex, int N, int pi0, int pj0, float (&m0)[4][4]) {
+    float t[5][5];
+    load_window<COH>(tex, N, pi0, pj0, t);
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -655,23 +674,30 @@ __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int b
                             isfinite(d) && isfinite(e);
             m0[r][s] = ok ? fmaxf(fmaxf(a, b), fmaxf(d, e)) : -INFINITY;
         }
-    if (TWO) {  // water layer: the entry bounds the water patch too, where it exists
-#pragma unroll
-        for (int r = 0; r < 5; ++r)
-#pragma unroll
-            for (int s = 0; s < 5; ++s) {
-                const int ii = pi0 + s, jj = pj0 + r;
-                t[r][s] = (ii < N && jj < N) ? ldc<COH>(c.wtex + size_t(jj) * N + ii) : -INFINITY;
-            }
+}
+
+// Levels 0..6 of one 64 x 64 block of patches (256 threads, 4 x 4 patches
+// each).  Warp w covers threads tx in [8 (w & 1), +8), ty in [4 (w >> 1), +4):
+// levels 1 and 2 stay in registers, levels 3 and 4 are 2 x 2 reductions across
+// lanes (__shfl_xor_sync), levels 5 and 6 combine the block's sixteen level-4
+// entries through shared memory.  With TWO (the water layer) a level-0 entry
+// bounds the water patch too, where it exists.
+template <bool COH, bool TWO = false>
+__device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int byi, float (*sm)[17]) {
+    const int P = c.P, N = c.N, K = c.K;
+    if (bxi * 64 >= P || byi * 64 >= P) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
+    const int pi0 = bxi * 64 + tx * 4, pj0 = byi * 64 + ty * 4;
+    float m0[4][4];
+    patch_maxima<COH>(c.tex, N, pi0, pj0, m0);
+    if (TWO) {
+        float w0[4][4];
+        patch_maxima<COH>(c.wtex, N, pi0, pj0, w0);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const float a = t[r][s], b = t[r][s + 1], d = t[r + 1][s], e = t[r + 1][s + 1];
-                const bool ok = (pi0 + s < N - 1) && (pj0 + r < N - 1) && isfinite(a) && isfinite(b) &&
-                                isfinite(d) && isfinite(e);
-                if (ok) m0[r][s] = fmaxf(m0[r][s], fmaxf(fmaxf(a, b), fmaxf(d, e)));
-            }
+            for (int s = 0; s < 4; ++s) m0[r][s] = fmaxf(m0[r][s], w0[r][s]);
     }
     if (pi0 < P && pj0 < P) {
 #pragma unroll
@@ -705,24 +731,40 @@ __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int b
         const int P2 = P >> 2, pi2 = pi0 >> 2, pj2 = pj0 >> 2;
         if (pi2 < P2 && pj2 < P2) c.mip[mip_off(P, 2) + size_t(pj2) * P2 + pi2] = m2;
     }
-    sm[ty][tx] = m2;
-    __syncthreads();
-    int n = 8;
-    for (int k = 3; k <= 6; ++k, n >>= 1) {
-        if (k > K) break;
-        float v = -INFINITY;
-        const int x = threadIdx.x % n, y = threadIdx.x / n;
-        const bool act = threadIdx.x < n * n;
-        if (act) v = fmaxf(fmaxf(sm[2 * y][2 * x], sm[2 * y][2 * x + 1]),
-                           fmaxf(sm[2 * y + 1][2 * x], sm[2 * y + 1][2 * x + 1]));
-        __syncthreads();
-        if (act) {
-            sm[y][x] = v;
-            const int Pk = P >> k, gx = bxi * n + x, gy = byi * n + y;
-            if (gx < Pk && gy < Pk) c.mip[mip_off(P, k) + size_t(gy) * Pk + gx] = v;
-        }
-        __syncthreads();
+    // level 3: threads (tx, tx ^ 1) x (ty, ty ^ 1) are lanes (l, l ^ 1) x (l, l ^ 8)
+    float m3 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, 1));
+    m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, 8));
+    if (K >= 3 && ((tx | ty) & 1) == 0) {
+        const int P3 = P >> 3, gx = bxi * 8 + (tx >> 1), gy = byi * 8 + (ty >> 1);
+        if (gx < P3 && gy < P3) c.mip[mip_off(P, 3) + size_t(gy) * P3 + gx] = m3;
     }
+    // level 4: tx bit 1 is lane bit 1, ty bit 1 is lane bit 4
+    float m4 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, 2));
+    m4 = fmaxf(m4, __shfl_xor_sync(0xffffffffu, m4, 16));
+    const bool lead4 = ((tx | ty) & 3) == 0;
+    if (K >= 4 && lead4) {
+        const int P4 = P >> 4, gx = bxi * 4 + (tx >> 2), gy = byi * 4 + (ty >> 2);
+        if (gx < P4 && gy < P4) c.mip[mip_off(P, 4) + size_t(gy) * P4 + gx] = m4;
+    }
+    if (K < 5) return;
+    // levels 5 and 6 from the 4 x 4 level-4 entries of the block
+    if (lead4) sm[ty >> 2][tx >> 2] = m4;
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int x = threadIdx.x & 1, y = threadIdx.x >> 1;
+        const float v = fmaxf(fmaxf(sm[2 * y][2 * x], sm[2 * y][2 * x + 1]),
+                              fmaxf(sm[2 * y + 1][2 * x], sm[2 * y + 1][2 * x + 1]));
+        const int P5 = P >> 5, gx = bxi * 2 + x, gy = byi * 2 + y;
+        if (gx < P5 && gy < P5) c.mip[mip_off(P, 5) + size_t(gy) * P5 + gx] = v;
+        sm[4 + y][x] = v;
+    }
+    __syncthreads();
+    if (K >= 6 && threadIdx.x == 0) {
+        const float v = fmaxf(fmaxf(sm[4][0], sm[4][1]), fmaxf(sm[5][0], sm[5][1]));
+        const int P6 = P >> 6;
+        if (bxi < P6 && byi < P6) c.mip[mip_off(P, 6) + size_t(byi) * P6 + bxi] = v;
+    }
+    __syncthreads();
 }
 
 template <bool TWO>
@@ -731,7 +773,6 @@ __global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParam
     mip_lo_block<false, TWO>(p.cas[blockIdx.z], blockIdx.x, blockIdx.y, sm);
 }
 
-// Levels 7..K of one cascade from level 6 (any block size; s0, s1 hold 4096 floats each).
 template <bool COH>
 __device__ __forceinline__ void mip_hi_levels(const MipCascade& c, float* s0, float* s1) {
     const int P = c.P, K = c.K;
@@ -820,6 +861,8 @@ int launch_maxmip(const MipParams& p, void* stream) {
 // bit for bit.
 
 constexpr int kRayStartLevel = 6;
+constexpr int kTopSlot = kMaxLevels - 1;  // level offsets need columns 0..K <= 13 (side <= 8192)
+static_assert(kMaxCascadeSize <= 8192, "a larger side needs more mip levels than the top slot leaves");
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -897,7 +940,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const int N = c.N, P = c.P, K = c.K;
     const float* __restrict__ mip = c.mip;
     const float* __restrict__ tex = c.tex;
-    const float top = ldc<COH>(mip + off[K]);
+    const float top = __int_as_float(off[kTopSlot]);
     if (!(top > -INFINITY)) return false;  // nothing visible in this cascade
     Ray r;
     r.eu = c.eu;
@@ -923,7 +966,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
     int k = min(K, kRayStartLevel);
     float t = ta;
-    const int budget = 8 * (2 * N + 8) * (K + 2);
+    const int budget = c.budget;
     for (int it = 0; it < budget; ++it) {
         const int ni = ci >> k, nj = cj >> k;
         const float tx = fmaf(exact_float((ni + bu) << k), idu, ou);
@@ -1090,9 +1133,15 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
     }
 }
 
+// Per cascade the mip level offsets and, in the last column, the top entry
+// (the cascade's maximum, read by every ray before its walk).
+template <bool COH>
 __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_off)[kMaxLevels], int tid, int nthreads) {
-    for (int e = tid; e < p.C * kMaxLevels; e += nthreads)
-        s_off[e / kMaxLevels][e % kMaxLevels] = p.cas[e / kMaxLevels].lvl_off[e % kMaxLevels];
+    for (int e = tid; e < p.C * kMaxLevels; e += nthreads) {
+        const int c = e / kMaxLevels, L = e % kMaxLevels;
+        const RayCascade& rc = p.cas[c];
+        s_off[c][L] = L == kTopSlot ? __float_as_int(ldc<COH>(rc.mip + rc.lvl_off[rc.K])) : rc.lvl_off[L];
+    }
 }
 
 // 9 CTAs of 128 threads per SM leave the walk its 56 registers without spills
@@ -1100,7 +1149,7 @@ __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_o
 template <bool COUNT, bool WATER>
 __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
     __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
-    load_level_offsets(p, s_off, threadIdx.y * 16 + threadIdx.x, 128);
+    load_level_offsets<false>(p, s_off, threadIdx.y * 16 + threadIdx.x, 128);
     __syncthreads();
     unsigned visits = 0, tests = 0;
     raycast_pixel<COUNT, false, WATER>(p, s_off, status, blockIdx.x * 16 + threadIdx.x, blockIdx.y * 8 + threadIdx.y,
@@ -1206,7 +1255,7 @@ __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const Batch
         for (int c = 0; c < I.n_cascades; ++c)
             wait_count(done + 4 * (I.first_cascade + c) + kPhaseMipHi, 1u, I.status, uint32_t(u));
     }
-    load_level_offsets(I.ray, off, threadIdx.x, blockDim.x);
+    load_level_offsets<COH>(I.ray, off, threadIdx.x, blockDim.x);
     __syncthreads();
     const int local = u - h->phase_base[kPhaseRays] - I.ray_unit_base;
     const int tw = h->ray_tile_w, th = h->ray_tile_h;

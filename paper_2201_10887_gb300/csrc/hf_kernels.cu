@@ -846,8 +846,9 @@ int launch_maxmip(const MipParams& p, void* stream) {
 //
 // Per-step arithmetic is kept small: exit times are fma(boundary, 1/d, -e/d)
 // with 1/d = 0, -e/d = +inf for an axis-parallel ray (no branch), integer
-// node boundaries become floats through the exact 2^23 bit trick, level
-// offsets come from shared memory, and all divisions happen once per ray.
+// node boundaries become floats by one exact conversion (I2F, on the lightly
+// used conversion pipe), level offsets come from shared memory, and all
+// divisions happen once per ray.
 // Screen coordinates are one fma per axis with host-computed scales.  The
 // per-ray reciprocals of the direction and the divisions and square root of
 // the patch root use the hardware approximations (rcp.approx, div.approx,
@@ -869,10 +870,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float exact_float(int x) {  // 0 <= x < 2^23
-    return __int_as_float(x | 0x4B000000) - 8388608.0f;
-}
-
 struct Ray {
     float eu, ev, ez;  // origin in patch units (u, v) and metres (z)
     float du, dv, dz;  // per metre of t
@@ -969,8 +966,8 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const int budget = c.budget;
     for (int it = 0; it < budget; ++it) {
         const int ni = ci >> k, nj = cj >> k;
-        const float tx = fmaf(exact_float((ni + bu) << k), idu, ou);
-        const float ty = fmaf(exact_float((nj + bv) << k), idv, ov);
+        const float tx = fmaf(__int2float_rn((ni + bu) << k), idu, ou);
+        const float ty = fmaf(__int2float_rn((nj + bv) << k), idv, ov);
         const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
         const float zmin = fmaf(zneg ? te : t, r.dz, ez);
         const float mx = ldc<COH>(mip + off[k] + nj * (P >> k) + ni);

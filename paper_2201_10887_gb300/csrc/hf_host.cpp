@@ -36,6 +36,26 @@ int cuda_fail(int e, const char* what) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Bits of x rounded to nearest even in BF16 / FP16 (normal FP16 results only).
+uint32_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+uint32_t f16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    const uint32_t sign = (u >> 16) & 0x8000u;
+    int e = int((u >> 23) & 0xFF) - 127 + 15;
+    uint32_t m = (u & 0x7FFFFFu) >> 13, rem = u & 0x1FFFu;
+    if (rem > 0x1000u || (rem == 0x1000u && (m & 1u))) ++m;
+    if (m == 0x400u) {
+        m = 0;
+        ++e;
+    }
+    return sign | (uint32_t(e) << 10) | m;
+}
+
 // Per-level occupancy bitmaps on the host (see hfi::Bitmaps).
 struct HostBitmaps {
     std::vector<uint64_t> bits;
@@ -122,7 +142,7 @@ struct ViewSlot {
 // Device layout of the persistent buffer.
 struct PersistentLayout {
     size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx;
-    size_t pair_offsets, coords, values;  // reduced-precision lists (0 bytes for FP32)
+    size_t pair_offsets, pairs;          // reduced-precision lists (0 bytes for FP32)
     size_t depth;                         // water depths (0 bytes without the water layer)
     size_t total;
 };
@@ -142,6 +162,7 @@ struct hf_ctx {
     std::vector<int64_t> offsets;  // n_buckets + 1
     std::vector<int64_t> pair_offsets;  // n_buckets + 1 (reduced precision only)
     int64_t n_pairs = 0;
+    uint32_t kb2 = 0;              // packed level-0 scale bits of the compact lists
     std::vector<float> staged;     // values in sorted order for hf_update_values
     std::vector<float> depth;      // water depths in sorted order (water layer only)
     char* dev = nullptr;
@@ -162,8 +183,7 @@ struct hf_ctx {
         l.idx = o; o = align256(o + size_t(n_cand) * 4);
         const bool compact = rbf.precision != HF_PREC_FP32;
         l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
-        l.coords = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
-        l.values = o; o = align256(o + (compact ? size_t(n_pairs) * 8 : 0));
+        l.pairs = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
         l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves) * 4 : 0));
         l.total = o;
         return l;
@@ -193,8 +213,8 @@ struct hf_ctx {
     CompactView compact() const {
         CompactView v;
         v.pair_offsets = reinterpret_cast<const int64_t*>(dev + lay.pair_offsets);
-        v.coords = reinterpret_cast<uint4*>(dev + lay.coords);
-        v.values = reinterpret_cast<float2*>(dev + lay.values);
+        v.pairs = reinterpret_cast<uint4*>(dev + lay.pairs);
+        v.kb2 = kb2;
         v.q = float(0.5 * c_fin);
         v.inv_q = float(2.0 / c_fin);
         return v;
@@ -463,6 +483,19 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         if (span > limit)
             return fail(HF_ERR_ARG, "candidate offsets span %.0f half-cells, more than the %s path holds exactly (%.0f)",
                         span, rbf->precision == HF_PREC_FP16 ? "FP16" : "BF16", limit);
+        // exponent scales per squared half-cell: the finest level's is -log2(e) / (8 sigma^2);
+        // level L's lowers the exponent by 2 (M - L), which must stay a normal number
+        const bool f16 = rbf->precision == HF_PREC_FP16;
+        const float kM = float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
+        const uint32_t kMb = f16 ? f16_bits(kM) : bf16_bits(kM);
+        const int shift = f16 ? 10 : 7, emask = f16 ? 31 : 255;
+        const int eM = int((kMb >> shift) & uint32_t(emask));
+        if (eM >= emask || eM - 2 * (M - lmin) < 1)
+            return fail(HF_ERR_ARG, "the %s exponent scales of levels %d..%d leave the normal range",
+                        f16 ? "FP16" : "BF16", lmin, M);
+        const uint32_t step = 2u << shift;
+        const uint32_t kb = kMb - uint32_t(M) * step;  // level 0's bits, modulo 2^32
+        ctx->kb2 = kb * 0x10001u;
         ctx->pair_offsets.resize(size_t(ctx->n_buckets) + 1);
         int64_t pr = 0;
         for (int64_t b = 0; b < ctx->n_buckets; ++b) {

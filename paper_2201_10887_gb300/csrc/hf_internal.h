@@ -65,18 +65,22 @@ struct ListsView {
     const float* depth;      // per leaf water depth (water layer only, else null)
 };
 
-// Compact candidate lists of the reduced-precision discretization: per bucket
-// its candidates in pairs.  Pair p holds eight 16-bit values (FP16 or BF16)
-// {x0, x1, y0, y1, k0, k1, 0, 0}: the candidates' centres relative to the
-// bucket's lower corner in units of half a finest cell (small integers, exact
-// in the 16-bit type) and their exponent scales -log2(e) q^2 / (2 sigma^2 c^2)
-// per squared unit; the two values stay FP32.  An odd list is padded with a
-// far-away, zero-weight entry.
+// Compact candidate lists of the reduced-precision discretization: per
+// bucket its candidates in pairs of 16 bytes: {x0 x1, y0 y1} in the 16-bit
+// type (FP16 or BF16), the candidates' centres relative to the bucket's lower
+// corner in units of half a finest cell (small integers, exact in the 16-bit
+// type), then the two FP32 values whose 4 lowest mantissa bits carry the
+// candidates' levels L.  The 16-bit exponent scale of level L,
+// -log2(e) q^2 / (2 sigma^2 c_L^2), is the finest level's with the exponent
+// field lowered by 2 (max_level - L): its bits are L * step + kb, step the
+// exponent unit x 2, so kb2 = kb * 0x10001 gives both scales of a pair with
+// one integer multiply-add.  An odd list is padded with a far-away entry of
+// value 0.
 struct CompactView {
     const int64_t* pair_offsets;  // n_buckets + 1
-    uint4* coords;                // per pair
-    float2* values;               // per pair
+    uint4* pairs;                 // per pair
     float q, inv_q;               // half a finest cell (m) and its inverse
+    uint32_t kb2;                 // (bits of the level-0 scale) * 0x10001, see above
 };
 
 // Per-frame cascade data for the prep kernel (visible rows, texel coordinates).

@@ -209,9 +209,14 @@ int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsV
 }
 
 // Compact pair lists for the reduced-precision path, one thread per bucket
-// (same (word, bit) mapping as the list fill).  Centres are converted from
-// the FP32 records: x / q is an exact integer for cells of a power-of-two
-// hierarchy, so the bucket-relative offsets are exact.
+// (same (word, bit) mapping as the list fill).  A pair of consecutive
+// candidates takes 16 bytes: x0 x1 and y0 y1 in the 16-bit type (centres
+// relative to the bucket's lower corner in units of half a finest cell: exact
+// small integers for cells of a power-of-two hierarchy), then the two FP32
+// values with their 4 lowest mantissa bits replaced by the candidates' levels
+// (a change of at most 15 ulp).  The kernel rebuilds a candidate's 16-bit
+// exponent scale from its level.  An odd list ends with a far-away entry of
+// value 0.
 template <int PREC>
 __device__ __forceinline__ unsigned short to16(float x) {
     if (PREC == HF_PREC_FP16) return __half_as_ushort(__float2half_rn(x));
@@ -234,30 +239,30 @@ __global__ void __launch_bounds__(256) k_fill_compact(const __grid_constant__ Fi
     const float x0q = float(bx << (M - Lb + 1)), y0q = float(by << (M - Lb + 1));
     const int64_t beg = a.lv.offsets[id], n = a.lv.offsets[id + 1] - beg;
     const int64_t pb = cv.pair_offsets[id];
-    const float q2 = cv.q * cv.q;
     for (int64_t m = 0; m < 2 * ((n + 1) / 2); m += 2) {
-        float xs[2], ys[2], ks[2], vs[2];
+        float xs[2], ys[2];
+        uint32_t vb[2];
         for (int s = 0; s < 2; ++s) {
             if (m + s < n) {
-                const float4 r = a.lv.recs[a.lv.idx[beg + m + s]];
+                const int32_t leaf = a.lv.idx[beg + m + s];
+                const float4 r = a.lv.recs[leaf];
+                int L = 0;  // records are sorted by level
+                while (L < M && leaf >= a.et.leaves.base[L + 1]) ++L;
                 xs[s] = r.x * cv.inv_q - x0q;
                 ys[s] = r.y * cv.inv_q - y0q;
-                ks[s] = r.z * q2;
-                vs[s] = r.w;
-            } else {  // padding: far away, zero weight
+                vb[s] = (__float_as_uint(r.w) & ~15u) | uint32_t(L);
+            } else {  // padding: far away, value 0
                 xs[s] = 1024.f;
                 ys[s] = 1024.f;
-                ks[s] = -1024.f;
-                vs[s] = 0.f;
+                vb[s] = uint32_t(M);
             }
         }
         uint4 c;
         c.x = uint32_t(to16<PREC>(xs[0])) | (uint32_t(to16<PREC>(xs[1])) << 16);
         c.y = uint32_t(to16<PREC>(ys[0])) | (uint32_t(to16<PREC>(ys[1])) << 16);
-        c.z = uint32_t(to16<PREC>(ks[0])) | (uint32_t(to16<PREC>(ks[1])) << 16);
-        c.w = 0u;
-        cv.coords[pb + m / 2] = c;
-        cv.values[pb + m / 2] = make_float2(vs[0], vs[1]);
+        c.z = vb[0];
+        c.w = vb[1];
+        cv.pairs[pb + m / 2] = c;
     }
 }
 
@@ -451,6 +456,7 @@ __device__ __forceinline__ int64_t lookup_bucket_at(const LookupTables& lt, floa
 
 struct F16Ops {
     typedef __half2 T;
+    static constexpr uint32_t kStep = 1u << 11;  // x4 in the exponent field
     static __device__ __forceinline__ T make(float a) { return __float2half2_rn(a); }
     static __device__ __forceinline__ T bits(uint32_t u) {
         T r;
@@ -468,6 +474,7 @@ struct F16Ops {
 
 struct BF16Ops {
     typedef __nv_bfloat162 T;
+    static constexpr uint32_t kStep = 1u << 8;   // x4 in the exponent field
     static __device__ __forceinline__ T make(float a) { return __float2bfloat162_rn(a); }
     static __device__ __forceinline__ T bits(uint32_t u) {
         T r;
@@ -509,20 +516,21 @@ __device__ __forceinline__ void discretize_texel_mixed(const DiscCascade& q, flo
     const T ONE = Ops::make(1.f);
     const int64_t pb = __ldg(cv.pair_offsets + bucket);
     const int np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
-    const uint4* cc = cv.coords + pb;
-    const float2* vv = cv.values + pb;
+    const uint4* cc = cv.pairs + pb;
+    const uint32_t kb2 = cv.kb2;
     float sw = 0.f, swv = 0.f;
 #pragma unroll 2
     for (int k = 0; k < np; ++k) {
         const uint4 c = __ldg(cc + k);
-        const float2 v = __ldg(vv + k);
         const T dx = __hsub2(Ops::bits(c.x), PX);
         const T dy = __hsub2(Ops::bits(c.y), PY);
         const T d2 = __hfma2(dx, dx, __hmul2(dy, dy));
-        const T e = Ops::exp2(__hmul2(Ops::bits(c.z), d2));
+        // both levels into one word (L0 | L1 << 16), then both 16-bit scales in one IMAD
+        const uint32_t lv = __byte_perm(c.z, c.w, 0x5410) & 0x000F000Fu;
+        const T e = Ops::exp2(__hmul2(Ops::bits(lv * Ops::kStep + kb2), d2));
         const float2 w = Ops::widen(__hfma2_relu(e, ONE, NK));
         sw += w.x + w.y;
-        swv = fmaf(w.x, v.x, fmaf(w.y, v.y, swv));
+        swv = fmaf(w.x, __uint_as_float(c.z), fmaf(w.y, __uint_as_float(c.w), swv));
     }
     *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
 }

@@ -569,10 +569,11 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
     if (!ctx || !values) return fail(HF_ERR_ARG, "null argument");
     if (n_values != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld values", (long long)ctx->n_leaves);
     if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    for (int64_t k = 0; k < n_values; ++k)  // validate before touching any state
+        if (!std::isfinite(values[k])) return fail(HF_ERR_ARG, "value %lld not finite", (long long)k);
     ctx->staged.resize(size_t(n_values));
     float vmin = INFINITY, vmax = -INFINITY;
     for (int64_t k = 0; k < n_values; ++k) {
-        if (!std::isfinite(values[k])) return fail(HF_ERR_ARG, "value %lld not finite", (long long)k);
         const int64_t s = ctx->perm[size_t(k)];
         ctx->staged[size_t(s)] = values[k];
         ctx->recs[size_t(s)].w = values[k];

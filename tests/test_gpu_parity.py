@@ -177,6 +177,18 @@ def test_update_values(orc, torch_cuda, tiny):
         info = r.cascade(0, c)
         ref = orc.texel_heights(ocas(orc, info), cells, tiny.sigma, tiny.radius).reshape(info.N, info.N)
         assert height_error(r.texture(0, c).cpu().numpy(), ref, amp) <= HEIGHT_REL
+    # a rejected update (a NaN in the middle) changes nothing
+    from paper_2201_10887_gb300 import hf
+    before = [r.texture(0, c).clone() for c in range(2)]
+    bad = new.copy()
+    bad[bad.size // 2] = np.nan
+    with pytest.raises(hf.HFError) as e:
+        r.update_values(bad)
+    assert e.value.code == hf.HF_ERR_ARG
+    r.render(cam)
+    r.sync()
+    for c in range(2):
+        assert torch_cuda.equal(r.texture(0, c), before[c])
     r.close()
 
 

@@ -316,6 +316,16 @@ int hf_frame_batch(const hf_batch_item* items, int32_t n, int32_t flags, void* h
  * last hf_sync (HF_ERR_TIMEOUT, HF_ERR_DATA) or by the CUDA runtime. */
 int hf_sync(hf_ctx* ctx, void* stream);
 
+/* Self-test of the failure path (no counterpart in the paper): the device
+ * loops that could wait on other work -- the batched launch's waits on
+ * completion counters -- and the ray walk are bounded, and when a bound runs
+ * out the kernel records HF_ERR_TIMEOUT in the context's status block and
+ * returns instead of hanging.  This launches one CTA that waits, polling at
+ * most `polls` times (1..2^20; a poll is a short sleep and one load), on a
+ * status word that nothing sets: the next hf_sync returns HF_ERR_TIMEOUT, clears the status,
+ * and the context stays usable.  For tests of error handling. */
+int hf_selftest_wait_timeout(hf_ctx* ctx, int32_t polls, void* stream);
+
 /* Frees the context's host memory.  Device buffers belong to the caller. */
 void hf_destroy(hf_ctx* ctx);
 

@@ -1078,9 +1078,19 @@ int hf_sync(hf_ctx* ctx, void* stream) {
         e = cudaMemset(ctx->d_status(), 0, 8);
         if (e) return cuda_fail(e, "status reset");
         if (st.flags & kStatusTimeout)
-            return fail(HF_ERR_TIMEOUT, "a ray traversal exceeded its step budget (pixel %u)", st.detail);
+            return fail(HF_ERR_TIMEOUT, "a bounded device loop gave up (a ray walk over its step budget or a "
+                        "batch wait over its poll limit; detail %u)", st.detail);
         return fail(HF_ERR_DATA, "device consistency check failed (item %u)", st.detail);
     }
+    return HF_OK;
+}
+
+int hf_selftest_wait_timeout(hf_ctx* ctx, int32_t polls, void* stream) {
+    if (!ctx) return fail(HF_ERR_ARG, "null context");
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    if (polls < 1 || polls > (1 << 20)) return fail(HF_ERR_ARG, "polls must be 1..2^20");
+    int e = launch_selftest_wait(ctx->d_status(), polls, stream);
+    if (e) return cuda_fail(e, "self-test launch");
     return HF_OK;
 }
 

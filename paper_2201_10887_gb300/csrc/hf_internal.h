@@ -22,7 +22,7 @@ struct DevStatus {
     uint32_t detail;
     unsigned long long counters[3 * HF_MAX_CASCADES];  // measurement pass (hf_view_stats)
     unsigned long long ray_counters[2];                  // measurement pass (hf_ray_stats)
-    uint32_t pad[10];
+    uint32_t pad[10];  // pad[0]: the never-set flag of hf_selftest_wait_timeout
 };
 static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
 
@@ -228,6 +228,7 @@ int launch_raycast(const RayParams& p, DevStatus* status, void* stream);
 int launch_raycast_count(const RayParams& p, DevStatus* status, void* stream);
 int batch_persistent_blocks(int* blocks_plain, int* blocks_rays);
 int launch_batch(const BatchHeader& h, void* dev_buf, void* stream);
+int launch_selftest_wait(DevStatus* status, int limit, void* stream);
 
 // Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the
 // prep / discretize parameters for output textures `tex` and the scratch

@@ -1205,11 +1205,11 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
 }
 
 __device__ __forceinline__ void wait_count(const uint32_t* ctr, uint32_t target, DevStatus* status,
-                                           uint32_t detail) {
+                                           uint32_t detail, int limit = kWaitLimit) {
     if (threadIdx.x == 0) {
         int it = 0;
         while (ld_acquire(ctr) < target) {
-            if (++it > kWaitLimit) {
+            if (++it > limit) {
                 report(status, kStatusTimeout, detail);
                 break;
             }
@@ -1217,6 +1217,19 @@ __device__ __forceinline__ void wait_count(const uint32_t* ctr, uint32_t target,
         }
     }
     __syncthreads();
+}
+
+// Self-test of the failure path: one CTA waits, at most `limit` polls, on a
+// word of the status block that nothing sets.
+__global__ void __launch_bounds__(32) k_selftest_wait(DevStatus* status, int limit) {
+    wait_count(&status->pad[0], 1u, status, 0xFFFFFFFEu, limit);
+}
+
+int launch_selftest_wait(DevStatus* status, int limit, void* stream) {
+    cudaError_t e = cudaMemsetAsync(&status->pad[0], 0, sizeof(uint32_t), cudaStream_t(stream));
+    if (e != cudaSuccess) return e;
+    k_selftest_wait<<<1, 32, 0, cudaStream_t(stream)>>>(status, limit);
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ void signal_done(uint32_t* ctr) {

@@ -29,7 +29,7 @@ EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_up
             "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
-            "hf_batch_launch", "hf_frame_batch", "hf_update_water"]
+            "hf_batch_launch", "hf_frame_batch", "hf_update_water", "hf_selftest_wait_timeout"]
 HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
 HF_BATCH_PERSISTENT = 16
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
@@ -104,6 +104,7 @@ def _load():
         "hf_bind_persistent": [vp, vp, sz, vp],
         "hf_update_values": [vp, vp, i64, vp],
         "hf_update_water": [vp, vp, i64, vp],
+        "hf_selftest_wait_timeout": [vp, i32, vp],
         "hf_set_camera": [vp, i32, P(hf_camera), vp, sz],
         "hf_discretize_cascades": [vp, i32, vp],
         "hf_build_maxmip": [vp, i32, vp],
@@ -192,6 +193,10 @@ def hf_update_values(ctx, values: np.ndarray, stream=None):
 def hf_update_water(ctx, depths: np.ndarray, stream=None):
     d = np.ascontiguousarray(depths, np.float32)
     _check(_lib.hf_update_water(ctx, d.ctypes.data_as(ct.c_void_p), ct.c_int64(d.size), _stream(stream)))
+
+
+def hf_selftest_wait_timeout(ctx, polls: int = 1000, stream=None):
+    _check(_lib.hf_selftest_wait_timeout(ctx, polls, _stream(stream)))
 
 
 def hf_set_camera(ctx, slot: int, cam: hf_camera, view_buf):

@@ -403,6 +403,8 @@ def run_ours(args, rank, world, local_rank):
                     "visits_per_ray": visits / (W * H * len(sched)),
                     "patch_tests_per_ray": ptests / (W * H * len(sched))},
     }
+    for v in kern.values():
+        v["frac"] = v["achieved"] / v["peak"]
     dom = max(("discretize", "maxmip", "raycast"), key=lambda k: kern[k]["ms"])
     d = kern[dom]
     kname = {"discretize": "k_discretize_f32", "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]

@@ -12,11 +12,22 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hf_internal.h"
 
 using namespace hfi;
 
 namespace {
+
+// An NVTX range around each entry point, so that profilers can attribute
+// kernels to API calls (header-only; costs nothing without a profiler).
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange&) = delete;
+    ApiRange& operator=(const ApiRange&) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -350,6 +361,7 @@ const char* hf_last_error(void) { return g_err.c_str(); }
 
 int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int64_t n_leaves,
                        const hf_rbf_params* rbf, hf_ctx** out) {
+    ApiRange range_("hf_create_quadtree");
     if (!desc || !rbf || !out) return fail(HF_ERR_ARG, "null argument");
     if (n_leaves < 1 || !leaves) return fail(HF_ERR_ARG, "no leaves");
     const hf_quadtree_desc& d = *desc;
@@ -524,6 +536,7 @@ int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
 }
 
 int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* stream) {
+    ApiRange range_("hf_bind_persistent");
     if (!ctx || !dev_persistent) return fail(HF_ERR_ARG, "null argument");
     if (reinterpret_cast<uintptr_t>(dev_persistent) & 255) return fail(HF_ERR_ARG, "buffer must be 256-byte aligned");
     if (bytes < ctx->lay.total)
@@ -566,6 +579,7 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
 }
 
 int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* stream) {
+    ApiRange range_("hf_update_values");
     if (!ctx || !values) return fail(HF_ERR_ARG, "null argument");
     if (n_values != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld values", (long long)ctx->n_leaves);
     if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
@@ -596,6 +610,7 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
 }
 
 int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* stream) {
+    ApiRange range_("hf_update_water");
     if (!ctx || !depths) return fail(HF_ERR_ARG, "null argument");
     if (!ctx->rbf.water) return fail(HF_ERR_STATE, "context was created without the water layer");
     if (n_depths != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld depths", (long long)ctx->n_leaves);
@@ -619,6 +634,7 @@ int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* st
 }
 
 int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes) {
+    ApiRange range_("hf_set_camera");
     if (!ctx || !cam || !dev_view) return fail(HF_ERR_ARG, "null argument");
     if (slot < 0 || slot >= HF_MAX_VIEWS) return fail(HF_ERR_ARG, "view slot %d out of range", slot);
     const hf_camera& c = *cam;
@@ -727,6 +743,7 @@ void fill_prep_cascade(const ViewSlot* v, int k, PrepCascade& q) {
 }  // namespace
 
 int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
+    ApiRange range_("hf_discretize_cascades");
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
     if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
@@ -753,6 +770,7 @@ int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
 }
 
 int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
+    ApiRange range_("hf_build_maxmip");
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
     const int C = v->cam.n_cascades, N = v->cam.cascade_size;
@@ -834,6 +852,7 @@ RayParams ray_params(const ViewSlot* v, bool water) {
 }  // namespace
 
 int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
+    ApiRange range_("hf_raycast");
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
     if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
@@ -846,6 +865,7 @@ int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* 
 }
 
 int hf_ray_stats(hf_ctx* ctx, int32_t slot, int64_t* visits, int64_t* patch_tests, void* stream) {
+    ApiRange range_("hf_ray_stats");
     ViewSlot* v = get_view(ctx, slot);
     if (!visits || !patch_tests) return fail(HF_ERR_ARG, "null argument");
     if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
@@ -864,6 +884,7 @@ int hf_ray_stats(hf_ctx* ctx, int32_t slot, int64_t* visits, int64_t* patch_test
 }
 
 int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream) {
+    ApiRange range_("hf_view_stats");
     ViewSlot* v = get_view(ctx, slot);
     if (!out) return fail(HF_ERR_ARG, "null argument");
     if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
@@ -932,6 +953,7 @@ int hf_batch_query_bytes(const hf_batch_item* items, int32_t n, int32_t flags, s
 }
 
 int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes) {
+    ApiRange range_("hf_batch_prepare");
     BatchPlan plan;
     int rc = plan_batch(items, n, &plan);
     if (rc) return rc;
@@ -1031,6 +1053,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
 }
 
 int hf_batch_launch(const void* host_buf, void* dev_buf, size_t dev_bytes, void* stream) {
+    ApiRange range_("hf_batch_launch");
     if (!host_buf || !dev_buf) return fail(HF_ERR_ARG, "null buffer");
     if (reinterpret_cast<uintptr_t>(dev_buf) & 255) return fail(HF_ERR_ARG, "device buffer must be 256-byte aligned");
     const BatchHeader& h = *static_cast<const BatchHeader*>(host_buf);
@@ -1049,6 +1072,7 @@ int hf_batch_launch(const void* host_buf, void* dev_buf, size_t dev_bytes, void*
 
 int hf_frame_batch(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes,
                    void* dev_buf, size_t dev_bytes, void* stream) {
+    ApiRange range_("hf_frame_batch");
     int rc = hf_batch_prepare(items, n, flags, host_buf, host_bytes);
     if (rc) return rc;
     return hf_batch_launch(host_buf, dev_buf, dev_bytes, stream);
@@ -1065,6 +1089,7 @@ int hf_get_cascade(const hf_ctx* ctx, int32_t slot, int32_t c, hf_cascade_info* 
 }
 
 int hf_sync(hf_ctx* ctx, void* stream) {
+    ApiRange range_("hf_sync");
     if (!ctx) return fail(HF_ERR_ARG, "null context");
     int e = cudaStreamSynchronize(cudaStream_t(stream));
     if (e) return cuda_fail(e, "stream synchronize");

@@ -13,6 +13,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <utility>
+
 #include "hf_internal.h"
 
 namespace hfi {
@@ -39,6 +41,28 @@ template <bool COH, class T>
 __device__ __forceinline__ T ldc(const T* p) {
     if (COH) return __ldcg(p);
     return __ldg(p);
+}
+
+// Programmatic dependent launch: the kernels of a frame are launched with
+// programmatic stream serialization, so a kernel is set up while its
+// predecessor drains; griddepcontrol.wait at its start then holds it until the
+// predecessor has completed and its writes are visible (a no-op for a kernel
+// launched without the attribute).
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... P, class... A>
+cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -315,6 +339,7 @@ __device__ __forceinline__ void prep_row(const PrepCascade& q, double dom_w, dou
 }
 
 __global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams p) {
+    wait_for_predecessor();
     const PrepCascade& q = p.cas[blockIdx.y];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < q.N) prep_row(q, p.dom_w, p.dom_h, p.eps_frac, t);
@@ -323,8 +348,7 @@ __global__ void __launch_bounds__(128) k_prep(const __grid_constant__ PrepParams
 int launch_prep(const PrepParams& p, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 127) / 128, p.C);
-    k_prep<<<grid, 128, 0, cudaStream_t(stream)>>>(p);
-    return cudaGetLastError();
+    return launch_dependent(k_prep, grid, dim3(128), cudaStream_t(stream), p);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +441,7 @@ template <bool WATER, int KERNEL>
 __global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
                                                         const __grid_constant__ LookupTables lt,
                                                         const ListsView lv, DevStatus* status) {
+    wait_for_predecessor();
     int di, dj;
     tile_texel(threadIdx.x, di, dj);
     discretize_texel<false, WATER, KERNEL>(p.cas[blockIdx.z], p.K, lt, lv, status, blockIdx.x * 32 + di,
@@ -539,6 +564,7 @@ template <class Ops>
 __global__ void __launch_bounds__(256) k_discretize_mixed(const __grid_constant__ DiscParams p,
                                                           const __grid_constant__ LookupTables lt,
                                                           const CompactView cv, DevStatus* status) {
+    wait_for_predecessor();
     int di, dj;
     tile_texel(threadIdx.x, di, dj);
     discretize_texel_mixed<Ops, false>(p.cas[blockIdx.z], p.K, lt, cv, status, blockIdx.x * 32 + di,
@@ -550,10 +576,8 @@ int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const C
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
     if (p.precision == HF_PREC_FP16)
-        k_discretize_mixed<F16Ops><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, cv, status);
-    else
-        k_discretize_mixed<BF16Ops><<<grid, 256, 0, cudaStream_t(stream)>>>(p, lt, cv, status);
-    return cudaGetLastError();
+        return launch_dependent(k_discretize_mixed<F16Ops>, grid, dim3(256), cudaStream_t(stream), p, lt, cv, status);
+    return launch_dependent(k_discretize_mixed<BF16Ops>, grid, dim3(256), cudaStream_t(stream), p, lt, cv, status);
 }
 
 int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
@@ -563,14 +587,12 @@ int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsVi
     cudaStream_t s = cudaStream_t(stream);
     const bool wend = p.kernel == HF_RBF_WENDLAND_C2;
     if (p.water && wend)
-        k_discretize_f32<true, HF_RBF_WENDLAND_C2><<<grid, 256, 0, s>>>(p, lt, lv, status);
-    else if (p.water)
-        k_discretize_f32<true, HF_RBF_GAUSSIAN><<<grid, 256, 0, s>>>(p, lt, lv, status);
-    else if (wend)
-        k_discretize_f32<false, HF_RBF_WENDLAND_C2><<<grid, 256, 0, s>>>(p, lt, lv, status);
-    else
-        k_discretize_f32<false, HF_RBF_GAUSSIAN><<<grid, 256, 0, s>>>(p, lt, lv, status);
-    return cudaGetLastError();
+        return launch_dependent(k_discretize_f32<true, HF_RBF_WENDLAND_C2>, grid, dim3(256), s, p, lt, lv, status);
+    if (p.water)
+        return launch_dependent(k_discretize_f32<true, HF_RBF_GAUSSIAN>, grid, dim3(256), s, p, lt, lv, status);
+    if (wend)
+        return launch_dependent(k_discretize_f32<false, HF_RBF_WENDLAND_C2>, grid, dim3(256), s, p, lt, lv, status);
+    return launch_dependent(k_discretize_f32<false, HF_RBF_GAUSSIAN>, grid, dim3(256), s, p, lt, lv, status);
 }
 
 // Measurement pass: the discretization's texel mapping and inner loop, but
@@ -777,6 +799,7 @@ __device__ __forceinline__ void mip_lo_block(const MipCascade& c, int bxi, int b
 
 template <bool TWO>
 __global__ void __launch_bounds__(256) k_mip_lo(const __grid_constant__ MipParams p) {
+    wait_for_predecessor();
     __shared__ float sm[16][17];
     mip_lo_block<false, TWO>(p.cas[blockIdx.z], blockIdx.x, blockIdx.y, sm);
 }
@@ -817,6 +840,7 @@ __device__ __forceinline__ void mip_hi_levels(const MipCascade& c, float* s0, fl
 }
 
 __global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipParams p) {
+    wait_for_predecessor();
     __shared__ float sm[2][4096];
     mip_hi_levels<false>(p.cas[blockIdx.x], sm[0], sm[1]);
 }
@@ -824,15 +848,11 @@ __global__ void __launch_bounds__(1024) k_mip_hi(const __grid_constant__ MipPara
 int launch_maxmip(const MipParams& p, void* stream) {
     if (p.C == 0) return cudaSuccess;
     dim3 grid((p.max_P + 63) / 64, (p.max_P + 63) / 64, p.C);
-    if (p.two)
-        k_mip_lo<true><<<grid, 256, 0, cudaStream_t(stream)>>>(p);
-    else
-        k_mip_lo<false><<<grid, 256, 0, cudaStream_t(stream)>>>(p);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = p.two ? launch_dependent(k_mip_lo<true>, grid, dim3(256), cudaStream_t(stream), p)
+                          : launch_dependent(k_mip_lo<false>, grid, dim3(256), cudaStream_t(stream), p);
     if (e != cudaSuccess) return e;
     if (p.max_K >= 7) {
-        k_mip_hi<<<p.C, 1024, 0, cudaStream_t(stream)>>>(p);
-        e = cudaGetLastError();
+        e = launch_dependent(k_mip_hi, dim3(p.C), dim3(1024), cudaStream_t(stream), p);
     }
     return e;
 }
@@ -1153,6 +1173,7 @@ __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_o
 // (8 and 64 registers for the walk over both surfaces).
 template <bool COUNT, bool WATER>
 __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
+    wait_for_predecessor();
     __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
     load_level_offsets<false>(p, s_off, threadIdx.y * 16 + threadIdx.x, 128);
     __syncthreads();
@@ -1173,10 +1194,8 @@ template <bool COUNT>
 int launch_raycast_t(const RayParams& p, DevStatus* status, void* stream) {
     dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
     if (p.water)
-        k_raycast<COUNT, true><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
-    else
-        k_raycast<COUNT, false><<<grid, dim3(16, 8), 0, cudaStream_t(stream)>>>(p, status);
-    return cudaGetLastError();
+        return launch_dependent(k_raycast<COUNT, true>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
+    return launch_dependent(k_raycast<COUNT, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
 }
 
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
@@ -1406,6 +1425,7 @@ __global__ void __launch_bounds__(256, RAYS_INSIDE ? 3 : 5) k_batch(const uint8_
 }
 
 __global__ void __launch_bounds__(256) k_batch_rays(const uint8_t* __restrict__ buf) {
+    wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
@@ -1429,6 +1449,7 @@ int batch_persistent_blocks(int* blocks_plain, int* blocks_rays) {
 // cascade by binary search over the phase's unit bases; kernel boundaries
 // order the phases, so the per-view code paths (and read-only loads) apply.
 __global__ void __launch_bounds__(128) k_bat_rows(const uint8_t* __restrict__ buf) {
+    wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
@@ -1439,6 +1460,7 @@ __global__ void __launch_bounds__(128) k_bat_rows(const uint8_t* __restrict__ bu
 }
 
 __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict__ buf) {
+    wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchItem* items = reinterpret_cast<const BatchItem*>(buf + h->items_off);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
@@ -1472,6 +1494,7 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
 }
 
 __global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ buf) {
+    wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
     __shared__ float sm[16][17];
@@ -1483,6 +1506,7 @@ __global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ b
 }
 
 __global__ void __launch_bounds__(1024) k_bat_miphi(const uint8_t* __restrict__ buf) {
+    wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
     __shared__ float sm[2][4096];
@@ -1509,26 +1533,14 @@ int launch_batch(const BatchHeader& h, void* dev_buf, void* stream) {
         const int nrow = h.phase_base[kPhaseTexels] - h.phase_base[kPhaseRows];
         const int ntex = h.phase_base[kPhaseMipLo] - h.phase_base[kPhaseTexels];
         const int nmip = h.phase_base[kPhaseMipHi] - h.phase_base[kPhaseMipLo];
-        if (nrow > 0) {
-            k_bat_rows<<<dim3(2 * h.max_rows_units, h.n_cascades), 128, 0, s>>>(buf);
-            if ((e = cudaGetLastError())) return e;
-        }
-        if (ntex > 0) {
-            k_bat_texels<<<ntex, 256, 0, s>>>(buf);
-            if ((e = cudaGetLastError())) return e;
-        }
-        if (nmip > 0) {
-            k_bat_miplo<<<nmip, 256, 0, s>>>(buf);
-            if ((e = cudaGetLastError())) return e;
-        }
-        k_bat_miphi<<<h.n_cascades, 1024, 0, s>>>(buf);
-        if ((e = cudaGetLastError())) return e;
+        if (nrow > 0 && (e = launch_dependent(k_bat_rows, dim3(2 * h.max_rows_units, h.n_cascades), dim3(128), s, buf)))
+            return e;
+        if (ntex > 0 && (e = launch_dependent(k_bat_texels, dim3(ntex), dim3(256), s, buf))) return e;
+        if (nmip > 0 && (e = launch_dependent(k_bat_miplo, dim3(nmip), dim3(256), s, buf))) return e;
+        if ((e = launch_dependent(k_bat_miphi, dim3(h.n_cascades), dim3(1024), s, buf))) return e;
     }
     const int rays = h.phase_base[kPhases] - h.phase_base[kPhaseRays];
-    if (!inside && rays > 0) {
-        k_batch_rays<<<rays, 256, 0, s>>>(buf);
-        return cudaGetLastError();
-    }
+    if (!inside && rays > 0) return launch_dependent(k_batch_rays, dim3(rays), dim3(256), s, buf);
     return cudaSuccess;
 }
 

@@ -286,3 +286,41 @@ def test_blend_is_continuous_across_overlap(orc, tiny):
     same = both & (Hh[1:] == Hh[:-1])
     assert change.sum() > 50
     assert np.percentile(rel[change], 99) < 4 * np.percentile(rel[same], 99)
+
+
+def test_blend_closed_form(orc, tiny):
+    """Two cascades over the same square holding flat planes at z1 > z2,
+    bands [1, 200] and [150, inf): a ray whose first hit (plane z1, cascade
+    0) projects to depth s in the overlap [150, 200] returns
+    (1 - a) t1 + a t2 with a = (s - 150) / 50 (reading R11), t1, t2 the
+    closed-form plane hits; before the overlap t1, cascade 0 reported."""
+    N = 33
+    z1, z2 = 12.5, 11.0
+    tex1, _ = _one_cascade_scene(N, 0, flat=z1)
+    tex2, _ = _one_cascade_scene(N, 0, flat=z2)
+    near0, far0, near1 = 1.0, 200.0, 150.0
+    c0 = _Cas(0.0, 0.0, 12.0, near0, far0, N)
+    c1 = _Cas(0.0, 0.0, 12.0, near1, 1e9, N)
+    cam = _scene_camera(tiny, (192.0, -60.0, 120.0), (0.0, 1.0, -0.55), w=64, h=48)
+    t, hit, _, _ = orc.raycast(cam, tiny.tree, [c0, c1], [tex1, tex2])
+    py, px = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    eye, d = _look_at_rays(cam, tiny.tree, px.ravel().astype(float), py.ravel().astype(float))
+    f = np.array(cam.forward, float)
+    dir2 = f[:2] / np.linalg.norm(f[:2])
+    ks = d[:, :2] @ dir2
+    t1 = (eye[2] - z1) / (-d[:, 2])
+    t2 = (eye[2] - z2) / (-d[:, 2])
+    P1 = eye + t1[:, None] * d
+    P2 = eye + t2[:, None] * d
+    ext = (N - 1) * 12.0
+    inside = lambda P: (P[:, 0] > 1e-6) & (P[:, 0] < ext - 1e-6) & (P[:, 1] > 1e-6) & (P[:, 1] < ext - 1e-6)
+    s1 = t1 * ks
+    a = np.clip((s1 - near1) / (far0 - near1), 0.0, 1.0)
+    band = (d[:, 2] < 0) & inside(P1) & inside(P2) & (s1 > near1 + 1e-6) & (s1 < far0 - 1e-6)
+    early = (d[:, 2] < 0) & inside(P1) & (s1 > near0 + 1e-6) & (s1 < near1 - 1e-6)
+    assert band.sum() > 100 and early.sum() > 100
+    assert np.all(hit[band] == 1) and np.all(hit[early] == 1)
+    expect = (1 - a) * t1 + a * t2
+    assert np.max(np.abs(t[band] - expect[band])) < 1e-9 * t2.max()
+    assert np.max(np.abs(t[early] - t1[early])) < 1e-9 * t1.max()
+    assert np.ptp(a[band]) > 0.5                  # the band is crossed, not touched

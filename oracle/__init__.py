@@ -43,7 +43,7 @@ class CameraC(ct.Structure):
                 ("vfov", ct.c_double), ("znear", ct.c_double), ("zfar", ct.c_double),
                 ("width", ct.c_int), ("height", ct.c_int), ("n_cascades", ct.c_int),
                 ("cascade_size", ct.c_int), ("split_lambda", ct.c_double),
-                ("overlap_frac", ct.c_double)]
+                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int)]
 
 
 class CascadeC(ct.Structure):
@@ -87,6 +87,9 @@ def lib():
         _lib.orc_ray_patch.argtypes = [d] * 11 + [P(d)]
         _lib.orc_fit.restype = i
         _lib.orc_fit.argtypes = [P(CameraC), P(Domain), P(ViewC)]
+        _lib.orc_ladder_fit.restype = None
+        _lib.orc_ladder_fit.argtypes = [d, d, d, d, d, i, i, P(ct.c_longlong), P(ct.c_longlong),
+                                        P(ct.c_longlong), P(d)]
         _lib.orc_frustum_box_vertices.restype = i
         _lib.orc_frustum_box_vertices.argtypes = [P(CameraC), P(Domain), P(d), i]
         _lib.orc_maxmip_size.restype = L
@@ -149,7 +152,7 @@ def camera_struct(cam, tree) -> CameraC:
     return CameraC((ct.c_double * 3)(*eye), (ct.c_double * 3)(*cam.forward),
                    (ct.c_double * 3)(*cam.up), cam.vfov, cam.znear, cam.zfar, cam.width,
                    cam.height, cam.n_cascades, cam.cascade_size, cam.split_lambda,
-                   cam.overlap_frac)
+                   cam.overlap_frac, int(getattr(cam, "texel_ladder", 0)))
 
 
 def fit(cam, tree, cells: Cells) -> ViewC:
@@ -159,6 +162,13 @@ def fit(cam, tree, cells: Cells) -> ViewC:
     if rc != 0:
         raise ValueError("orc_fit rejected the camera")
     return v
+
+
+def ladder_fit(x0: float, y0: float, x1: float, y1: float, c_min: float, N: int, n: int):
+    """Lattice fit of one box: (m, i0, j0, h) with h = c_min 2^(m/n)."""
+    m, i0, j0, h = ct.c_longlong(), ct.c_longlong(), ct.c_longlong(), ct.c_double()
+    lib().orc_ladder_fit(x0, y0, x1, y1, c_min, N, n, ct.byref(m), ct.byref(i0), ct.byref(j0), ct.byref(h))
+    return m.value, i0.value, j0.value, h.value
 
 
 def frustum_box_vertices(cam, tree, cells: Cells) -> np.ndarray:

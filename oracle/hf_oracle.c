@@ -6,6 +6,7 @@
  *   Wendland C2 weight (another interpolant) .. orc_rbf_weight (kernel 1)
  *   Eq. 2 (normalised weighted sum) ........... orc_rbf_points, orc_texel_heights
  *   Section 3 (cascade fitting) ............... orc_fit, orc_frustum_box_vertices
+ *   lattice fit for texel reuse (extension) ... orc_ladder_fit
  *   Section 3 (visible-texel mask) ............ orc_mask
  *   Section 5 (maximum mipmap, Tevs et al.) ... orc_maxmip
  *   Section 5 (ray casting, bilinear patches) . orc_ray_patch, orc_raycast
@@ -356,6 +357,57 @@ static int clip_band(const double hull[][2], int nh, const double* dir2, const d
  * the texel spacing h = E / (N - 1) puts the four box corners on texel
  * centres.  A relative slack of 1e-9 keeps values that land on a multiple
  * from flipping on rounding.                                              */
+/* Lattice fit (not in the paper; it makes texels of consecutive frames
+ * coincide so that they can be reused).  Texel spacings come from the ladder
+ * h_m = c_min 2^(m/n), m an integer >= -8n; the fit takes the smallest m
+ * with (N - 2) h_m >= the box's larger side, which depends on the box's size
+ * only, so moving the box never changes h.  The origin is the box's lower
+ * corner rounded down to the lattice of h_m: from there N - 1 spacings
+ * reach past the far side, because rounding down costs less than one
+ * spacing.  Texel (i, j) lies on lattice point (i0 + i, j0 + j).  The same
+ * 1e-9 relative slack as the stable fit keeps boundary cases from flipping. */
+static double ladder_spacing(double c_min, long long m, int n) {
+    return c_min * pow(2.0, (double)m / (double)n);
+}
+
+void orc_ladder_fit(double x0, double y0, double x1, double y1, double c_min, int N, int n,
+                    long long* m, long long* i0, long long* j0, double* h) {
+    double side = fmax(x1 - x0, y1 - y0);
+    long long lo = -8LL * n;
+    long long k = lo;
+    if (side > 0.0) {
+        double need = side * (1.0 - 1e-9) / (double)(N - 2);
+        double guess = floor((double)n * log2(need / c_min)) - 2.0;
+        if (guess > (double)lo) k = (long long)guess;
+        while (ladder_spacing(c_min, k, n) < need) k++;
+    }
+    *m = k;
+    *h = ladder_spacing(c_min, k, n);
+    *i0 = (long long)floor(x0 / *h + 1e-9);
+    *j0 = (long long)floor(y0 / *h + 1e-9);
+}
+
+static void lattice_fit(orc_cascade* c, double c_min, int N, int n) {
+    c->N = N;
+    if (c->n_poly < 3) {
+        c->n_poly = 0;
+        c->aabb[0] = c->aabb[1] = c->aabb[2] = c->aabb[3] = 0.0;
+        c->snap_x = c->snap_y = c->snap_k = 0;
+        c->h = c_min;
+    } else {
+        double x0 = c->poly[0][0], x1 = x0, y0 = c->poly[0][1], y1 = y0;
+        for (int i = 1; i < c->n_poly; ++i) {
+            x0 = fmin(x0, c->poly[i][0]); x1 = fmax(x1, c->poly[i][0]);
+            y0 = fmin(y0, c->poly[i][1]); y1 = fmax(y1, c->poly[i][1]);
+        }
+        c->aabb[0] = x0; c->aabb[1] = y0; c->aabb[2] = x1; c->aabb[3] = y1;
+        orc_ladder_fit(x0, y0, x1, y1, c_min, N, n, &c->snap_k, &c->snap_x, &c->snap_y, &c->h);
+    }
+    c->ox = (double)c->snap_x * c->h;
+    c->oy = (double)c->snap_y * c->h;
+    c->E = (double)(N - 1) * c->h;
+}
+
 static void stable_fit(orc_cascade* c, double c_min, int N) {
     c->N = N;
     if (c->n_poly < 3) {
@@ -402,6 +454,7 @@ int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out) {
     memset(out, 0, sizeof(*out));
     int C = cam->n_cascades;
     if (C < 1 || C > ORC_MAX_CASCADES || cam->cascade_size < 2) return -1;
+    if (cam->texel_ladder < 0 || (cam->texel_ladder > 0 && cam->cascade_size < 4)) return -1;
     out->n_cascades = C;
     double F[3], U[3], R[3];
     camera_basis(cam, F, U, R);
@@ -441,7 +494,10 @@ int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out) {
         c->n_poly = out->n_hull >= 3
                         ? clip_band(out->hull, out->n_hull, out->dir2, cam->eye, c->near_, c->far_ext, c->poly)
                         : 0;
-        stable_fit(c, dom->c_min, cam->cascade_size);
+        if (cam->texel_ladder > 0)
+            lattice_fit(c, dom->c_min, cam->cascade_size, cam->texel_ladder);
+        else
+            stable_fit(c, dom->c_min, cam->cascade_size);
     }
     return 0;
 }

@@ -41,6 +41,7 @@ typedef struct {
     int width, height;      /* image size */
     int n_cascades, cascade_size;
     double split_lambda, overlap_frac;
+    int texel_ladder;       /* 0: the paper's stable fit; n > 0: lattice fit (orc_ladder_fit) */
 } orc_camera;
 
 typedef struct {
@@ -48,7 +49,8 @@ typedef struct {
     int n_poly;                        /* 0 = empty cascade */
     double poly[ORC_MAX_POLY][2];      /* CCW cascade polygon */
     double aabb[4];                    /* x0, y0, x1, y1 */
-    long long snap_x, snap_y, snap_k;  /* ox = snap_x*c_min, oy = snap_y*c_min, E = 2*snap_k*c_min */
+    long long snap_x, snap_y, snap_k;  /* stable fit: ox = snap_x*c_min, oy = snap_y*c_min, E = 2*snap_k*c_min;
+                                          lattice fit: h = c_min 2^(snap_k/n), ox = snap_x*h, oy = snap_y*h */
     double ox, oy, E, h;
     int N;
 } orc_cascade;
@@ -84,6 +86,10 @@ void orc_rbf_points(const double* cx, const double* cy, const double* cs, const 
 
 /* ---- Section 3: cascade fitting ---- */
 int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out);
+/* lattice fit of a box [x0, x1] x [y0, y1] for n ladder steps per octave:
+ * returns the ladder index m, the lattice origin (i0, j0) and h */
+void orc_ladder_fit(double x0, double y0, double x1, double y1, double c_min, int N, int n,
+                    long long* m, long long* i0, long long* j0, double* h);
 int orc_frustum_box_vertices(const orc_camera* cam, const orc_domain* dom, double* xyz,
                              int cap);
 /* visibility of texels (i, j) of one cascade; margin = distance to the nearest decision

@@ -259,3 +259,85 @@ def test_mask_covers_polygon_with_valid_patches(orc, tiny):
             pj = np.clip(np.floor((pts[:, 1] - c.oy) / c.h).astype(int), 0, c.N - 2)
             ok = vis[pj, pi] & vis[pj, pi + 1] & vis[pj + 1, pi] & vis[pj + 1, pi + 1]
             assert np.all(ok)
+
+
+# ---- lattice fit (texel reuse across frames; not part of the paper) ----
+
+def test_ladder_fit_worked_examples(orc):
+    """Hand-derived cases.  Box 1000 x 500 m at (3.3, 7.9), N = 1026, c_min
+    = 10: a spacing must reach 1000 / 1024 = 0.9765625 m.  With 4 steps per
+    octave 10 * 2^(-13/4) = 1.05112 >= 0.97656 > 10 * 2^(-14/4) = 0.88388,
+    so m = -13, and the origin is (floor(3.3 / 1.05112), floor(7.9 /
+    1.05112)) = (3, 7).  With 1 step per octave 10 * 2^-3 = 1.25 >= 0.97656 >
+    0.625: m = -3, origin (floor(2.64), floor(6.32)) = (2, 6)."""
+    m, i0, j0, h = orc.ladder_fit(3.3, 7.9, 1003.3, 507.9, 10.0, 1026, 4)
+    assert (m, i0, j0) == (-13, 3, 7)
+    assert h == pytest.approx(10.0 * 2.0 ** -3.25, rel=1e-15)
+    assert orc.ladder_fit(3.3, 7.9, 1003.3, 507.9, 10.0, 1026, 1)[:3] == (-3, 2, 6)
+
+
+def test_ladder_fit_boundaries(orc):
+    """A side of exactly (N - 2) h_m keeps m (the 1e-9 slack), a side larger
+    by 1e-6 takes the next step; an origin exactly on a lattice point stays on
+    it; a tiny box takes the finest allowed spacing c_min 2^-8."""
+    cmin, N, n = 2.5, 130, 2
+    h3 = cmin * 2.0 ** 1.5
+    side = 128 * h3
+    assert orc.ladder_fit(0.0, 0.0, side, 1.0, cmin, N, n)[0] == 3
+    assert orc.ladder_fit(0.0, 0.0, side * (1 + 1e-6), 1.0, cmin, N, n)[0] == 4
+    m, i0, j0, h = orc.ladder_fit(5 * h3, 7 * h3, 5 * h3 + side, 7 * h3 + 1.0, cmin, N, n)
+    assert (m, i0, j0) == (3, 5, 7)
+    m, _, _, h = orc.ladder_fit(1.0, 1.0, 1.0 + 1e-6, 1.0, cmin, N, n)
+    assert m == -16 and h == pytest.approx(cmin / 256.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4])
+def test_ladder_fit_rules(orc, tiny, n):
+    """For every camera: h on the ladder, the smallest step whose N - 2
+    spacings reach the box's larger side, the origin on the lattice of h at
+    most one spacing below the box corner, and the N x N texels covering the
+    box."""
+    cells = orc.Cells(tiny.tree)
+    cmin = cells.domain.c_min
+    seen = 0
+    for cam in _cams(tiny):
+        v = orc.fit(cam.with_(texel_ladder=n), tiny.tree, cells)
+        for k in range(v.n_cascades):
+            c = v.cas[k]
+            if not c.n_poly:
+                continue
+            seen += 1
+            x0, y0, x1, y1 = c.aabb
+            side = max(x1 - x0, y1 - y0)
+            assert c.h == pytest.approx(cmin * 2.0 ** (c.snap_k / n), rel=1e-14)
+            assert (c.N - 2) * c.h >= side * (1 - 1e-9)
+            assert (c.N - 2) * cmin * 2.0 ** ((c.snap_k - 1) / n) < side * (1 - 1e-9)
+            assert c.ox == c.snap_x * c.h and c.oy == c.snap_y * c.h
+            assert c.E == (c.N - 1) * c.h
+            assert x0 - c.h < c.ox <= x0 + 1e-9 * c.h and y0 - c.h < c.oy <= y0 + 1e-9 * c.h
+            assert c.ox + c.E >= x1 - 1e-9 * side and c.oy + c.E >= y1 - 1e-9 * side
+    assert seen >= 10
+
+
+def test_ladder_fit_keeps_spacing_under_translation(orc):
+    """Moving the camera by any distance (far from the domain's edges) keeps
+    the box size, hence the ladder step, and moves the origin along the
+    lattice: texels of the two frames coincide wherever they overlap."""
+    lib = orc.lib()
+    dom = orc.Domain(1.0e5, 1.0e5, 0.0, 80.0, 2.5, 40.0)
+    for yaw in [0.3, 1.2, 2.9]:
+        for shift in [(7.3, 0.0), (0.0, -3.9), (11.1, 5.7), (123.45, -67.8)]:
+            def cam_at(dx, dy):
+                fwd = (math.cos(yaw) * 0.8, math.sin(yaw) * 0.8, -0.6)
+                return orc.CameraC((ct.c_double * 3)(50000.0 + dx, 50000.0 + dy, 600.0),
+                                   (ct.c_double * 3)(*fwd), (ct.c_double * 3)(0, 0, 1),
+                                   math.radians(60), 1.0, 4000.0, 640, 480, 3, 512, 0.5, 0.05, 4)
+            va, vb = orc.ViewC(), orc.ViewC()
+            assert lib.orc_fit(ct.byref(cam_at(0, 0)), ct.byref(dom), ct.byref(va)) == 0
+            assert lib.orc_fit(ct.byref(cam_at(*shift)), ct.byref(dom), ct.byref(vb)) == 0
+            for k in range(3):
+                a, b = va.cas[k], vb.cas[k]
+                assert b.snap_k == a.snap_k and b.h == a.h
+                for ax, d in ((0, shift[0]), (1, shift[1])):
+                    da = (b.snap_x - a.snap_x) if ax == 0 else (b.snap_y - a.snap_y)
+                    assert abs(da * a.h - d) <= a.h * (1 + 1e-9)

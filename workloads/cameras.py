@@ -29,6 +29,7 @@ class Camera:
     cascade_size: int
     split_lambda: float = 1.0
     overlap_frac: float = 0.05
+    texel_ladder: int = 0         # 0: stable fit; n > 0: lattice fit, n texel sizes per octave
 
     def with_(self, **kw) -> "Camera":
         return replace(self, **kw)

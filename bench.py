@@ -443,6 +443,7 @@ def run_ours(args, rank, world, local_rank):
         line["interpolant_variants"] = time_precision_variants(
             scene, cams, sched[:min(len(sched), 240)], args.warmup, dev, flush, stream,
             variants=(("wendland_c2", {"kernel": 1}),))
+        line["temporal_reuse"] = time_temporal_reuse(scene, args.warmup, dev, flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
@@ -488,6 +489,72 @@ def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream,
         r.close()
         del r
         torch.cuda.empty_cache()
+    return out
+
+
+def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed=2):
+    """Frame time on the same flight path flown slower (1 200 and 12 000
+    frames instead of 120: ~100 m and ~10 m per frame), n consecutive frames
+    from its middle, three ways: the stable fit computing every texel, the
+    lattice fit (`ladder` texel sizes per octave) computing every texel, and
+    the lattice fit carrying texels over from the previous frame
+    (hf_discretize_reuse; view slots 0 and 1 alternate).  L2 flushed between
+    frames as in the main line; the carried-over share of the visible texels
+    comes from an untimed counting pass over the same frames."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2201_10887_gb300 import Renderer
+    c0 = scene.cameras[0]
+    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
+    out = {"texel_ladder": ladder, "frames": n}
+    for n_frames in (1200, 12000):
+        path = workloads.flight_path(scene.tree, scene.fbm, seed, n_frames, c0.width, c0.height,
+                                     n_cascades=c0.n_cascades, cascade_size=c0.cascade_size,
+                                     split_lambda=c0.split_lambda)
+        first = n_frames // 2 - (n + warmup) // 2
+        seq = path[first:first + warmup + n]
+        step_m = float(np.mean([np.linalg.norm(np.subtract(a.eye, b.eye)) for a, b in zip(seq, seq[1:])]))
+        res = {"metres_per_frame": step_m}
+        for mode in ("stable", "lattice", "lattice_reuse"):
+            cams_m = [c.with_(texel_ladder=0 if mode == "stable" else ladder) for c in seq]
+            reuse = mode == "lattice_reuse"
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+            for k, cam in enumerate(cams_m):
+                slot = k % 2
+                prev = 1 - slot if reuse and k > 0 else None
+                e = ev[k - warmup] if k >= warmup else None
+                flush.fill_(float(k))
+                if e:
+                    e[0].record(stream)
+                r.set_camera(cam, slot)
+                r.discretize(slot, reuse_from=prev)
+                if e:
+                    e[1].record(stream)
+                r.build_maxmip(slot)
+                r.raycast(slot)
+                if e:
+                    e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            r.sync()
+            res[mode] = {"frame_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in ev),
+                         "discretize_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev)}
+            if reuse:
+                reused = vis = 0
+                for k, cam in enumerate(cams_m[warmup - 1:]):
+                    slot = k % 2
+                    r.set_camera(cam, slot)
+                    r.discretize(slot, reuse_from=1 - slot if k > 0 else None)
+                    if k > 0:
+                        st = r.stats(slot)
+                        reused += sum(st["reused_texels"])
+                        vis += sum(st["visible_texels"])
+                r.sync()
+                res[mode]["reused_fraction"] = reused / max(vis, 1)
+        out[f"flight_{n_frames}_frames"] = res
+    r.close()
+    del r
+    torch.cuda.empty_cache()
     return out
 
 

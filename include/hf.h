@@ -119,7 +119,18 @@ typedef struct {
  * vfov in radians; znear/zfar are clip distances along forward.
  * n_cascades textures of cascade_size^2 texels are fitted; split_lambda
  * blends logarithmic (1) and uniform (0) splits; the far plane of every
- * cascade but the last is pushed out by overlap_frac of its depth span. */
+ * cascade but the last is pushed out by overlap_frac of its depth span.
+ * texel_ladder selects the fit of each cascade's band polygon: 0 is the
+ * paper's stable fit (extent an even multiple of the smallest cell c_min,
+ * origin on a multiple of c_min, texel = extent / (N - 1)); n in 1..64 is
+ * the lattice fit, which lets hf_discretize_reuse carry texels over from
+ * one frame to the next: the texel spacing is restricted to the ladder
+ * h_m = c_min 2^(m/n) (m >= -8n), taking the smallest m with (N - 2) h_m >=
+ * the box's larger side, and the origin is the box corner rounded down to a
+ * multiple of h_m, so texel (i, j) sits on the lattice point (snap_x + i,
+ * snap_y + j) of spacing h_m whatever the camera's position.  The lattice
+ * fit needs cascade_size >= 4; its texels are up to 2^(1/n) coarser than
+ * the stable fit's.  reserved must be 0. */
 typedef struct {
     double eye[3];
     double forward[3];
@@ -128,6 +139,8 @@ typedef struct {
     int32_t width, height;
     int32_t n_cascades, cascade_size;
     double split_lambda, overlap_frac;
+    int32_t texel_ladder;
+    int32_t reserved;
 } hf_camera;
 
 /* Fitted cascade (Section 3) plus the device buffers bound to it. */
@@ -137,13 +150,17 @@ typedef struct {
     int32_t N;                                   /* texture side */
     double poly[HF_MAX_POLY][2];                 /* CCW, domain-local */
     double aabb[4];                              /* x0, y0, x1, y1 of the polygon */
-    int64_t snap_x, snap_y, snap_k;              /* ox = snap_x c_min, oy = snap_y c_min, extent = 2 snap_k c_min */
+    int64_t snap_x, snap_y, snap_k;              /* stable fit: ox = snap_x c_min, oy = snap_y c_min, extent = 2 snap_k c_min;
+                                                    lattice fit: texel = c_min 2^(snap_k / texel_ladder), ox = snap_x texel,
+                                                    oy = snap_y texel */
     double ox, oy, extent, texel;                /* texel = extent / (N - 1) */
     float* tex;                                  /* device, N*N FP32 heights, -inf where invisible */
     float* mip;                                  /* device, max mipmap (see hf_build_maxmip) */
     int32_t* spans;                              /* device, N rows x {first, last} visible column; last < first = none */
     int64_t mip_floats;                          /* number of floats in mip */
     float* water_tex;                            /* device, N*N FP32 water surface, -inf where dry or invisible; NULL without the water layer */
+    int32_t texel_ladder;                        /* the camera's texel_ladder (0 = stable fit) */
+    int32_t reuse_source;                        /* cascade of the earlier frame the last hf_discretize_reuse copied from, -1 = none */
 } hf_cascade_info;
 
 typedef struct hf_ctx hf_ctx;
@@ -198,6 +215,27 @@ int hf_set_camera(hf_ctx* ctx, int32_t view_slot, const hf_camera* cam, void* de
  * same pass also writes the water surface textures (hf_update_water). */
 int hf_discretize_cascades(hf_ctx* ctx, int32_t view_slot, void* stream);
 
+/* Step 1 with texels carried over from an earlier frame (temporal reuse; the
+ * paper recomputes every frame).  view_slot's camera is set; prev_slot (a
+ * different slot of the same context, with its own buffers) holds an earlier
+ * frame discretized since its camera was last set.  Each of view_slot's
+ * cascades takes as its source the earlier frame's cascade with the same
+ * texel lattice that overlaps it most: with the lattice fit, the same
+ * spacing (snap_k, texel_ladder); with the stable fit, an identical fit
+ * (snaps and size).  Every visible texel whose lattice point the source
+ * computed (visible there) is copied from it -- heights depend only on the
+ * texel's position and the leaf data, so the copy equals a recomputation bit
+ * for bit -- and every other visible texel is computed as in
+ * hf_discretize_cascades.  Nothing is carried over when the leaf values or
+ * depths changed since prev_slot was discretized (hf_update_values,
+ * hf_update_water).  prev_slot's textures are read on `stream`: the caller
+ * keeps prev_slot untouched, and its earlier work ordered before this call
+ * (same stream, or an event), until this work is done.  HF_ERR_ARG for
+ * prev_slot == view_slot or overlapping view buffers, HF_ERR_STATE if either
+ * slot is not ready.  hf_get_cascade reports the source (reuse_source),
+ * hf_view_stats the texels carried over. */
+int hf_discretize_reuse(hf_ctx* ctx, int32_t view_slot, int32_t prev_slot, void* stream);
+
 /* Step 2a (Section 5, maximum mipmap of Tevs et al.): level 0 holds, per
  * bilinear patch (texels i..i+1, j..j+1), the maximum of its four corners,
  * or -inf if a corner is invisible; patches are padded with -inf to P x P,
@@ -225,13 +263,18 @@ int hf_get_cascade(const hf_ctx* ctx, int32_t view_slot, int32_t c, hf_cascade_i
 
 /* Work counts of the last discretization of a view slot, per cascade:
  * visible texels, list entries walked (the candidates of Section 4), and
- * weighted-sum terms with w > 0 (the influencing set I of Eq. 2).  Runs a
- * counting pass of the discretization on `stream` and waits for it; meant
- * for measurement, not for the frame loop. */
+ * weighted-sum terms with w > 0 (the influencing set I of Eq. 2), all as if
+ * every visible texel were computed, and the visible texels that
+ * hf_discretize_reuse copied from the earlier frame instead (0 after
+ * hf_discretize_cascades; counted by reading that frame's textures again, so
+ * valid while they are unchanged).  Runs a counting pass of the
+ * discretization on `stream` and waits for it; meant for measurement, not
+ * for the frame loop. */
 typedef struct {
     int64_t visible_texels[HF_MAX_CASCADES];
     int64_t candidates[HF_MAX_CASCADES];
     int64_t influencers[HF_MAX_CASCADES];
+    int64_t reused_texels[HF_MAX_CASCADES];
 } hf_view_stats_t;
 int hf_view_stats(hf_ctx* ctx, int32_t view_slot, hf_view_stats_t* out, void* stream);
 

@@ -7,7 +7,9 @@
 //   4. split distances (logarithmic, or blended with uniform by lambda),
 //   5. per cascade, the hull clipped to its depth band; all far planes but
 //      the last are pushed out so adjacent cascades overlap,
-//   6. stable texel-aligned fit of the band polygon's bounding box.
+//   6. stable texel-aligned fit of the band polygon's bounding box (or, with
+//      hf_camera.texel_ladder > 0, the lattice fit that hf_discretize_reuse
+//      relies on: spacing from a fixed ladder, origin on the texel lattice).
 //
 // The frustum/box intersection is built by clipping the faces of each solid
 // against the other's half-spaces (Sutherland-Hodgman); the hull is Andrew's
@@ -132,6 +134,9 @@ std::vector<P2> clip_depth(const std::vector<P2>& in, const double* dir, const d
     return out;
 }
 
+// Ladder of lattice-fit texel spacings: c_min 2^(m/n).
+double ladder_texel(double c_min, int64_t m, int n) { return c_min * std::exp2(double(m) / double(n)); }
+
 }  // namespace
 
 int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomain& dom,
@@ -248,13 +253,48 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
         c.n_poly = int(poly.size());
         for (size_t i = 0; i < poly.size(); ++i) { c.poly[i][0] = poly[i].x; c.poly[i][1] = poly[i].y; }
         const double cm = dom.c_min;
+        c.texel_ladder = cam.texel_ladder;
+        c.reuse_source = -1;
+        double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
         if (c.n_poly >= 3) {
-            double x0 = poly[0].x, x1 = x0, y0 = poly[0].y, y1 = y0;
+            x0 = x1 = poly[0].x;
+            y0 = y1 = poly[0].y;
             for (const P2& p : poly) {
                 x0 = std::min(x0, p.x); x1 = std::max(x1, p.x);
                 y0 = std::min(y0, p.y); y1 = std::max(y1, p.y);
             }
             c.aabb[0] = x0; c.aabb[1] = y0; c.aabb[2] = x1; c.aabb[3] = y1;
+        } else {
+            c.n_poly = 0;
+        }
+        if (cam.texel_ladder > 0) {
+            // lattice fit: the spacing is the smallest ladder value
+            // c_min 2^(m/n), m >= -8n, whose N - 2 spacings span the box's
+            // larger side (so it depends on the box's size, not its place);
+            // the origin is the box corner rounded down onto that lattice,
+            // which leaves N - 1 spacings enough to reach the far side
+            const int n = cam.texel_ladder;
+            const int64_t m_lo = -8 * int64_t(n);
+            int64_t m = c.n_poly ? m_lo : 0;
+            if (c.n_poly) {
+                const double need = std::max(x1 - x0, y1 - y0) * (1.0 - 1e-9) / double(N - 2);
+                if (ladder_texel(cm, m_lo, n) < need) {
+                    m = std::max(m_lo, int64_t(std::ceil(double(n) * std::log2(need / cm))));
+                    while (m > m_lo && ladder_texel(cm, m - 1, n) >= need) --m;
+                    while (ladder_texel(cm, m, n) < need) ++m;
+                }
+            }
+            const double h = ladder_texel(cm, m, n);
+            c.snap_k = m;
+            c.snap_x = c.n_poly ? int64_t(std::floor(x0 / h + 1e-9)) : 0;
+            c.snap_y = c.n_poly ? int64_t(std::floor(y0 / h + 1e-9)) : 0;
+            c.texel = h;
+            c.ox = double(c.snap_x) * h;
+            c.oy = double(c.snap_y) * h;
+            c.extent = double(N - 1) * h;
+            continue;
+        }
+        if (c.n_poly) {
             // even multiple of c_min covering the larger side; origin on a
             // multiple of c_min; widen until the box is covered (1e-9 slack
             // so values landing on a multiple do not flip on rounding)
@@ -266,7 +306,6 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
                 kk++;
             c.snap_x = sxn; c.snap_y = syn; c.snap_k = kk;
         } else {
-            c.n_poly = 0;
             c.snap_x = c.snap_y = 0;
             c.snap_k = 1;
         }

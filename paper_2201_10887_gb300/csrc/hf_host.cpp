@@ -148,6 +148,13 @@ struct ViewSlot {
     int2* spans[HF_MAX_CASCADES] = {};
     float* xs[HF_MAX_CASCADES] = {};
     float* ys[HF_MAX_CASCADES] = {};
+    uint64_t data_version = 0;  // the context's leaf data this slot was discretized from
+    // source of the texels the last hf_discretize_reuse carried over, per cascade
+    struct Reuse {
+        const float* tex = nullptr;
+        const float* wtex = nullptr;
+        int32_t N = 0, di = 0, dj = 0;
+    } reuse[HF_MAX_CASCADES];
 };
 
 // Device layout of the persistent buffer.
@@ -180,6 +187,7 @@ struct hf_ctx {
     size_t dev_bytes = 0;
     PersistentLayout lay{};
     std::unique_ptr<ViewSlot> views[HF_MAX_VIEWS];
+    uint64_t data_version = 0;  // bumped by hf_update_values / hf_update_water
 
     PersistentLayout layout() const {
         PersistentLayout l{};
@@ -262,15 +270,32 @@ ViewSlot* get_view(hf_ctx* ctx, int32_t slot) {
     return ctx->views[slot].get();
 }
 
-}  // namespace
+// Texel grid and grown-polygon edge constraints of a fitted cascade for the
+// row kernel (the buffers are set by the caller).
+void fill_prep_geometry(const hf_cascade_info& ci, int N, PrepCascade& q) {
+    q.ox = ci.ox;
+    q.oy = ci.oy;
+    q.h = ci.texel;
+    q.inv_h = 1.0 / ci.texel;
+    q.lattice = ci.texel_ladder > 0 ? 1 : 0;
+    q.lat_x = ci.snap_x;
+    q.lat_y = ci.snap_y;
+    q.N = N;
+    q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
+    const double delta = std::sqrt(2.0) * ci.texel;  // one texel diagonal
+    for (int e = 0; e < q.n_edges; ++e) {
+        const double ax = ci.poly[e][0], ay = ci.poly[e][1];
+        const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
+        const double len = std::hypot(bx - ax, by - ay);
+        const double nx = (by - ay) / len, ny = -(bx - ax) / len;
+        q.ny[e] = ny;
+        q.c[e] = nx * ax + ny * ay + delta;
+        q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
+        q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
+    }
+}
 
-int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
-                                   char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
-                                   PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
-                                   DevStatus** status) {
-    if (!ctx || !cam || !tex) return fail(HF_ERR_ARG, "null argument");
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    const hf_camera& c = *cam;
+int check_camera(const hf_camera& c) {
     if (!finite3(c.eye) || !finite3(c.forward) || !finite3(c.up))
         return fail(HF_ERR_ARG, "camera vectors must be finite");
     if (c.forward[0] == 0.0 && c.forward[1] == 0.0 && c.forward[2] == 0.0) return fail(HF_ERR_ARG, "zero forward vector");
@@ -281,6 +306,22 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
     if (c.cascade_size < 2 || c.cascade_size > kMaxCascadeSize) return fail(HF_ERR_ARG, "cascade_size must be 2..%d", kMaxCascadeSize);
     if (!(c.split_lambda >= 0.0 && c.split_lambda <= 1.0)) return fail(HF_ERR_ARG, "split_lambda must be in [0, 1]");
     if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
+    if (c.texel_ladder < 0 || c.texel_ladder > 64) return fail(HF_ERR_ARG, "texel_ladder must be 0..64");
+    if (c.texel_ladder > 0 && c.cascade_size < 4) return fail(HF_ERR_ARG, "the lattice fit needs cascade_size >= 4");
+    if (c.reserved != 0) return fail(HF_ERR_ARG, "hf_camera.reserved must be 0");
+    return HF_OK;
+}
+
+}  // namespace
+
+int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
+                                   char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
+                                   PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
+                                   DevStatus** status) {
+    if (!ctx || !cam || !tex) return fail(HF_ERR_ARG, "null argument");
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    const hf_camera& c = *cam;
+    if (int rc = check_camera(c)) return rc;
     const int C = c.n_cascades, N = c.cascade_size;
     const size_t need = size_t(C) * size_t(N) * 16;
     if (need > scratch_bytes)
@@ -312,23 +353,7 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
     for (int k = 0; k < C; ++k) {
         const hf_cascade_info& ci = fit->cas[k];
         PrepCascade& q = pp->cas[k];
-        q.ox = ci.ox;
-        q.oy = ci.oy;
-        q.h = ci.texel;
-        q.inv_h = 1.0 / ci.texel;
-        q.N = N;
-        q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
-        const double delta = std::sqrt(2.0) * ci.texel;
-        for (int e = 0; e < q.n_edges; ++e) {
-            const double ax = ci.poly[e][0], ay = ci.poly[e][1];
-            const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
-            const double len = std::hypot(bx - ax, by - ay);
-            const double nx = (by - ay) / len, ny = -(bx - ax) / len;
-            q.ny[e] = ny;
-            q.c[e] = nx * ax + ny * ay + delta;
-            q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
-            q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
-        }
+        fill_prep_geometry(ci, N, q);
         q.spans = spans + size_t(k) * N;
         q.xs = xs + size_t(k) * N;
         q.ys = ys + size_t(k) * N;
@@ -431,6 +456,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     ctx->c_max = d.root_cell / double(int64_t(1) << lmin);
     ctx->zmin = vmin;
     ctx->zmax = vmax;
+    ++ctx->data_version;
     if (rbf->water) ctx->depth.assign(size_t(n_leaves), 0.f);
 
     // records in (level, iy, ix) order: centre, weight scale, value
@@ -596,6 +622,7 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
     }
     ctx->zmin = vmin;
     ctx->zmax = vmax;
+    ++ctx->data_version;
     for (size_t k = 0; k < ctx->depth.size(); ++k)
         if (ctx->depth[k] > 0.f) ctx->zmax = std::max(double(ctx->zmax), double(ctx->recs[k].w) + ctx->depth[k]);
     cudaStream_t s = cudaStream_t(stream);
@@ -626,6 +653,7 @@ int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* st
     for (int64_t s = 0; s < n_depths; ++s)
         zmax = std::max(zmax, double(ctx->recs[size_t(s)].w) + (ctx->depth[size_t(s)] > 0.f ? ctx->depth[size_t(s)] : 0.0));
     ctx->zmax = zmax;
+    ++ctx->data_version;
     cudaStream_t s = cudaStream_t(stream);
     int e = cudaMemcpyAsync(ctx->dev + ctx->lay.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
     if (!e) e = cudaStreamSynchronize(s);
@@ -638,16 +666,7 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
     if (!ctx || !cam || !dev_view) return fail(HF_ERR_ARG, "null argument");
     if (slot < 0 || slot >= HF_MAX_VIEWS) return fail(HF_ERR_ARG, "view slot %d out of range", slot);
     const hf_camera& c = *cam;
-    if (!finite3(c.eye) || !finite3(c.forward) || !finite3(c.up))
-        return fail(HF_ERR_ARG, "camera vectors must be finite");
-    if (c.forward[0] == 0.0 && c.forward[1] == 0.0 && c.forward[2] == 0.0) return fail(HF_ERR_ARG, "zero forward vector");
-    if (!(c.vfov > 0.0 && c.vfov < 3.1)) return fail(HF_ERR_ARG, "vfov must be in (0, 3.1) radians");
-    if (!(c.znear > 0.0 && c.zfar > c.znear && std::isfinite(c.zfar))) return fail(HF_ERR_ARG, "need 0 < znear < zfar");
-    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return fail(HF_ERR_ARG, "image size out of range");
-    if (c.n_cascades < 1 || c.n_cascades > HF_MAX_CASCADES) return fail(HF_ERR_ARG, "n_cascades must be 1..%d", HF_MAX_CASCADES);
-    if (c.cascade_size < 2 || c.cascade_size > kMaxCascadeSize) return fail(HF_ERR_ARG, "cascade_size must be 2..%d", kMaxCascadeSize);
-    if (!(c.split_lambda >= 0.0 && c.split_lambda <= 1.0)) return fail(HF_ERR_ARG, "split_lambda must be in [0, 1]");
-    if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
+    if (int rc = check_camera(c)) return rc;
     if (reinterpret_cast<uintptr_t>(dev_view) & 255) return fail(HF_ERR_ARG, "view buffer must be 256-byte aligned");
     const size_t need = per_view_bytes(c.n_cascades, c.cascade_size, ctx->rbf.water != 0);
     if (bytes < need) return fail(HF_ERR_NOMEM, "view buffer has %zu bytes, %zu needed", bytes, need);
@@ -707,6 +726,11 @@ DiscParams disc_params(const hf_ctx* ctx, const ViewSlot* v) {
         dc.ys = v->ys[k];
         dc.tex = v->tex[k];
         dc.wtex = v->wtex[k];
+        dc.prev = v->reuse[k].tex;
+        dc.prev_w = v->reuse[k].wtex;
+        dc.prev_N = v->reuse[k].N;
+        dc.prev_di = v->reuse[k].di;
+        dc.prev_dj = v->reuse[k].dj;
     }
     return dp;
 }
@@ -717,24 +741,7 @@ namespace {
 
 // Grown-polygon edge constraints and buffers of cascade k for the row kernel.
 void fill_prep_cascade(const ViewSlot* v, int k, PrepCascade& q) {
-    const hf_cascade_info& ci = v->fit.cas[k];
-    q.ox = ci.ox;
-    q.oy = ci.oy;
-    q.h = ci.texel;
-    q.inv_h = 1.0 / ci.texel;
-    q.N = v->cam.cascade_size;
-    q.n_edges = ci.n_poly >= 3 ? ci.n_poly : 0;
-    const double delta = std::sqrt(2.0) * ci.texel;  // one texel diagonal
-    for (int e = 0; e < q.n_edges; ++e) {
-        const double ax = ci.poly[e][0], ay = ci.poly[e][1];
-        const double bx = ci.poly[(e + 1) % ci.n_poly][0], by = ci.poly[(e + 1) % ci.n_poly][1];
-        const double len = std::hypot(bx - ax, by - ay);
-        const double nx = (by - ay) / len, ny = -(bx - ax) / len;
-        q.ny[e] = ny;
-        q.c[e] = nx * ax + ny * ay + delta;
-        q.sgn[e] = nx > 0.0 ? 1 : (nx < 0.0 ? -1 : 0);
-        q.inv_nx[e] = nx != 0.0 ? 1.0 / nx : 0.0;
-    }
+    fill_prep_geometry(v->fit.cas[k], v->cam.cascade_size, q);
     q.spans = v->spans[k];
     q.xs = v->xs[k];
     q.ys = v->ys[k];
@@ -742,11 +749,9 @@ void fill_prep_cascade(const ViewSlot* v, int k, PrepCascade& q) {
 
 }  // namespace
 
-int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
-    ApiRange range_("hf_discretize_cascades");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+namespace {
+
+int discretize_view(hf_ctx* ctx, ViewSlot* v, void* stream) {
     const int C = v->cam.n_cascades, N = v->cam.cascade_size;
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
@@ -766,7 +771,82 @@ int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
                                     stream);
     if (e) return cuda_fail(e, "discretization kernel launch");
     v->stage = 2;
+    v->data_version = ctx->data_version;
     return HF_OK;
+}
+
+// The earlier frame's cascade whose texel lattice matches cascade k of v and
+// overlaps it most: lattice fit, the same spacing; stable fit, the same fit.
+int reuse_source(const ViewSlot* v, int k, const ViewSlot* p, ViewSlot::Reuse* r) {
+    const hf_cascade_info& a = v->fit.cas[k];
+    const int N = v->cam.cascade_size;
+    int best = -1;
+    int64_t best_area = 0;
+    if (a.n_poly < 3) return -1;
+    for (int q = 0; q < p->cam.n_cascades; ++q) {
+        const hf_cascade_info& b = p->fit.cas[q];
+        const int M = p->cam.cascade_size;
+        if (b.n_poly < 3 || a.texel_ladder != b.texel_ladder) continue;
+        int64_t di = 0, dj = 0;
+        if (a.texel_ladder > 0) {
+            if (a.snap_k != b.snap_k || a.texel != b.texel) continue;
+            di = a.snap_x - b.snap_x;
+            dj = a.snap_y - b.snap_y;
+        } else if (a.snap_x != b.snap_x || a.snap_y != b.snap_y || a.snap_k != b.snap_k || N != M) {
+            continue;
+        }
+        // texel i of v is texel i + di of p: the overlap of [di, di + N) and [0, M)
+        const int64_t wx = std::min<int64_t>(di + N, M) - std::max<int64_t>(di, 0);
+        const int64_t wy = std::min<int64_t>(dj + N, M) - std::max<int64_t>(dj, 0);
+        if (wx <= 0 || wy <= 0 || wx * wy <= best_area) continue;
+        best = q;
+        best_area = wx * wy;
+        r->tex = p->tex[q];
+        r->wtex = p->wtex[q];
+        r->N = M;
+        r->di = int32_t(di);
+        r->dj = int32_t(dj);
+    }
+    return best;
+}
+
+}  // namespace
+
+int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
+    ApiRange range_("hf_discretize_cascades");
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    for (int k = 0; k < HF_MAX_CASCADES; ++k) {
+        v->reuse[k] = ViewSlot::Reuse();
+        v->fit.cas[k].reuse_source = -1;
+    }
+    return discretize_view(ctx, v, stream);
+}
+
+int hf_discretize_reuse(hf_ctx* ctx, int32_t slot, int32_t prev_slot, void* stream) {
+    ApiRange range_("hf_discretize_reuse");
+    ViewSlot* v = get_view(ctx, slot);
+    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+    if (prev_slot == slot) return fail(HF_ERR_ARG, "a slot cannot reuse its own texels");
+    const ViewSlot* p = get_view(ctx, prev_slot);
+    if (!p || p->stage < 2) return fail(HF_ERR_STATE, "view slot %d holds no discretized frame", prev_slot);
+    if (v->dev < p->dev + p->bytes && p->dev < v->dev + v->bytes)
+        return fail(HF_ERR_ARG, "view slots %d and %d share buffer memory", slot, prev_slot);
+    const bool same_data = p->data_version == ctx->data_version;
+    for (int k = 0; k < HF_MAX_CASCADES; ++k) {
+        v->reuse[k] = ViewSlot::Reuse();
+        v->fit.cas[k].reuse_source = -1;
+    }
+    for (int k = 0; k < v->cam.n_cascades && same_data; ++k) {
+        ViewSlot::Reuse r;
+        const int q = reuse_source(v, k, p, &r);
+        if (q < 0) continue;
+        v->reuse[k] = r;
+        v->fit.cas[k].reuse_source = q;
+    }
+    return discretize_view(ctx, v, stream);
 }
 
 int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
@@ -893,7 +973,7 @@ int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream)
     int e = cudaMemsetAsync(st->counters, 0, sizeof(st->counters), s);
     if (!e) e = launch_stats(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), st, stream);
     if (e) return cuda_fail(e, "counting pass launch");
-    unsigned long long c[3 * HF_MAX_CASCADES];
+    unsigned long long c[4 * HF_MAX_CASCADES];
     e = cudaMemcpyAsync(c, st->counters, sizeof(c), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "counting pass");
@@ -902,6 +982,7 @@ int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream)
         out->visible_texels[k] = int64_t(c[k]);
         out->candidates[k] = int64_t(c[HF_MAX_CASCADES + k]);
         out->influencers[k] = int64_t(c[2 * HF_MAX_CASCADES + k]);
+        out->reused_texels[k] = int64_t(c[3 * HF_MAX_CASCADES + k]);
     }
     return HF_OK;
 }
@@ -1007,6 +1088,10 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
         I.dom_w = ctx->width;
         I.dom_h = ctx->height;
         I.eps_frac = 1e-6;
+        for (int k = 0; k < HF_MAX_CASCADES; ++k) {  // batched frames compute every texel
+            v->reuse[k] = ViewSlot::Reuse();
+            v->fit.cas[k].reuse_source = -1;
+        }
         const DiscParams dp = disc_params(ctx, v);
         I.K = dp.K;
         I.precision = ctx->rbf.precision;
@@ -1039,6 +1124,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             }
         }
         v->stage = 3;
+        v->data_version = ctx->data_version;
     }
     // global unit numbering: phase after phase
     int base = 0;

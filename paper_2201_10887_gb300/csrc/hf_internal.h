@@ -20,11 +20,11 @@ enum : uint32_t { kStatusTimeout = 1u, kStatusData = 2u };
 struct DevStatus {
     uint32_t flags;
     uint32_t detail;
-    unsigned long long counters[3 * HF_MAX_CASCADES];  // measurement pass (hf_view_stats)
+    unsigned long long counters[4 * HF_MAX_CASCADES];  // measurement pass (hf_view_stats)
     unsigned long long ray_counters[2];                  // measurement pass (hf_ray_stats)
-    uint32_t pad[10];  // pad[0]: the never-set flag of hf_selftest_wait_timeout
+    uint32_t pad[26];  // pad[0]: the never-set flag of hf_selftest_wait_timeout
 };
-static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
+static_assert(sizeof(DevStatus) == 384, "status block is 384 bytes");
 
 // Per-level occupancy bitmaps of a set of quadtree cells: bit (iy*nx[L]+ix)
 // of level L is set when cell (L, ix, iy) is in the set.  prefix[w] counts
@@ -86,6 +86,8 @@ struct CompactView {
 // Per-frame cascade data for the prep kernel (visible rows, texel coordinates).
 struct PrepCascade {
     double ox, oy, h, inv_h;
+    int64_t lat_x, lat_y;  // lattice fit: texel (i, j) at ((lat_x + i) h, (lat_y + j) h)
+    int32_t lattice;       // 1: lattice fit, 0: stable fit (texel at ox + i h, oy + j h)
     int32_t N;
     int32_t n_edges;  // 0 = empty cascade
     // grown polygon edge e: nx x + ny y <= c, i.e. x <= or >= (c - ny y) / nx
@@ -112,6 +114,12 @@ struct DiscCascade {
     const float* ys;
     float* tex;
     float* wtex;  // water surface texture (water layer only)
+    // temporal reuse (hf_discretize_reuse): texel (i, j) is texel
+    // (i + prev_di, j + prev_dj) of an earlier frame's texture on the same
+    // lattice; prev == nullptr: none
+    const float* prev;
+    const float* prev_w;
+    int32_t prev_N, prev_di, prev_dj;
 };
 
 struct DiscParams {

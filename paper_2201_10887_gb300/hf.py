@@ -26,7 +26,7 @@ ERROR_NAMES = {HF_ERR_ARG: "HF_ERR_ARG", HF_ERR_STATE: "HF_ERR_STATE", HF_ERR_NO
 LEAF_DTYPE = np.dtype([("level", "<i4"), ("ix", "<i4"), ("iy", "<i4"), ("value", "<f4")])
 
 EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_update_values",
-            "hf_set_camera", "hf_discretize_cascades", "hf_build_maxmip", "hf_raycast",
+            "hf_set_camera", "hf_discretize_cascades", "hf_discretize_reuse", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
             "hf_batch_launch", "hf_frame_batch", "hf_update_water", "hf_selftest_wait_timeout"]
@@ -56,7 +56,7 @@ class hf_camera(ct.Structure):
                 ("vfov", ct.c_double), ("znear", ct.c_double), ("zfar", ct.c_double),
                 ("width", ct.c_int32), ("height", ct.c_int32), ("n_cascades", ct.c_int32),
                 ("cascade_size", ct.c_int32), ("split_lambda", ct.c_double),
-                ("overlap_frac", ct.c_double)]
+                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class hf_cascade_info(ct.Structure):
@@ -67,7 +67,7 @@ class hf_cascade_info(ct.Structure):
                 ("ox", ct.c_double), ("oy", ct.c_double), ("extent", ct.c_double),
                 ("texel", ct.c_double), ("tex", ct.c_void_p), ("mip", ct.c_void_p),
                 ("spans", ct.c_void_p), ("mip_floats", ct.c_int64),
-                ("water_tex", ct.c_void_p)]
+                ("water_tex", ct.c_void_p), ("texel_ladder", ct.c_int32), ("reuse_source", ct.c_int32)]
 
     @property
     def h(self) -> float:
@@ -84,7 +84,8 @@ class hf_cascade_info(ct.Structure):
 class hf_view_stats_t(ct.Structure):
     _fields_ = [("visible_texels", ct.c_int64 * HF_MAX_CASCADES),
                 ("candidates", ct.c_int64 * HF_MAX_CASCADES),
-                ("influencers", ct.c_int64 * HF_MAX_CASCADES)]
+                ("influencers", ct.c_int64 * HF_MAX_CASCADES),
+                ("reused_texels", ct.c_int64 * HF_MAX_CASCADES)]
 
 
 class hf_batch_item(ct.Structure):
@@ -107,6 +108,7 @@ def _load():
         "hf_selftest_wait_timeout": [vp, i32, vp],
         "hf_set_camera": [vp, i32, P(hf_camera), vp, sz],
         "hf_discretize_cascades": [vp, i32, vp],
+        "hf_discretize_reuse": [vp, i32, i32, vp],
         "hf_build_maxmip": [vp, i32, vp],
         "hf_raycast": [vp, i32, vp, vp, vp],
         "hf_get_cascade": [vp, i32, i32, P(hf_cascade_info)],
@@ -208,6 +210,10 @@ def hf_discretize_cascades(ctx, slot: int, stream=None):
     _check(_lib.hf_discretize_cascades(ctx, slot, _stream(stream)))
 
 
+def hf_discretize_reuse(ctx, slot: int, prev_slot: int, stream=None):
+    _check(_lib.hf_discretize_reuse(ctx, slot, prev_slot, _stream(stream)))
+
+
 def hf_build_maxmip(ctx, slot: int, stream=None):
     _check(_lib.hf_build_maxmip(ctx, slot, _stream(stream)))
 
@@ -227,7 +233,8 @@ def hf_view_stats(ctx, slot: int, n_cascades: int, stream=None) -> dict:
     _check(_lib.hf_view_stats(ctx, slot, ct.byref(st), _stream(stream)))
     return {"visible_texels": list(st.visible_texels)[:n_cascades],
             "candidates": list(st.candidates)[:n_cascades],
-            "influencers": list(st.influencers)[:n_cascades]}
+            "influencers": list(st.influencers)[:n_cascades],
+            "reused_texels": list(st.reused_texels)[:n_cascades]}
 
 
 def hf_discretize_noalloc(ctx, cam: hf_camera, tex_out, stream=None):

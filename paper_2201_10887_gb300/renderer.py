@@ -15,11 +15,12 @@ from . import hf
 
 def camera_struct(cam) -> hf.hf_camera:
     """hf_camera from any object with eye, forward, up, vfov, znear, zfar,
-    width, height, n_cascades, cascade_size, split_lambda, overlap_frac."""
+    width, height, n_cascades, cascade_size, split_lambda, overlap_frac and
+    optionally texel_ladder (0 = the stable fit)."""
     return hf.hf_camera((ct.c_double * 3)(*cam.eye), (ct.c_double * 3)(*cam.forward),
                         (ct.c_double * 3)(*cam.up), cam.vfov, cam.znear, cam.zfar, cam.width,
                         cam.height, cam.n_cascades, cam.cascade_size, cam.split_lambda,
-                        cam.overlap_frac)
+                        cam.overlap_frac, int(getattr(cam, "texel_ladder", 0)), 0)
 
 
 class Renderer:
@@ -87,8 +88,13 @@ class Renderer:
         hf.hf_set_camera(self.ctx, slot, camera_struct(cam), v["buf"])
         return v
 
-    def discretize(self, slot: int = 0, stream=None):
-        hf.hf_discretize_cascades(self.ctx, slot, stream)
+    def discretize(self, slot: int = 0, stream=None, reuse_from: int = None):
+        """Step 1 for a view slot; with ``reuse_from`` (another slot holding an
+        earlier frame) texels on the same lattice are carried over from it."""
+        if reuse_from is None:
+            hf.hf_discretize_cascades(self.ctx, slot, stream)
+        else:
+            hf.hf_discretize_reuse(self.ctx, slot, reuse_from, stream)
 
     def build_maxmip(self, slot: int = 0, stream=None):
         hf.hf_build_maxmip(self.ctx, slot, stream)
@@ -98,10 +104,10 @@ class Renderer:
         hf.hf_raycast(self.ctx, slot, v["t"], v["hit"], stream)
         return v["t"].view(v["shape"]), v["hit"].view(v["shape"])
 
-    def render(self, cam=None, slot: int = 0, stream=None):
+    def render(self, cam=None, slot: int = 0, stream=None, reuse_from: int = None):
         if cam is not None:
             self.set_camera(cam, slot)
-        self.discretize(slot, stream)
+        self.discretize(slot, stream, reuse_from)
         self.build_maxmip(slot, stream)
         return self.raycast(slot, stream)
 

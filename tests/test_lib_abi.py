@@ -139,12 +139,19 @@ def test_call_order_and_buffer_checks(hfmod, tiny):
     assert lib.hf_build_maxmip(ctx, 0, None) == hfmod.HF_ERR_STATE
     # no persistent buffer bound yet
     assert lib.hf_discretize_cascades(ctx, 0, None) == hfmod.HF_ERR_STATE
-    bad = camera_struct(cam.with_(vfov=0.0))
+    for bad_cam in (cam.with_(vfov=0.0), cam.with_(texel_ladder=-1), cam.with_(texel_ladder=65),
+                    cam.with_(texel_ladder=2, cascade_size=3)):
+        bad = camera_struct(bad_cam)
+        assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
+    bad = camera_struct(cam)
+    bad.reserved = 1
     assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
+    # reuse needs the persistent buffer first, like every device step
+    assert lib.hf_discretize_reuse(ctx, 0, 1, None) == hfmod.HF_ERR_STATE
     hfmod.hf_destroy(ctx)
 
 
-@pytest.mark.parametrize("variant", ["base", "three", "steep", "side", "far_origin"])
+@pytest.mark.parametrize("variant", ["base", "three", "steep", "side", "far_origin", "lattice1", "lattice4"])
 def test_library_fit_matches_oracle(hfmod, orc, tiny, variant):
     import math
     import workloads
@@ -155,7 +162,10 @@ def test_library_fit_matches_oracle(hfmod, orc, tiny, variant):
            "steep": base.with_(n_cascades=2, forward=(0.0, 0.2, -1.0)),
            "side": base.with_(n_cascades=4, split_lambda=0.5, forward=(-0.8, 0.1, -0.6),
                               vfov=math.radians(40)),
-           "far_origin": base.with_(n_cascades=3, split_lambda=0.5)}[variant]
+           "far_origin": base.with_(n_cascades=3, split_lambda=0.5),
+           "lattice1": base.with_(n_cascades=3, texel_ladder=1),
+           "lattice4": base.with_(n_cascades=4, split_lambda=0.5, texel_ladder=4,
+                                  forward=(-0.8, 0.1, -0.6))}[variant]
     ctx = _tiny_ctx(hfmod, scene)
     assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
     cells = orc.Cells(scene.tree)
@@ -168,7 +178,13 @@ def test_library_fit_matches_oracle(hfmod, orc, tiny, variant):
         if li.n_poly:
             assert np.max(np.abs(li.polygon() - oc.polygon())) < 1e-9 * scene.tree.width
         assert li.near == pytest.approx(oc.near, abs=1e-9) and li.far_ext == pytest.approx(oc.far_ext, abs=1e-9)
-        assert li.texel == oc.h and li.ox == oc.ox and li.oy == oc.oy
+        if cam.texel_ladder:  # c_min 2^(m/n): the two sides may round the power differently
+            assert li.texel == pytest.approx(oc.h, rel=1e-15) and li.texel_ladder == cam.texel_ladder
+            assert li.ox == pytest.approx(oc.ox, rel=1e-15, abs=1e-12)
+            assert li.oy == pytest.approx(oc.oy, rel=1e-15, abs=1e-12)
+        else:
+            assert li.texel == oc.h and li.ox == oc.ox and li.oy == oc.oy
+        assert li.reuse_source == -1
     hfmod.hf_destroy(ctx)
 
 
@@ -195,6 +211,8 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
                                     width=int(rng.integers(16, 400)), height=int(rng.integers(16, 400)),
                                     split_lambda=float(rng.uniform(0, 1)),
                                     overlap_frac=float(rng.uniform(0, 0.2)))
+        if trial % 3 == 0:
+            cam = cam.with_(texel_ladder=int(rng.integers(1, 9)), cascade_size=max(cam.cascade_size, 4))
         assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
         ov = orc.fit(cam, tiny.tree, cells)
         for c in range(cam.n_cascades):

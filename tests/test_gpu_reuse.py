@@ -69,11 +69,12 @@ def _expected_reuse(r, slot, prev_slot, c):
     return n
 
 
-def _run_flight(torch_cuda, scene, cams, water_depth=None, precision=0, check_rays=True):
+def _run_flight(torch_cuda, scene, cams, water_depth=None, precision=0, check_rays=True, kernel=0):
     """Frames k in slots k % 2, each reusing the other slot; every frame is
     also discretized afresh in slot 2.  Returns the carried-over fraction."""
     from paper_2201_10887_gb300 import Renderer
-    r = Renderer(scene.tree, scene.sigma, scene.radius, precision=precision, water=water_depth is not None)
+    r = Renderer(scene.tree, scene.sigma, scene.radius, precision=precision, water=water_depth is not None,
+                 kernel=kernel)
     if water_depth is not None:
         r.update_water(water_depth)
     reused = visible = 0
@@ -139,6 +140,14 @@ def test_reuse_water_layer(torch_cuda):
     s = workloads.tiny_flood_config()
     cams = _flight(s.cameras[0], 4, ladder=2, n_cascades=2, cascade_size=160)
     assert _run_flight(torch_cuda, s, cams, water_depth=s.depth) > 0.5
+
+
+def test_reuse_long_jumps_and_wendland(torch_cuda, tiny):
+    """Long jumps and turns: one cascade finds a source, the other not, most
+    texels are computed; the Wendland kernel carries over too."""
+    cams = _flight(tiny.cameras[0], 4, step=(120.0, 0.0), yaw_deg=45.0, ladder=4, n_cascades=2, cascade_size=160)
+    _run_flight(torch_cuda, tiny, cams)
+    _run_flight(torch_cuda, tiny, _flight(tiny.cameras[0], 3, ladder=2, n_cascades=2, cascade_size=128), kernel=1)
 
 
 def test_reuse_fp16(torch_cuda, tiny):

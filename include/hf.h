@@ -249,7 +249,11 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t view_slot, void* stream);
 /* Step 2b (Section 5): one ray per pixel, nearest cascade first; writes
  * t_dev[y*width + x] = distance from the eye to the hit (FP32, NaN on a
  * miss) and hit_dev[y*width + x] = 0 on a miss, else 1 + the index of the
- * first cascade hit.  Pixel (0, 0) is the top-left corner.  In the overlap
+ * first cascade hit.  Pixel (0, 0) is the top-left corner.  The outputs may
+ * be device memory, managed memory, or pinned host memory mapped at the same
+ * address (cudaHostAlloc / cudaHostRegister): the kernel then writes the
+ * results to the host itself, with no separate copy; pageable host memory is
+ * refused (HF_ERR_ARG).  In the overlap
  * of cascades c and c+1 both are intersected and the hit distances are
  * blended linearly across the overlap band.  With the water layer a ray
  * stops, inside each cascade, at whichever surface it meets first (the

@@ -931,11 +931,33 @@ RayParams ray_params(const ViewSlot* v, bool water) {
 
 }  // namespace
 
+namespace {
+
+// Kernel outputs may be device memory, managed memory or pinned host memory
+// mapped at the same address (the kernel then writes over the host link
+// itself); pageable host memory would fault the kernel and is refused.
+int check_kernel_output(const void* p, const char* what) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HF_ERR_ARG, "%s is not an address CUDA knows", what);
+    }
+    if (a.type == cudaMemoryTypeUnregistered)
+        return fail(HF_ERR_ARG, "%s is pageable host memory: pass device memory or pinned host memory", what);
+    if (a.type == cudaMemoryTypeHost && a.devicePointer != p)
+        return fail(HF_ERR_ARG, "%s is pinned host memory not mapped at the same device address", what);
+    return HF_OK;
+}
+
+}  // namespace
+
 int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
     ApiRange range_("hf_raycast");
     ViewSlot* v = get_view(ctx, slot);
     if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
     if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
+    if (int rc = check_kernel_output(t_dev, "t output")) return rc;
+    if (int rc = check_kernel_output(hit_dev, "hit output")) return rc;
     RayParams rp = ray_params(v, ctx->rbf.water != 0);
     rp.t_out = t_dev;
     rp.hit_out = hit_dev;

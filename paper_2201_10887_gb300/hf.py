@@ -218,8 +218,17 @@ def hf_build_maxmip(ctx, slot: int, stream=None):
     _check(_lib.hf_build_maxmip(ctx, slot, _stream(stream)))
 
 
+def _out_ptr(t) -> ct.c_void_p:
+    """A kernel output: a contiguous CUDA tensor or a pinned host tensor."""
+    if not t.is_contiguous() or not (t.is_cuda or t.is_pinned()):
+        raise ValueError("expected a contiguous CUDA tensor or a pinned host tensor")
+    return ct.c_void_p(t.data_ptr())
+
+
 def hf_raycast(ctx, slot: int, t_out, hit_out, stream=None):
-    _check(_lib.hf_raycast(ctx, slot, _dptr(t_out), _dptr(hit_out), _stream(stream)))
+    """t_out / hit_out: CUDA tensors, or pinned host tensors that the kernel
+    writes directly."""
+    _check(_lib.hf_raycast(ctx, slot, _out_ptr(t_out), _out_ptr(hit_out), _stream(stream)))
 
 
 def hf_get_cascade(ctx, slot: int, c: int) -> hf_cascade_info:

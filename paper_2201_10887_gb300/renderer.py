@@ -31,14 +31,17 @@ class Renderer:
     ``water=True`` the leaves also carry water depths (``update_water``) and
     every view gets a water surface texture per cascade (the max mipmap then
     bounds both surfaces).  ``kernel`` selects the RBF weight (hf.HF_RBF_*).
+    With ``host_outputs`` the ray cast writes ``t`` and ``hit`` straight into
+    pinned host tensors (no copy after the frame).
     """
 
     def __init__(self, tree, sigma: float, radius: float, precision: int = hf.HF_PREC_FP32,
                  bucket_level: int = -1, device=None, stream=None, water: bool = False,
-                 kernel: int = hf.HF_RBF_GAUSSIAN):
+                 kernel: int = hf.HF_RBF_GAUSSIAN, host_outputs: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
+        self.host_outputs = bool(host_outputs)
         desc = hf.hf_quadtree_desc(tree.origin_x, tree.origin_y, tree.root_cell, tree.root_nx,
                                    tree.root_ny, tree.max_level)
         leaves = hf.leaves_array(tree.level, tree.ix, tree.iy, tree.value)
@@ -63,8 +66,12 @@ class Renderer:
             self.views[slot] = v
         npx = cam.width * cam.height
         if v.get("npx") != npx:
-            v["t"] = self.torch.empty(npx, dtype=self.torch.float32, device=self.device)
-            v["hit"] = self.torch.empty(npx, dtype=self.torch.uint8, device=self.device)
+            if self.host_outputs:
+                v["t"] = self.torch.empty(npx, dtype=self.torch.float32, pin_memory=True)
+                v["hit"] = self.torch.empty(npx, dtype=self.torch.uint8, pin_memory=True)
+            else:
+                v["t"] = self.torch.empty(npx, dtype=self.torch.float32, device=self.device)
+                v["hit"] = self.torch.empty(npx, dtype=self.torch.uint8, device=self.device)
             v["npx"] = npx
         v["shape"] = (cam.height, cam.width)
         v["C"] = cam.n_cascades
@@ -72,7 +79,9 @@ class Renderer:
 
     def bind_view(self, slot: int, cam, view_buf, t_out, hit_out):
         """Use caller-provided buffers for a view slot (uint8 view buffer of
-        at least view_bytes(), float32 t and uint8 hit of width*height)."""
+        at least view_bytes(), float32 t and uint8 hit of width*height; t and
+        hit may be pinned host tensors, which the ray cast then writes
+        directly)."""
         need = self.view_bytes(cam.n_cascades, cam.cascade_size)
         npx = cam.width * cam.height
         if view_buf.numel() < need or t_out.numel() < npx or hit_out.numel() < npx:

@@ -294,3 +294,30 @@ def test_dem_frame_sampled(orc, torch_cuda, frame):
     assert frac <= HIT_MISMATCH and off == 0, (frac, off)
     assert terr <= RAY_REL, terr
     r.close()
+
+
+def test_outputs_in_pinned_host_memory(torch_cuda, tiny):
+    """The ray cast writes t and hit straight into pinned host memory, bit for
+    bit what it writes to device memory; pageable host memory is refused
+    before any launch."""
+    import ctypes as ct
+    from paper_2201_10887_gb300 import Renderer, hf
+    cam = tiny.cameras[0].with_(n_cascades=2, cascade_size=128)
+    a = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    b = Renderer(tiny.tree, tiny.sigma, tiny.radius, host_outputs=True)
+    ta, ha = a.render(cam)
+    tb, hb = b.render(cam)
+    b.sync()
+    assert not tb.is_cuda and tb.is_pinned()
+    assert torch_cuda.equal(ta.cpu().view(torch_cuda.int32), tb.view(torch_cuda.int32))
+    assert torch_cuda.equal(ha.cpu(), hb)
+    assert (hb > 0).sum() > 1000
+    pageable_t = np.zeros(cam.width * cam.height, np.float32)
+    pageable_h = np.zeros(cam.width * cam.height, np.uint8)
+    rc = hf.lib().hf_raycast(a.ctx, 0, pageable_t.ctypes.data_as(ct.c_void_p),
+                             pageable_h.ctypes.data_as(ct.c_void_p), None)
+    assert rc == hf.HF_ERR_ARG
+    assert "pageable" in hf.hf_last_error()
+    assert not pageable_t.any()
+    a.close()
+    b.close()

@@ -47,7 +47,8 @@ def test_noalloc_matches_regular_entry_point(torch_cuda, tiny):
     r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     amp = float(np.abs(tiny.tree.value).max())
     cams = [tiny.cameras[0].with_(n_cascades=3, cascade_size=200, split_lambda=0.5),
-            tiny.cameras[0].with_(n_cascades=2, cascade_size=160, forward=(0.3, 0.9, -0.4))]
+            tiny.cameras[0].with_(n_cascades=2, cascade_size=160, forward=(0.3, 0.9, -0.4)),
+            tiny.cameras[0].with_(n_cascades=2, cascade_size=144, texel_ladder=2)]
     for cam in cams:  # two calls in a row, each against the regular entry point
         ref = _regular_textures(r, cam)
         N = cam.cascade_size

@@ -373,6 +373,14 @@ int hf_sync(hf_ctx* ctx, void* stream);
  * and the context stays usable.  For tests of error handling. */
 int hf_selftest_wait_timeout(hf_ctx* ctx, int32_t polls, void* stream);
 
+/* Measurement support (no counterpart in the paper): the current device's
+ * throughput of the two arithmetic units the discretization is designed
+ * against -- MUFU ex2.approx (the exponential of Eq. 1) and FP32 fused
+ * multiply-add -- in operations per second over all SMs, and its SM count.
+ * Short dependency-chain kernels on `stream`, timed with CUDA events; waits
+ * for them.  Needs no context. */
+int hf_measure_unit_rates(double* ex2_per_s, double* ffma_per_s, int32_t* sm_count, void* stream);
+
 /* Frees the context's host memory.  Device buffers belong to the caller. */
 void hf_destroy(hf_ctx* ctx);
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libhf.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["hf_host.cpp", "hf_fit.cpp", "hf_kernels.cu", "hf_noalloc.cu"]
+SOURCES = ["hf_host.cpp", "hf_fit.cpp", "hf_kernels.cu", "hf_noalloc.cu", "hf_rates.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-pthread,-ffp-contract=off",
           "-I" + CSRC, "-I" + INCLUDE]

@@ -1227,6 +1227,16 @@ int hf_selftest_wait_timeout(hf_ctx* ctx, int32_t polls, void* stream) {
     return HF_OK;
 }
 
+int hf_measure_unit_rates(double* ex2_per_s, double* ffma_per_s, int32_t* sm_count, void* stream) {
+    ApiRange range_("hf_measure_unit_rates");
+    if (!ex2_per_s || !ffma_per_s || !sm_count) return fail(HF_ERR_ARG, "null argument");
+    int sms = 0;
+    int e = measure_unit_rates(ex2_per_s, ffma_per_s, &sms, stream);
+    if (e) return cuda_fail(e, "unit-rate kernels");
+    *sm_count = sms;
+    return HF_OK;
+}
+
 void hf_destroy(hf_ctx* ctx) { delete ctx; }
 
 }  // extern "C"

@@ -225,6 +225,7 @@ int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsV
 int launch_prep(const PrepParams& p, void* stream);
 int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                         const CompactView& cv, int precision, void* stream);
+int measure_unit_rates(double* ex2_per_s, double* ffma_per_s, int* sm_count, void* stream);
 int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
                             DevStatus* status, void* stream);
 int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,

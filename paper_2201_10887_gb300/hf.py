@@ -29,7 +29,8 @@ EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_up
             "hf_set_camera", "hf_discretize_cascades", "hf_discretize_reuse", "hf_build_maxmip", "hf_raycast",
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
-            "hf_batch_launch", "hf_frame_batch", "hf_update_water", "hf_selftest_wait_timeout"]
+            "hf_batch_launch", "hf_frame_batch", "hf_update_water", "hf_selftest_wait_timeout",
+            "hf_measure_unit_rates"]
 HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
 HF_BATCH_PERSISTENT = 16
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
@@ -120,6 +121,7 @@ def _load():
         "hf_batch_prepare": [P(hf_batch_item), i32, i32, vp, sz],
         "hf_batch_launch": [vp, vp, sz, vp],
         "hf_frame_batch": [P(hf_batch_item), i32, i32, vp, sz, vp, sz, vp],
+        "hf_measure_unit_rates": [P(ct.c_double), P(ct.c_double), P(i32), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -287,6 +289,13 @@ def hf_frame_batch(items, flags: int, host_buf, dev_buf, stream=None):
 
 def hf_sync(ctx, stream=None):
     _check(_lib.hf_sync(ctx, _stream(stream)))
+
+
+def hf_measure_unit_rates(stream=None) -> dict:
+    """Measured MUFU ex2 and FP32 FMA rates (operations / s) and the SM count."""
+    ex2, ffma, sms = ct.c_double(), ct.c_double(), ct.c_int32()
+    _check(_lib.hf_measure_unit_rates(ct.byref(ex2), ct.byref(ffma), ct.byref(sms), _stream(stream)))
+    return {"ex2_per_s": ex2.value, "ffma_per_s": ffma.value, "sms": sms.value}
 
 
 def hf_destroy(ctx):

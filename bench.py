@@ -39,7 +39,7 @@ WORKLOAD = "dem: 4096^2-equivalent quadtree (10-160 m cells, 4.5 M leaves), 4x20
 # Nominal sm_103a unit counts per SM and clock: FP32 lanes and MUFU (ex2) lanes.
 SMS = 152
 FP32_PER_SM = 128
-MUFU_PER_SM = 16
+MUFU_PER_SM = 32   # ex2 lanes per SM on GB300 (twice earlier parts; hf_measure_unit_rates confirms)
 FP32_OPS_PER_TERM = 9   # 2 sub, d^2 (mul + fma), scale, -K, max, sum, fma
 RAY_OPS_PER_VISIT = 20  # exit times, z range, node index, compare
 RAY_OPS_PER_TEST = 30   # bilinear coefficients, quadratic, root selection (+ 1 sqrt)

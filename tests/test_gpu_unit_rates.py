@@ -1,8 +1,9 @@
 """hf_measure_unit_rates: the measured MUFU ex2 and FP32 FMA rates that the
 benchmark reports beside its derived peaks.  Checked against the device's SM
-count and the unit counts per SM (16 ex2 and 128 FMA lanes) at its clock
-range: a measured rate may not exceed the derived one at the maximum clock
-by more than rounding, nor fall far below it."""
+count and the unit counts per SM (32 ex2 lanes -- GB300 doubles the 16 of
+earlier parts -- and 128 FMA lanes) at its clock range: a measured rate may
+not exceed the derived one at the maximum clock by more than rounding, nor
+fall far below it."""
 
 import pytest
 
@@ -20,6 +21,6 @@ def test_unit_rates_match_the_unit_counts():
     r = hf.hf_measure_unit_rates()
     assert r["sms"] == props.multi_processor_count
     max_hz = 2.2e9  # above the part's maximum SM clock (2070 MHz)
-    for key, lanes in (("ex2_per_s", 16), ("ffma_per_s", 128)):
+    for key, lanes in (("ex2_per_s", 32), ("ffma_per_s", 128)):
         derived = lanes * r["sms"] * max_hz
         assert 0.3 * derived < r[key] <= 1.01 * derived, (key, r[key], derived)

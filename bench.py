@@ -727,7 +727,7 @@ def run_flood_workload(args):
         for f in frame_schedule(args.frames, args.warmup, 0, 1):
             r.render(cams[f])
         r.sync()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in sched]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in sched]
         torch.cuda.synchronize()
         for k, f in enumerate(sched):
             flush.fill_(float(k))
@@ -743,7 +743,7 @@ def run_flood_workload(args):
             e[3].record(stream)
         torch.cuda.synchronize()
         r.sync()
-        return {"frame": [e[0].elapsed_time(e[3]) for e in ev], "discretize": [e[0].elapsed_time(e[1]) for e in ev],
+        return {"frame": [e[0].elapsed_time(e[3]) for e in ev], "discretize": [e[4].elapsed_time(e[1]) for e in ev],
                 "maxmip": [e[1].elapsed_time(e[2]) for e in ev], "raycast": [e[2].elapsed_time(e[3]) for e in ev]}
 
     rw = Renderer(scene.tree, scene.sigma, scene.radius, water=True)

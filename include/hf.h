@@ -315,7 +315,8 @@ int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_o
 /* Batched frames (the paper times one view; serving many views and tiles at
  * once is this library's extension).  Each item is one view slot of one
  * context whose camera is set with hf_set_camera; t_dev / hit_dev receive its
- * ray cast as in hf_raycast.  hf_batch_prepare writes descriptors of all items
+ * ray cast as in hf_raycast (device memory or pinned host memory, checked by
+ * hf_batch_prepare).  hf_batch_prepare writes descriptors of all items
  * into a caller-provided host buffer (pinned, so that hf_batch_launch can be
  * captured in a CUDA graph); hf_batch_launch copies them to a caller-provided
  * device buffer and runs the whole batch: one persistent launch drains a work

@@ -1068,6 +1068,10 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
     if ((flags & kBatchRaysInside) && !(flags & kBatchPersistent))
         return fail(HF_ERR_ARG, "HF_BATCH_RAYS_INSIDE needs HF_BATCH_PERSISTENT");
     if (((flags & kBatchRayTileMask) >> 1) == 3) return fail(HF_ERR_ARG, "choose one ray tile shape");
+    for (int32_t i = 0; i < n; ++i) {
+        if (int rc2 = check_kernel_output(items[i].t_dev, "batch item t output")) return rc2;
+        if (int rc2 = check_kernel_output(items[i].hit_dev, "batch item hit output")) return rc2;
+    }
     int dev = 0;
     int e = cudaGetDevice(&dev);
     if (e) return cuda_fail(e, "cudaGetDevice");

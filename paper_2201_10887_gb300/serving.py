@@ -6,8 +6,10 @@ first come first served while a view slot is free and their device memory
 (cascade textures, max mipmaps, outputs) fits the budget, launches each
 admitted group as one batched frame (``hf_frame_batch``) on the next of a few
 streams -- so groups admitted while others are still running overlap on the
-device -- and copies each view's ray-cast result to pinned host memory.  A
-request's latency runs from its arrival to its result being on the host.
+device.  Each view's ray cast writes its result straight into pinned host
+memory (``host_outputs``; else into device memory, copied afterwards), so the
+device budget holds only the views' cascades.  A request's latency runs from
+its arrival to its result being on the host.
 Slots and memory are returned as soon as a group's event has completed.
 """
 
@@ -61,10 +63,12 @@ class Arena:
 
 class Server:
     def __init__(self, renderer: Renderer, memory_budget: int, max_slots: int = 32,
-                 n_streams: int = 3, max_group: int = 16, flags: int = 0, keep_results=False):
+                 n_streams: int = 3, max_group: int = 16, flags: int = 0, keep_results=False,
+                 host_outputs: bool = True):
         import torch
         self.torch = torch
         self.r = renderer
+        self.host_outputs = bool(host_outputs)
         self.budget = int(memory_budget)
         self.max_slots = max_slots
         self.max_group = max_group
@@ -82,10 +86,12 @@ class Server:
         self.max_used = 0
 
     def request_bytes(self, cam) -> int:
-        """Device memory of one view: per-view buffer plus t and hit."""
+        """Device memory of one view: per-view buffer (plus t and hit when
+        the outputs stay on the device)."""
         r = Arena._round
         npx = cam.width * cam.height
-        return r(self.r.view_bytes(cam.n_cascades, cam.cascade_size)) + r(4 * npx) + r(npx)
+        out = 0 if self.host_outputs else r(4 * npx) + r(npx)
+        return r(self.r.view_bytes(cam.n_cascades, cam.cascade_size)) + out
 
     def _bind(self, req, slot, off):
         cam = req.camera
@@ -93,8 +99,11 @@ class Server:
         vb = r(self.r.view_bytes(cam.n_cascades, cam.cascade_size))
         npx = cam.width * cam.height
         buf = self.pool[off: off + vb]
-        t = self.pool[off + vb: off + vb + 4 * npx].view(self.torch.float32)
-        h = self.pool[off + vb + r(4 * npx): off + vb + r(4 * npx) + npx]
+        if self.host_outputs:
+            t, h = self._host_outputs(slot, cam)
+        else:
+            t = self.pool[off + vb: off + vb + 4 * npx].view(self.torch.float32)
+            h = self.pool[off + vb + r(4 * npx): off + vb + r(4 * npx) + npx]
         self.r.bind_view(slot, cam, buf, t, h)
 
     def _host_outputs(self, slot, cam):
@@ -121,13 +130,14 @@ class Server:
             self.host_desc[k] = torch.empty(host_bytes, dtype=torch.uint8, pin_memory=True)
             self.dev_desc[k] = torch.empty(dev_bytes, dtype=torch.uint8, device=self.r.device)
         hf.hf_frame_batch(items, self.flags, self.host_desc[k], self.dev_desc[k], s)
-        with torch.cuda.stream(s):
-            for req, slot in group:
-                v = self.r.views[slot]
-                n = req.camera.width * req.camera.height
-                ht, hh = self._host_outputs(slot, req.camera)
-                ht[:n].copy_(v["t"][:n], non_blocking=True)
-                hh[:n].copy_(v["hit"][:n], non_blocking=True)
+        if not self.host_outputs:
+            with torch.cuda.stream(s):
+                for req, slot in group:
+                    v = self.r.views[slot]
+                    n = req.camera.width * req.camera.height
+                    ht, hh = self._host_outputs(slot, req.camera)
+                    ht[:n].copy_(v["t"][:n], non_blocking=True)
+                    hh[:n].copy_(v["hit"][:n], non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(s)
         self.stream_event[k] = ev

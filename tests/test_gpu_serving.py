@@ -35,15 +35,18 @@ def _requests(tiny, n=24, seed=3, span=0.15):
     return reqs
 
 
-@pytest.mark.parametrize("realtime", [False, True])
-def test_server_results_equal_single_views(torch_cuda, tiny, realtime):
+@pytest.mark.parametrize("realtime,host_outputs", [(False, True), (True, True), (False, False)])
+def test_server_results_equal_single_views(torch_cuda, tiny, realtime, host_outputs):
+    """Each result equals the view rendered alone, with the ray casts writing
+    into pinned host memory or into device memory copied afterwards."""
     from paper_2201_10887_gb300 import Renderer, Server
     r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     reqs = _requests(tiny)
-    probe = Server(r, 1 << 20, max_slots=1)
+    probe = Server(r, 1 << 20, max_slots=1, host_outputs=host_outputs)
     sizes = [probe.request_bytes(q.camera) for q in reqs]
     budget = int(2.5 * max(sizes))              # only a few views fit at once
-    srv = Server(r, budget, max_slots=6, n_streams=3, max_group=4, keep_results=True)
+    srv = Server(r, budget, max_slots=6, n_streams=3, max_group=4, keep_results=True,
+                 host_outputs=host_outputs)
     out = srv.run(reqs, realtime=realtime)
     assert out["requests"] == len(reqs) and len(out["results"]) == len(reqs)
     assert out["max_memory_used"] <= budget

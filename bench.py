@@ -534,9 +534,10 @@ def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream,
 
 
 def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed=2):
-    """Frame time on the same flight path flown slower (1 200 and 12 000
-    frames instead of 120: ~100 m and ~10 m per frame), n consecutive frames
-    from its middle, three ways: the stable fit computing every texel, the
+    """Frame time on the flight path of the main line (120 frames, ~1 km per
+    frame) and the same path flown slower (1 200 and 12 000 frames: ~100 m
+    and ~10 m per frame), up to n consecutive frames from its middle, three
+    ways: the stable fit computing every texel, the
     lattice fit (`ladder` texel sizes per octave) computing every texel, and
     the lattice fit carrying texels over from the previous frame
     (hf_discretize_reuse; view slots 0 and 1 alternate).  L2 flushed between
@@ -549,11 +550,13 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
     c0 = scene.cameras[0]
     r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
     out = {"texel_ladder": ladder, "frames": n}
-    for n_frames in (1200, 12000):
+    n_all = n
+    for n_frames in (120, 1200, 12000):
         path = workloads.flight_path(scene.tree, scene.fbm, seed, n_frames, c0.width, c0.height,
                                      n_cascades=c0.n_cascades, cascade_size=c0.cascade_size,
                                      split_lambda=c0.split_lambda)
-        first = n_frames // 2 - (n + warmup) // 2
+        n = min(n_all, n_frames - warmup)
+        first = max(0, n_frames // 2 - (n + warmup) // 2)
         seq = path[first:first + warmup + n]
         step_m = float(np.mean([np.linalg.norm(np.subtract(a.eye, b.eye)) for a, b in zip(seq, seq[1:])]))
         res = {"metres_per_frame": step_m}
@@ -595,6 +598,7 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
                         vis += sum(st["visible_texels"])
                 r.sync()
                 res[mode]["reused_fraction"] = reused / max(vis, 1)
+        res["frames"] = n
         out[f"flight_{n_frames}_frames"] = res
     r.close()
     del r

@@ -755,7 +755,6 @@ int discretize_view(hf_ctx* ctx, ViewSlot* v, void* stream) {
     const int C = v->cam.n_cascades, N = v->cam.cascade_size;
     PrepParams pp;
     std::memset(&pp, 0, sizeof(pp));
-    (void)N;
     pp.C = C;
     pp.max_N = N;
     pp.dom_w = ctx->width;

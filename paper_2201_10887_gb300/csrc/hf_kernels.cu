@@ -992,7 +992,12 @@ struct RayDir {
 // terrain and, where its four corners are wet, the water surface: the first
 // patch with any root holds the first hit of either surface, the nearer root
 // of the two (the water surface on a tie; on_water says which).
-template <bool COUNT, bool COH, bool UNION = false>
+// SIGNS (bit 0: du > 0, bit 1: dv > 0, bit 2: dz < 0) is constant per ray
+// and nearly always per warp: the walk is compiled for each combination.  A
+// zero component takes the non-positive branch, which leaves the walk as it
+// would be: the exit time along it is infinite, and the clamp of the other
+// coordinate returns the current cell.
+template <bool COUNT, bool COH, bool UNION, int SIGNS>
 __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
                                               float ez, float ta, float tb, float& t_hit, bool& on_water,
                                               DevStatus* status, uint32_t pixel, unsigned& visits, unsigned& tests) {
@@ -1018,8 +1023,8 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const float idu = d.rdx * c.h, idv = d.rdy * c.h;
     const float ou = d.dx != 0.f ? -r.eu * idu : INFINITY;
     const float ov = d.dy != 0.f ? -r.ev * idv : INFINITY;
-    const int bu = r.du > 0.f ? 1 : 0, bv = r.dv > 0.f ? 1 : 0;
-    const bool zneg = r.dz < 0.f;
+    constexpr int bu = SIGNS & 1, bv = (SIGNS >> 1) & 1;
+    constexpr bool zneg = (SIGNS >> 2) & 1;
     const float slack = 2e-6f * fabsf(top);
     int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
@@ -1065,7 +1070,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
             ncj = cj;
             if (k > 0) {
                 int c2 = __float2int_rd(fmaf(te, r.dv, r.ev));
-                c2 = r.dv > 0.f ? max(c2, cj) : (r.dv < 0.f ? min(c2, cj) : cj);
+                c2 = bv ? max(c2, cj) : min(c2, cj);
                 ncj = min(max(c2, nj << k), ((nj + 1) << k) - 1);
             }
         } else {
@@ -1073,7 +1078,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
             nci = ci;
             if (k > 0) {
                 int c2 = __float2int_rd(fmaf(te, r.du, r.eu));
-                c2 = r.du > 0.f ? max(c2, ci) : (r.du < 0.f ? min(c2, ci) : ci);
+                c2 = bu ? max(c2, ci) : min(c2, ci);
                 nci = min(max(c2, ni << k), ((ni + 1) << k) - 1);
             }
         }
@@ -1128,7 +1133,7 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayD
 // Section 5: the blend runs linearly in projected depth across the overlap
 // band of cascades c and c+1 when both are hit); 0x80 marks a first-hit
 // cascade whose hit is on the water surface.
-template <bool COUNT, bool COH, bool UNION>
+template <bool COUNT, bool COH, bool UNION, int SIGNS>
 __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_off)[kMaxLevels], const RayDir& d,
                                               DevStatus* status, uint32_t pix, unsigned& visits, unsigned& tests,
                                               float& t, int& hit) {
@@ -1139,7 +1144,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
         float ta, tb, tc;
         bool wet = false;
         if (!cascade_interval(cc, d, ta, tb)) continue;
-        if (!trace_cascade<COUNT, COH, UNION>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
+        if (!trace_cascade<COUNT, COH, UNION, SIGNS>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
             continue;
         hit = (1 + c) | (wet ? 0x80 : 0);
         t = tc;
@@ -1150,7 +1155,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
                 float ta2, tb2, t2;
                 bool wet2 = false;
                 if (cascade_interval(cn, d, ta2, tb2) &&
-                    trace_cascade<COUNT, COH, UNION>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
+                    trace_cascade<COUNT, COH, UNION, SIGNS>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
                                                      visits, tests)) {
                     const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
                     t = fmaf(al, t2 - tc, tc);
@@ -1185,7 +1190,16 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
     const uint32_t pix = uint32_t(y) * uint32_t(p.W) + uint32_t(x);
     int hit;
     float t;
-    cast_cascades<COUNT, COH, WATER>(p, s_off, d, status, pix, visits, tests, t, hit);
+    switch ((d.dx > 0.f ? 1 : 0) | (d.dy > 0.f ? 2 : 0) | (d.dz < 0.f ? 4 : 0)) {
+    case 0: cast_cascades<COUNT, COH, WATER, 0>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 1: cast_cascades<COUNT, COH, WATER, 1>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 2: cast_cascades<COUNT, COH, WATER, 2>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 3: cast_cascades<COUNT, COH, WATER, 3>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 4: cast_cascades<COUNT, COH, WATER, 4>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 5: cast_cascades<COUNT, COH, WATER, 5>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 6: cast_cascades<COUNT, COH, WATER, 6>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    default: cast_cascades<COUNT, COH, WATER, 7>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    }
     if (!COUNT) {
         p.t_out[pix] = t;
         p.hit_out[pix] = uint8_t(hit);

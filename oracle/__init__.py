@@ -87,6 +87,8 @@ def lib():
         _lib.orc_ray_patch.argtypes = [d] * 11 + [P(d)]
         _lib.orc_fit.restype = i
         _lib.orc_fit.argtypes = [P(CameraC), P(Domain), P(ViewC)]
+        _lib.orc_fit_follow.restype = i
+        _lib.orc_fit_follow.argtypes = [P(CameraC), P(Domain), P(ct.c_longlong), P(ViewC)]
         _lib.orc_ladder_fit.restype = None
         _lib.orc_ladder_fit.argtypes = [d, d, d, d, d, i, i, P(ct.c_longlong), P(ct.c_longlong),
                                         P(ct.c_longlong), P(d)]
@@ -155,10 +157,16 @@ def camera_struct(cam, tree) -> CameraC:
                    cam.overlap_frac, int(getattr(cam, "texel_ladder", 0)))
 
 
-def fit(cam, tree, cells: Cells) -> ViewC:
+def fit(cam, tree, cells: Cells, follow=None) -> ViewC:
+    """Section 3 fit; `follow` (ladder steps of an earlier frame's cascades)
+    applies the lattice fit's hysteresis."""
     v = ViewC()
     c = camera_struct(cam, tree)
-    rc = lib().orc_fit(ct.byref(c), ct.byref(cells.domain), ct.byref(v))
+    if follow is not None:
+        steps = (ct.c_longlong * MAX_CASCADES)(*([int(x) for x in follow] + [0] * (MAX_CASCADES - len(follow))))
+        rc = lib().orc_fit_follow(ct.byref(c), ct.byref(cells.domain), steps, ct.byref(v))
+    else:
+        rc = lib().orc_fit(ct.byref(c), ct.byref(cells.domain), ct.byref(v))
     if rc != 0:
         raise ValueError("orc_fit rejected the camera")
     return v

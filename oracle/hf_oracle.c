@@ -387,7 +387,7 @@ void orc_ladder_fit(double x0, double y0, double x1, double y1, double c_min, in
     *j0 = (long long)floor(y0 / *h + 1e-9);
 }
 
-static void lattice_fit(orc_cascade* c, double c_min, int N, int n) {
+static void lattice_fit(orc_cascade* c, double c_min, int N, int n, const long long* follow) {
     c->N = N;
     if (c->n_poly < 3) {
         c->n_poly = 0;
@@ -402,6 +402,14 @@ static void lattice_fit(orc_cascade* c, double c_min, int N, int n) {
         }
         c->aabb[0] = x0; c->aabb[1] = y0; c->aabb[2] = x1; c->aabb[3] = y1;
         orc_ladder_fit(x0, y0, x1, y1, c_min, N, n, &c->snap_k, &c->snap_x, &c->snap_y, &c->h);
+        /* hysteresis (following an earlier frame): keep that frame's step if
+         * it is one step coarser than the smallest that fits */
+        if (follow && *follow == c->snap_k + 1) {
+            c->snap_k = *follow;
+            c->h = ladder_spacing(c_min, c->snap_k, n);
+            c->snap_x = (long long)floor(x0 / c->h + 1e-9);
+            c->snap_y = (long long)floor(y0 / c->h + 1e-9);
+        }
     }
     c->ox = (double)c->snap_x * c->h;
     c->oy = (double)c->snap_y * c->h;
@@ -451,6 +459,10 @@ static void stable_fit(orc_cascade* c, double c_min, int N) {
  * first cascade starts at n, the last ends at f, and every far plane but
  * the last is pushed out by overlap_frac of its cascade's depth span.     */
 int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out) {
+    return orc_fit_follow(cam, dom, NULL, out);
+}
+
+int orc_fit_follow(const orc_camera* cam, const orc_domain* dom, const long long* follow, orc_view* out) {
     memset(out, 0, sizeof(*out));
     int C = cam->n_cascades;
     if (C < 1 || C > ORC_MAX_CASCADES || cam->cascade_size < 2) return -1;
@@ -495,7 +507,7 @@ int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out) {
                         ? clip_band(out->hull, out->n_hull, out->dir2, cam->eye, c->near_, c->far_ext, c->poly)
                         : 0;
         if (cam->texel_ladder > 0)
-            lattice_fit(c, dom->c_min, cam->cascade_size, cam->texel_ladder);
+            lattice_fit(c, dom->c_min, cam->cascade_size, cam->texel_ladder, follow ? follow + k : NULL);
         else
             stable_fit(c, dom->c_min, cam->cascade_size);
     }

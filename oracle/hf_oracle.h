@@ -86,6 +86,10 @@ void orc_rbf_points(const double* cx, const double* cy, const double* cs, const 
 
 /* ---- Section 3: cascade fitting ---- */
 int orc_fit(const orc_camera* cam, const orc_domain* dom, orc_view* out);
+/* the same, with the lattice fit following an earlier frame: cascade k keeps
+ * ladder step follow[k] where that is one step coarser than the smallest
+ * that fits (follow: n_cascades steps, or NULL) */
+int orc_fit_follow(const orc_camera* cam, const orc_domain* dom, const long long* follow, orc_view* out);
 /* lattice fit of a box [x0, x1] x [y0, y1] for n ladder steps per octave:
  * returns the ladder index m, the lattice origin (i0, j0) and h */
 void orc_ladder_fit(double x0, double y0, double x1, double y1, double c_min, int N, int n,

@@ -341,3 +341,30 @@ def test_ladder_fit_keeps_spacing_under_translation(orc):
                 for ax, d in ((0, shift[0]), (1, shift[1])):
                     da = (b.snap_x - a.snap_x) if ax == 0 else (b.snap_y - a.snap_y)
                     assert abs(da * a.h - d) <= a.h * (1 + 1e-9)
+
+
+def test_ladder_fit_follow_rule(orc, tiny):
+    """Hysteresis of the lattice fit: a cascade keeps an earlier frame's
+    ladder step only when it is exactly one step coarser than the smallest
+    that fits; the box stays covered and the origin on the lattice."""
+    cells = orc.Cells(tiny.tree)
+    cmin = cells.domain.c_min
+    seen = 0
+    for cam in _cams(tiny):
+        cam = cam.with_(texel_ladder=4)
+        v0 = orc.fit(cam, tiny.tree, cells)
+        m = [v0.cas[k].snap_k for k in range(v0.n_cascades)]
+        for delta, expect in ((1, 1), (2, 0), (-1, 0), (0, 0)):
+            v = orc.fit(cam, tiny.tree, cells, follow=[x + delta for x in m])
+            for k in range(v.n_cascades):
+                c = v.cas[k]
+                if not c.n_poly:
+                    continue
+                seen += 1
+                assert c.snap_k == m[k] + expect, (delta, k)
+                x0, y0, x1, y1 = c.aabb
+                assert c.h == pytest.approx(cmin * 2.0 ** (c.snap_k / 4), rel=1e-14)
+                assert c.ox == c.snap_x * c.h and x0 - c.h < c.ox <= x0 + 1e-9 * c.h
+                assert c.oy == c.snap_y * c.h and y0 - c.h < c.oy <= y0 + 1e-9 * c.h
+                assert c.ox + c.E >= x1 - 1e-9 * c.E and c.oy + c.E >= y1 - 1e-9 * c.E
+    assert seen >= 40

@@ -538,9 +538,11 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
     frame) and the same path flown slower (1 200 and 12 000 frames: ~100 m
     and ~10 m per frame), up to n consecutive frames from its middle, three
     ways: the stable fit computing every texel, the
-    lattice fit (`ladder` texel sizes per octave) computing every texel, and
-    the lattice fit carrying texels over from the previous frame
-    (hf_discretize_reuse; view slots 0 and 1 alternate).  L2 flushed between
+    lattice fit (`ladder` texel sizes per octave) computing every texel, the
+    lattice fit carrying texels over from the previous frame
+    (hf_discretize_reuse; view slots 0 and 1 alternate), and the same with
+    the fit following the previous frame's texel sizes
+    (hf_set_camera_follow).  L2 flushed between
     frames as in the main line; the carried-over share of the visible texels
     comes from an untimed counting pass over the same frames."""
     import numpy as np
@@ -560,9 +562,10 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
         seq = path[first:first + warmup + n]
         step_m = float(np.mean([np.linalg.norm(np.subtract(a.eye, b.eye)) for a, b in zip(seq, seq[1:])]))
         res = {"metres_per_frame": step_m}
-        for mode in ("stable", "lattice", "lattice_reuse"):
+        for mode in ("stable", "lattice", "lattice_reuse", "lattice_follow_reuse"):
             cams_m = [c.with_(texel_ladder=0 if mode == "stable" else ladder) for c in seq]
-            reuse = mode == "lattice_reuse"
+            reuse = mode.endswith("reuse")
+            follow = mode == "lattice_follow_reuse"
             ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n)]
             for k, cam in enumerate(cams_m):
                 slot = k % 2
@@ -571,7 +574,7 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
                 flush.fill_(float(k))
                 if e:
                     e[0].record(stream)
-                r.set_camera(cam, slot)
+                r.set_camera(cam, slot, follow=prev if follow else None)
                 if e:
                     e[3].record(stream)
                 r.discretize(slot, reuse_from=prev)
@@ -590,7 +593,7 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
                 reused = vis = 0
                 for k, cam in enumerate(cams_m[warmup - 1:]):
                     slot = k % 2
-                    r.set_camera(cam, slot)
+                    r.set_camera(cam, slot, follow=1 - slot if (follow and k > 0) else None)
                     r.discretize(slot, reuse_from=1 - slot if k > 0 else None)
                     if k > 0:
                         st = r.stats(slot)

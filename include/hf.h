@@ -209,6 +209,17 @@ int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* st
 int hf_set_camera(hf_ctx* ctx, int32_t view_slot, const hf_camera* cam, void* dev_view,
                   size_t bytes);
 
+/* hf_set_camera with hysteresis for a flight of frames on the lattice fit:
+ * cascade k keeps the ladder step of prev_slot's cascade k (the previous
+ * frame; prev_slot may equal view_slot) when that step is exactly one above
+ * the smallest that fits -- still covering the box, with texels up to one
+ * ladder step coarser -- so that the texel size changes only when it must
+ * and hf_discretize_reuse finds more texels to carry over.  Cameras with
+ * another texel_ladder, or the stable fit, are fitted as by hf_set_camera.
+ * HF_ERR_STATE if prev_slot has no camera. */
+int hf_set_camera_follow(hf_ctx* ctx, int32_t view_slot, const hf_camera* cam, void* dev_view,
+                         size_t bytes, int32_t prev_slot);
+
 /* Step 1 (Section 3 mask, Section 4 Eq. 2): computes the visible-texel rows
  * of every cascade and evaluates the RBF approximation at every visible
  * texel; invisible texels are set to -infinity.  With the water layer the

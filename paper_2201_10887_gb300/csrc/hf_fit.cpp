@@ -140,7 +140,7 @@ double ladder_texel(double c_min, int64_t m, int n) { return c_min * std::exp2(d
 }  // namespace
 
 int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomain& dom,
-                 FitResult* out) {
+                 FitResult* out, const int64_t* follow) {
     std::memset(out, 0, sizeof(*out));
     const int C = cam.n_cascades, N = cam.cascade_size;
     // camera basis: forward, up made orthogonal to it, right = forward x up
@@ -283,6 +283,9 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
                     while (m > m_lo && ladder_texel(cm, m - 1, n) >= need) --m;
                     while (ladder_texel(cm, m, n) < need) ++m;
                 }
+                // hysteresis: an earlier frame's step one coarser still fits,
+                // and keeping it keeps that frame's texels on this lattice
+                if (follow && follow[k] == m + 1) m = follow[k];
             }
             const double h = ladder_texel(cm, m, n);
             c.snap_k = m;

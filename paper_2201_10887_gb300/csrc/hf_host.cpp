@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <string>
 #include <thread>
@@ -661,8 +662,10 @@ int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* st
     return HF_OK;
 }
 
-int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes) {
-    ApiRange range_("hf_set_camera");
+namespace {
+
+int set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes,
+               const int64_t* follow) {
     if (!ctx || !cam || !dev_view) return fail(HF_ERR_ARG, "null argument");
     if (slot < 0 || slot >= HF_MAX_VIEWS) return fail(HF_ERR_ARG, "view slot %d out of range", slot);
     const hf_camera& c = *cam;
@@ -678,7 +681,7 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
     v.eye_local[1] = c.eye[1] - ctx->desc.origin_y;
     v.eye_local[2] = c.eye[2];
     FitDomain dom{ctx->width, ctx->height, ctx->zmin, ctx->zmax, ctx->c_min};
-    int rc = fit_cascades(c, v.eye_local, dom, &v.fit);
+    int rc = fit_cascades(c, v.eye_local, dom, &v.fit, follow);
     if (rc) return fail(rc, "cascade fit produced an oversized polygon");
     v.dev = static_cast<char*>(dev_view);
     v.bytes = bytes;
@@ -704,6 +707,28 @@ int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_vie
     }
     v.stage = 1;
     return HF_OK;
+}
+
+}  // namespace
+
+int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes) {
+    ApiRange range_("hf_set_camera");
+    return set_camera(ctx, slot, cam, dev_view, bytes, nullptr);
+}
+
+int hf_set_camera_follow(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes,
+                         int32_t prev_slot) {
+    ApiRange range_("hf_set_camera_follow");
+    if (!ctx || !cam) return fail(HF_ERR_ARG, "null argument");
+    const ViewSlot* p = get_view(ctx, prev_slot);
+    if (!p || p->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera to follow", prev_slot);
+    int64_t follow[HF_MAX_CASCADES];
+    for (int k = 0; k < HF_MAX_CASCADES; ++k)  // no step to keep: never one above the fitted one
+        follow[k] = std::numeric_limits<int64_t>::min();
+    if (p->cam.texel_ladder == cam->texel_ladder && cam->texel_ladder > 0)
+        for (int k = 0; k < p->cam.n_cascades; ++k)
+            if (p->fit.cas[k].n_poly >= 3) follow[k] = p->fit.cas[k].snap_k;
+    return set_camera(ctx, slot, cam, dev_view, bytes, follow);
 }
 
 namespace {

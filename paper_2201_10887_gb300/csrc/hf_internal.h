@@ -282,8 +282,10 @@ struct FitResult {
     double hull[64][2];
     hf_cascade_info cas[HF_MAX_CASCADES];
 };
-// eye_local: eye relative to the domain origin (FP64).
+// eye_local: eye relative to the domain origin (FP64).  follow: with the
+// lattice fit, cascade k keeps ladder step follow[k] when it is one step
+// coarser than the smallest that fits (hysteresis); nullptr = none.
 int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomain& dom,
-                 FitResult* out);
+                 FitResult* out, const int64_t* follow = nullptr);
 
 }  // namespace hfi

@@ -30,7 +30,7 @@ EXPORTED = ["hf_create_quadtree", "hf_query_bytes", "hf_bind_persistent", "hf_up
             "hf_get_cascade", "hf_view_stats", "hf_sync", "hf_destroy", "hf_last_error",
             "hf_discretize_noalloc", "hf_ray_stats", "hf_batch_query_bytes", "hf_batch_prepare",
             "hf_batch_launch", "hf_frame_batch", "hf_update_water", "hf_selftest_wait_timeout",
-            "hf_measure_unit_rates"]
+            "hf_measure_unit_rates", "hf_set_camera_follow"]
 HF_BATCH_RAYS_INSIDE, HF_BATCH_RAY_TILE_32x8, HF_BATCH_RAY_TILE_8x32, HF_BATCH_WARP_16x2 = 1, 2, 4, 8
 HF_BATCH_PERSISTENT = 16
 HF_NOALLOC_SCRATCH_BYTES = 256 * 1024
@@ -108,6 +108,7 @@ def _load():
         "hf_update_water": [vp, vp, i64, vp],
         "hf_selftest_wait_timeout": [vp, i32, vp],
         "hf_set_camera": [vp, i32, P(hf_camera), vp, sz],
+        "hf_set_camera_follow": [vp, i32, P(hf_camera), vp, sz, i32],
         "hf_discretize_cascades": [vp, i32, vp],
         "hf_discretize_reuse": [vp, i32, i32, vp],
         "hf_build_maxmip": [vp, i32, vp],
@@ -206,6 +207,11 @@ def hf_selftest_wait_timeout(ctx, polls: int = 1000, stream=None):
 def hf_set_camera(ctx, slot: int, cam: hf_camera, view_buf):
     _check(_lib.hf_set_camera(ctx, slot, ct.byref(cam), _dptr(view_buf),
                               view_buf.numel() * view_buf.element_size()))
+
+
+def hf_set_camera_follow(ctx, slot: int, cam: hf_camera, view_buf, prev_slot: int):
+    _check(_lib.hf_set_camera_follow(ctx, slot, ct.byref(cam), _dptr(view_buf),
+                                     view_buf.numel() * view_buf.element_size(), prev_slot))
 
 
 def hf_discretize_cascades(ctx, slot: int, stream=None):

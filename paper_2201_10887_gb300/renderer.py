@@ -77,7 +77,7 @@ class Renderer:
         v["C"] = cam.n_cascades
         return v
 
-    def bind_view(self, slot: int, cam, view_buf, t_out, hit_out):
+    def bind_view(self, slot: int, cam, view_buf, t_out, hit_out, follow: int = None):
         """Use caller-provided buffers for a view slot (uint8 view buffer of
         at least view_bytes(), float32 t and uint8 hit of width*height; t and
         hit may be pinned host tensors, which the ray cast then writes
@@ -88,13 +88,21 @@ class Renderer:
             raise ValueError("view buffers too small")
         self.views[slot] = {"buf": view_buf, "t": t_out, "hit": hit_out, "npx": npx,
                             "shape": (cam.height, cam.width), "C": cam.n_cascades, "external": True}
-        hf.hf_set_camera(self.ctx, slot, camera_struct(cam), view_buf)
+        self._fit(slot, cam, view_buf, follow)
         return self.views[slot]
 
+    def _fit(self, slot, cam, buf, follow):
+        if follow is None:
+            hf.hf_set_camera(self.ctx, slot, camera_struct(cam), buf)
+        else:
+            hf.hf_set_camera_follow(self.ctx, slot, camera_struct(cam), buf, follow)
+
     # -- per-frame steps ------------------------------------------------------
-    def set_camera(self, cam, slot: int = 0):
+    def set_camera(self, cam, slot: int = 0, follow: int = None):
+        """Fit `cam` to a view slot; with `follow` (the slot of the previous
+        frame) the lattice fit keeps that frame's texel sizes where it can."""
         v = self._slot_buffers(slot, cam)
-        hf.hf_set_camera(self.ctx, slot, camera_struct(cam), v["buf"])
+        self._fit(slot, cam, v["buf"], follow)
         return v
 
     def discretize(self, slot: int = 0, stream=None, reuse_from: int = None):
@@ -113,9 +121,11 @@ class Renderer:
         hf.hf_raycast(self.ctx, slot, v["t"], v["hit"], stream)
         return v["t"].view(v["shape"]), v["hit"].view(v["shape"])
 
-    def render(self, cam=None, slot: int = 0, stream=None, reuse_from: int = None):
+    def render(self, cam=None, slot: int = 0, stream=None, reuse_from: int = None, follow: int = None):
+        """One frame; `reuse_from` carries texels over from another slot's
+        earlier frame, `follow` fits with hysteresis against a slot's camera."""
         if cam is not None:
-            self.set_camera(cam, slot)
+            self.set_camera(cam, slot, follow)
         self.discretize(slot, stream, reuse_from)
         self.build_maxmip(slot, stream)
         return self.raycast(slot, stream)

@@ -69,9 +69,12 @@ def _expected_reuse(r, slot, prev_slot, c):
     return n
 
 
-def _run_flight(torch_cuda, scene, cams, water_depth=None, precision=0, check_rays=True, kernel=0):
+def _run_flight(torch_cuda, scene, cams, water_depth=None, precision=0, check_rays=True, kernel=0,
+                follow=False):
     """Frames k in slots k % 2, each reusing the other slot; every frame is
-    also discretized afresh in slot 2.  Returns the carried-over fraction."""
+    also discretized afresh in slot 2 (with `follow`, both fitted with
+    hysteresis against the previous frame's slot).  Returns the carried-over
+    fraction."""
     from paper_2201_10887_gb300 import Renderer
     r = Renderer(scene.tree, scene.sigma, scene.radius, precision=precision, water=water_depth is not None,
                  kernel=kernel)
@@ -80,8 +83,9 @@ def _run_flight(torch_cuda, scene, cams, water_depth=None, precision=0, check_ra
     reused = visible = 0
     for k, cam in enumerate(cams):
         slot, prev = k % 2, (k + 1) % 2
-        t, hit = r.render(cam, slot=slot, reuse_from=prev if k else None)
-        t2, hit2 = r.render(cam, slot=2)
+        fol = prev if (k and follow) else None
+        t2, hit2 = r.render(cam, slot=2, follow=fol)
+        t, hit = r.render(cam, slot=slot, reuse_from=prev if k else None, follow=fol)
         r.sync()
         st = r.stats(slot)
         for c in range(cam.n_cascades):
@@ -154,6 +158,20 @@ def test_reuse_fp16(torch_cuda, tiny):
     from paper_2201_10887_gb300 import hf
     cams = _flight(tiny.cameras[0], 4, ladder=4, n_cascades=2, cascade_size=160)
     assert _run_flight(torch_cuda, tiny, cams, precision=hf.HF_PREC_FP16) > 0.5
+
+
+def test_reuse_with_fit_hysteresis(torch_cuda, tiny):
+    """A camera climbing and sinking every frame: fits that follow the
+    previous frame keep its texel sizes where one ladder step allows, frames
+    still equal fresh ones fitted the same way, and at least as many texels
+    carry over as without hysteresis."""
+    base = tiny.cameras[0]
+    cams = []
+    for k, c in enumerate(_flight(base, 8, step=(6.0, 4.0), yaw_deg=0.5, ladder=8, n_cascades=3, cascade_size=160)):
+        cams.append(c.with_(eye=(c.eye[0], c.eye[1], c.eye[2] + (25.0 if k % 2 else -25.0))))
+    plain = _run_flight(torch_cuda, tiny, cams)
+    held = _run_flight(torch_cuda, tiny, cams, follow=True)
+    assert held >= plain and held > 0.3, (plain, held)
 
 
 def test_reuse_rules(torch_cuda, tiny):

@@ -279,3 +279,40 @@ def test_arena_first_fit_and_merge():
     a.release(x, 1000)
     a.release(1024, 2000)
     assert a.free == [(0, 10_000)] and a.used() == 0
+
+
+def test_fit_follow_against_oracle(hfmod, orc, tiny):
+    """hf_set_camera_follow against the oracle's fit with the same earlier
+    ladder steps, over pairs of nearby random cameras; a slot without a
+    camera cannot be followed."""
+    import math
+    from paper_2201_10887_gb300.renderer import camera_struct
+    rng = np.random.default_rng(5)
+    ctx = _tiny_ctx(hfmod, tiny)
+    cells = orc.Cells(tiny.tree)
+    lib = hfmod.lib()
+    kept = 0
+    for trial in range(120):
+        yaw, pitch = rng.uniform(0, 2 * math.pi), rng.uniform(-1.2, -0.2)
+        fwd = (math.cos(pitch) * math.cos(yaw), math.cos(pitch) * math.sin(yaw), math.sin(pitch))
+        eye = (tiny.tree.origin_x + rng.uniform(0, 640), tiny.tree.origin_y + rng.uniform(0, 640),
+               rng.uniform(200, 900))
+        a = tiny.cameras[0].with_(eye=eye, forward=fwd, n_cascades=int(rng.integers(1, 5)),
+                                  cascade_size=int(rng.integers(16, 400)), texel_ladder=int(rng.integers(1, 6)))
+        b = a.with_(eye=(eye[0] + rng.normal(0, 20), eye[1] + rng.normal(0, 20), eye[2] * rng.uniform(0.8, 1.25)))
+        assert _set_camera_fake(hfmod, ctx, a, a.n_cascades, a.cascade_size) == 0
+        infos = [hfmod.hf_get_cascade(ctx, 0, c) for c in range(a.n_cascades)]
+        steps = [i.snap_k if i.n_poly else 10 ** 9 for i in infos]  # an empty cascade is not followed
+        need = hfmod.hf_query_bytes(ctx, b.n_cascades, b.cascade_size)[1]
+        assert lib.hf_set_camera_follow(ctx, 1, ct.byref(camera_struct(b)), ct.c_void_p(1 << 30),
+                                        ct.c_size_t(need), 0) == 0
+        ob = orc.fit(b, tiny.tree, cells, follow=steps)
+        plain = orc.fit(b, tiny.tree, cells)
+        for c in range(b.n_cascades):
+            li = hfmod.hf_get_cascade(ctx, 1, c)
+            assert (li.snap_x, li.snap_y, li.snap_k) == (ob.cas[c].snap_x, ob.cas[c].snap_y, ob.cas[c].snap_k), (trial, c)
+            kept += int(ob.cas[c].n_poly > 0 and ob.cas[c].snap_k != plain.cas[c].snap_k)
+    assert kept > 0
+    assert lib.hf_set_camera_follow(ctx, 2, ct.byref(camera_struct(a)), ct.c_void_p(1 << 30),
+                                    ct.c_size_t(1 << 30), 7) == hfmod.HF_ERR_STATE
+    hfmod.hf_destroy(ctx)

@@ -601,6 +601,35 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
                         vis += sum(st["visible_texels"])
                 r.sync()
                 res[mode]["reused_fraction"] = reused / max(vis, 1)
+        # throughput: frames alternate between two streams; frame k's
+        # discretization waits for frame k-1's (whose texels it reads), so
+        # frame k-1's max mip and ray cast overlap it (no L2 flush here)
+        cams_m = [c.with_(texel_ladder=ladder) for c in seq]
+        sts = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done = None
+        for k, cam in enumerate(cams_m):
+            if k == warmup:
+                for st in sts:
+                    stream.wait_stream(st)
+                p0.record(stream)
+                for st in sts:
+                    st.wait_stream(stream)
+            slot = k % 2
+            st = sts[slot]
+            if done is not None:
+                st.wait_event(done)
+            r.set_camera(cam, slot, follow=1 - slot if k else None)
+            r.discretize(slot, st, reuse_from=1 - slot if k else None)
+            done = torch.cuda.Event()
+            done.record(st)
+            r.build_maxmip(slot, st)
+            r.raycast(slot, st)
+        for st in sts:
+            stream.wait_stream(st)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        res["lattice_follow_reuse_two_in_flight_ms"] = p0.elapsed_time(p1) / n
         res["frames"] = n
         out[f"flight_{n_frames}_frames"] = res
     r.close()

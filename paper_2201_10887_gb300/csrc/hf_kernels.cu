@@ -404,27 +404,35 @@ __device__ __forceinline__ int64_t prev_index(const DiscCascade& q, int i, int j
 // (terrain and depths live on the same cells, Section 2): the water surface
 // texel is v + sum w_i d_i / sum w_i where that depth is positive, else -inf.
 
-template <bool COH, bool WATER = false, int KERNEL = HF_RBF_GAUSSIAN>
-__device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, const LookupTables& lt,
-                                                 const ListsView& lv, DevStatus* status, int i, int j) {
-    if (i >= q.N || j >= q.N) return;
+// Writes texel (i, j) if it is invisible (-inf) or carried over from an
+// earlier frame and returns true; false: the texel must be computed.
+template <bool COH, bool WATER>
+__device__ __forceinline__ bool texel_settled(const DiscCascade& q, int i, int j) {
     const int2 sp = ldc<COH>(q.spans + j);
     const size_t o = size_t(j) * q.N + i;
-    float* out = q.tex + o;
     if (i < sp.x || i > sp.y) {
-        *out = -INFINITY;
+        q.tex[o] = -INFINITY;
         if (WATER) q.wtex[o] = -INFINITY;
-        return;
+        return true;
     }
     const int64_t po = prev_index(q, i, j);
     if (po >= 0) {
         const float old = ldc<COH>(q.prev + po);
         if (old != -INFINITY) {
-            *out = old;
+            q.tex[o] = old;
             if (WATER) q.wtex[o] = ldc<COH>(q.prev_w + po);
-            return;
+            return true;
         }
     }
+    return false;
+}
+
+// Eq. 2 at visible texel (i, j), walking its bucket's list in global memory.
+template <bool COH, bool WATER, int KERNEL>
+__device__ __forceinline__ void texel_rbf(const DiscCascade& q, float K, const LookupTables& lt,
+                                          const ListsView& lv, DevStatus* status, int i, int j) {
+    const size_t o = size_t(j) * q.N + i;
+    float* out = q.tex + o;
     const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
     const int64_t bucket = lookup_bucket(lt, px, py);
     if (bucket < 0) {
@@ -450,6 +458,14 @@ __device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, 
     const float v = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
     *out = v;
     if (WATER) q.wtex[o] = swd > 0.f ? v + swd / sw : -INFINITY;
+}
+
+template <bool COH, bool WATER = false, int KERNEL = HF_RBF_GAUSSIAN>
+__device__ __forceinline__ void discretize_texel(const DiscCascade& q, float K, const LookupTables& lt,
+                                                 const ListsView& lv, DevStatus* status, int i, int j) {
+    if (i >= q.N || j >= q.N) return;
+    if (texel_settled<COH, WATER>(q, i, j)) return;
+    texel_rbf<COH, WATER, KERNEL>(q, K, lt, lv, status, i, j);
 }
 
 // texel of thread t (0..255) in a 32 x 8 tile: warp = 8 x 4 patch

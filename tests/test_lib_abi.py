@@ -313,6 +313,7 @@ def test_fit_follow_against_oracle(hfmod, orc, tiny):
             assert (li.snap_x, li.snap_y, li.snap_k) == (ob.cas[c].snap_x, ob.cas[c].snap_y, ob.cas[c].snap_k), (trial, c)
             kept += int(ob.cas[c].n_poly > 0 and ob.cas[c].snap_k != plain.cas[c].snap_k)
     assert kept > 0
-    assert lib.hf_set_camera_follow(ctx, 2, ct.byref(camera_struct(a)), ct.c_void_p(1 << 30),
-                                    ct.c_size_t(1 << 30), 7) == hfmod.HF_ERR_STATE
+    for bad_prev in (7, -1, 999):
+        assert lib.hf_set_camera_follow(ctx, 2, ct.byref(camera_struct(a)), ct.c_void_p(1 << 30),
+                                        ct.c_size_t(1 << 30), bad_prev) == hfmod.HF_ERR_STATE
     hfmod.hf_destroy(ctx)

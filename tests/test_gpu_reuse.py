@@ -154,6 +154,27 @@ def test_reuse_long_jumps_and_wendland(torch_cuda, tiny):
     _run_flight(torch_cuda, tiny, _flight(tiny.cameras[0], 3, ladder=2, n_cascades=2, cascade_size=128), kernel=1)
 
 
+def test_reuse_after_water_update(torch_cuda):
+    """New water depths invalidate the earlier frame's texels as new terrain
+    values do: nothing carries over, and the frame equals a fresh one."""
+    import workloads
+    from paper_2201_10887_gb300 import Renderer
+    s = workloads.tiny_flood_config()
+    cams = _flight(s.cameras[0], 2, ladder=4, n_cascades=2, cascade_size=128)
+    r = Renderer(s.tree, s.sigma, s.radius, water=True)
+    r.update_water(s.depth)
+    r.render(cams[0], slot=0)
+    r.update_water((s.depth * 1.5).astype(np.float32))
+    r.render(cams[1], slot=1, reuse_from=0)
+    r.render(cams[1], slot=2)
+    r.sync()
+    for c in range(2):
+        assert r.cascade(1, c).reuse_source == -1
+        assert torch_cuda.equal(_bits(r.texture(1, c)), _bits(r.texture(2, c)))
+        assert torch_cuda.equal(_bits(r.water_texture(1, c)), _bits(r.water_texture(2, c)))
+    r.close()
+
+
 def test_reuse_fp16(torch_cuda, tiny):
     from paper_2201_10887_gb300 import hf
     cams = _flight(tiny.cameras[0], 4, ladder=4, n_cascades=2, cascade_size=160)

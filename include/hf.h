@@ -91,7 +91,7 @@ typedef struct {
  * square "bucket": every leaf at or below level bucket_level is a bucket,
  * coarser leaves are split into their level-bucket_level descendants so a
  * list never covers more than one level-bucket_level cell.  bucket_level
- * = -1 selects max(0, max_level - 2).
+ * = -1 selects max(0, max_level - 1).
  * kernel selects the weight function of Eq. 2: HF_RBF_GAUSSIAN is Eq. 1;
  * HF_RBF_WENDLAND_C2 is Wendland's compactly supported C2 function
  * (1 - r)^4 (4 r + 1) of r = |p_i - p| / (radius c_i), zero for r >= 1 (sigma

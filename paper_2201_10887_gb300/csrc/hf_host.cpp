@@ -418,7 +418,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
     ctx->desc = d;
     ctx->rbf = *rbf;
     ctx->M = M;
-    ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 2) : rbf->bucket_level;
+    ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 1) : rbf->bucket_level;
     ctx->n_leaves = n_leaves;
     ctx->c_fin = d.root_cell / double(int64_t(1) << M);
     ctx->width = d.root_cell * d.root_nx;

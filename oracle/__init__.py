@@ -69,7 +69,8 @@ class ViewC(ct.Structure):
 
 class RCascade(ct.Structure):
     _fields_ = [("ox", ct.c_double), ("oy", ct.c_double), ("h", ct.c_double),
-                ("near", ct.c_double), ("far_ext", ct.c_double), ("N", ct.c_int)]
+                ("near", ct.c_double), ("far_ext", ct.c_double), ("N", ct.c_int),
+                ("stop_level", ct.c_int)]
 
 
 _lib = None
@@ -87,6 +88,8 @@ def lib():
         _lib.orc_ray_patch.argtypes = [d] * 11 + [P(d)]
         _lib.orc_fit.restype = i
         _lib.orc_fit.argtypes = [P(CameraC), P(Domain), P(ViewC)]
+        _lib.orc_stop_level.restype = i
+        _lib.orc_stop_level.argtypes = [d, d, i, d, d, i]
         _lib.orc_fit_follow.restype = i
         _lib.orc_fit_follow.argtypes = [P(CameraC), P(Domain), P(ct.c_longlong), P(ViewC)]
         _lib.orc_ladder_fit.restype = None
@@ -261,11 +264,17 @@ def ray_patch(h00, h10, h01, h11, a0, b0, z0, da, db, dz, dt):
 
 
 def rcascades(cascades) -> "ct.Array":
-    """Ray-casting descriptors from objects with ox, oy, h, near, far_ext, N."""
+    """Ray-casting descriptors from objects with ox, oy, h, near, far_ext, N
+    and optionally stop_level (coarse-level stop; 0 = the bilinear surface)."""
     arr = (RCascade * len(cascades))()
     for k, c in enumerate(cascades):
-        arr[k] = RCascade(c.ox, c.oy, c.h, c.near, c.far_ext, c.N)
+        arr[k] = RCascade(c.ox, c.oy, c.h, c.near, c.far_ext, c.N, int(getattr(c, "stop_level", 0)))
     return arr
+
+
+def stop_level(lod_pixels: float, vfov: float, height: int, near: float, h: float, N: int) -> int:
+    """Coarse-level stop level of a cascade (orc_stop_level)."""
+    return lib().orc_stop_level(lod_pixels, vfov, height, near, h, N)
 
 
 def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0, water_textures=None):
@@ -278,6 +287,10 @@ def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0, water
     C = len(cascades)
     rc = rcascades(cascades)
     texs = [np.ascontiguousarray(t, np.float32) for t in textures]
+    if mips is None and any(rc[k].stop_level > 0 for k in range(C)):
+        if water_textures is not None:
+            raise ValueError("the coarse-level stop is defined for the terrain alone")
+        mips = [maxmip(t) for t in texs]  # the box field of a coarse-level stop
     tp = (ct.POINTER(ct.c_float) * C)(*[_p(t, ct.c_float) for t in texs])
     if water_textures is not None:
         if mode != 0:

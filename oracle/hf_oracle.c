@@ -10,6 +10,7 @@
  *   Section 3 (visible-texel mask) ............ orc_mask
  *   Section 5 (maximum mipmap, Tevs et al.) ... orc_maxmip
  *   Section 5 (ray casting, bilinear patches) . orc_ray_patch, orc_raycast
+ *   coarse-level stop (extension) ............. orc_stop_level, trace_boxes
  * Where the paper leaves a detail open, the reading taken is stated at the
  * function and is the same one the product library follows.
  */
@@ -682,6 +683,56 @@ static double exit_time(double e, double d, double lo, double hi) {
     return INFINITY;
 }
 
+/* Coarse-level stop (an extension after the LOD-dependent early ray
+ * termination the paper cites): far from the eye a node of the max mipmap
+ * smaller than a few pixels can stand in for the surface under it.  Stop
+ * level of a cascade: the largest k with 2^k h <= lod_pixels times the pixel
+ * pitch at the cascade's near depth, 2 tan(vfov / 2) / height * near (the
+ * footprint only grows beyond it), capped at the mipmap's top level.       */
+int orc_stop_level(double lod, double vfov, int height, double near_, double h, int N) {
+    if (!(lod > 0.0) || !(near_ > 0.0)) return 0;
+    double reach = lod * (2.0 * tan(0.5 * vfov) / (double)height) * near_;
+    int P = mip_P(N), K = 0;
+    while ((1 << K) < P) K++;
+    int L = 0;
+    while (L < K && ldexp(h, L + 1) <= reach * (1.0 + 1e-9)) L++;
+    return L;
+}
+
+/* First hit of the level-L box field: the ray walks the level-L nodes of the
+ * max mipmap in order (a 2-D DDA on cells of 2^L patches) and stops in the
+ * first node whose maximum it reaches -- at the node's entry if it enters
+ * below the box top, else where it comes down to it.                      */
+static int trace_boxes(const float* mip, int N, int L, const prj_ray* r, double ta, double tb,
+                       double* t_hit, long long* visits) {
+    int P = mip_P(N), PL = P >> L;
+    long off = 0;
+    for (int k = 0; k < L; ++k) off += (long)(P >> k) * (P >> k);
+    double s = ldexp(1.0, L);
+    int ni = clampi((int)floor((r->eu + ta * r->du) / s), 0, PL - 1);
+    int nj = clampi((int)floor((r->ev + ta * r->dv) / s), 0, PL - 1);
+    double t = ta;
+    for (long guard = 0; guard < 4L * (PL + 2); ++guard) {
+        double tx = exit_time(r->eu, r->du, ni * s, (ni + 1) * s);
+        double ty = exit_time(r->ev, r->dv, nj * s, (nj + 1) * s);
+        double te = fmin(fmin(tx, ty), tb);
+        if (te < t) te = t;
+        (*visits)++;
+        double M = (double)mip[off + (long)nj * PL + ni];
+        double z0 = r->ez + t * r->dz, z1 = r->ez + te * r->dz;
+        if (fmin(z0, z1) <= M) {
+            *t_hit = z0 <= M ? t : t + (M - z0) / r->dz;
+            return 1;
+        }
+        if (te >= tb) return 0;
+        if (tx <= ty) ni += r->du > 0.0 ? 1 : -1;
+        else nj += r->dv > 0.0 ? 1 : -1;
+        if (ni < 0 || nj < 0 || ni >= PL || nj >= PL) return 0;
+        t = te;
+    }
+    return 0;
+}
+
 /* First hit by walking every patch the ray crosses (2-D DDA).             */
 static int trace_dda(const float* tex, int N, const prj_ray* r, double ta, double tb,
                      double* t_hit, long long* visits) {
@@ -792,12 +843,13 @@ static int cascade_interval(const orc_rcascade* c, const prj_ray* r, double ks, 
  * water surface on a tie; *on_water says which.  A water patch exists where
  * its four corners are wet (finite), as a terrain patch needs four visible
  * corners.                                                                 */
-static int trace_cascade(const float* tex, const float* wtex, const float* mip, int N,
+static int trace_cascade(const float* tex, const float* wtex, const float* mip, int N, int stop,
                          const prj_ray* r, double ta, double tb, int mode, double* t_hit,
                          int* on_water, long long* visits) {
     double t1 = 0.0, t2 = 0.0;
-    int h1 = mode == 0 ? trace_dda(tex, N, r, ta, tb, &t1, visits)
-                       : trace_mip(tex, mip, N, r, ta, tb, &t1, visits);
+    int h1 = stop > 0 ? trace_boxes(mip, N, stop, r, ta, tb, &t1, visits)
+             : mode == 0 ? trace_dda(tex, N, r, ta, tb, &t1, visits)
+                         : trace_mip(tex, mip, N, r, ta, tb, &t1, visits);
     int h2 = wtex ? trace_dda(wtex, N, r, ta, tb, &t2, visits) : 0;
     *on_water = h2 && (!h1 || t2 <= t1);
     if (*on_water) {
@@ -842,8 +894,8 @@ void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
             double ta, tb, tc;
             int wet = 0;
             if (!cascade_interval(&cas[c], &r, ks, tmin, tmax, &ta, &tb)) continue;
-            if (!trace_cascade(tex[c], wtex ? wtex[c] : NULL, mip ? mip[c] : NULL, cas[c].N, &r, ta, tb,
-                               mode, &tc, &wet, &visits))
+            if (!trace_cascade(tex[c], wtex ? wtex[c] : NULL, mip ? mip[c] : NULL, cas[c].N, cas[c].stop_level,
+                               &r, ta, tb, mode, &tc, &wet, &visits))
                 continue;
             hit = (1 + c) | (wet ? 0x80 : 0);
             t = tc;
@@ -857,7 +909,7 @@ void orc_raycast(const orc_camera* cam, const orc_rcascade* cas, int C,
                 int wet2 = 0;
                 if (cascade_interval(n2, &r2, ks, tmin, tmax, &ta2, &tb2)) {
                     int h2 = trace_cascade(tex[c + 1], wtex ? wtex[c + 1] : NULL, mip ? mip[c + 1] : NULL,
-                                           n2->N, &r2, ta2, tb2, mode, &t2, &wet2, &visits);
+                                           n2->N, n2->stop_level, &r2, ta2, tb2, mode, &t2, &wet2, &visits);
                     if (h2) {
                         double al = (s - n2->near_) / (cas[c].far_ext - n2->near_);
                         al = al < 0.0 ? 0.0 : (al > 1.0 ? 1.0 : al);

@@ -65,11 +65,14 @@ typedef struct {
     orc_cascade cas[ORC_MAX_CASCADES];
 } orc_view;
 
-/* Cascade used by the ray caster: only what rendering needs. */
+/* Cascade used by the ray caster: only what rendering needs.  stop_level
+ * 0 is the bilinear surface (Section 5); L >= 1 is the coarse-level stop: the
+ * level-L box field of the max mipmap (orc_stop_level). */
 typedef struct {
     double ox, oy, h;
     double near_, far_ext;
     int N;
+    int stop_level;
 } orc_rcascade;
 
 /* ---- Eq. 1 / Eq. 2 ---- */
@@ -107,6 +110,10 @@ void orc_texel_heights(const orc_cascade* cas, const orc_domain* dom, const doub
                        double* out);
 
 /* ---- Section 5: maximum mipmap and ray casting ---- */
+/* coarse-level stop of a cascade: the largest level k (0..K of its max mipmap)
+ * whose nodes, 2^k h wide, span at most lod_pixels pixels at the cascade's near
+ * depth; 0 when lod_pixels <= 0 or near <= 0 */
+int orc_stop_level(double lod_pixels, double vfov, int height, double near_, double h, int N);
 long orc_maxmip_size(int N);
 void orc_maxmip(const float* tex, int N, float* mip);
 /* first root of bilinear(a,b) - z along a ray segment inside one patch */

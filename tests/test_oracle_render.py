@@ -324,3 +324,86 @@ def test_blend_closed_form(orc, tiny):
     assert np.max(np.abs(t[band] - expect[band])) < 1e-9 * t2.max()
     assert np.max(np.abs(t[early] - t1[early])) < 1e-9 * t1.max()
     assert np.ptp(a[band]) > 0.5                  # the band is crossed, not touched
+
+
+# ---- coarse-level stop (extension: the level-L box field of the max mipmap) ----
+
+def test_stop_level_worked_example(orc):
+    """60 deg vertical field of view over 1080 rows: a pixel spans
+    2 tan(30 deg) / 1080 = 1.0692e-3 of the distance, so 2 pixels at 1 km are
+    2.138 m.  Nodes of 0.5 m texels: 2^2 * 0.5 = 2 m fits, 4 m does not -> 2;
+    3 m texels: even level 0 is too wide -> 0.  No stop without a positive
+    distance or pixel count; capped at the top level (N = 33: P = 32, K = 5)."""
+    v = math.radians(60.0)
+    assert orc.stop_level(2.0, v, 1080, 1000.0, 0.5, 2048) == 2
+    assert orc.stop_level(2.0, v, 1080, 1000.0, 3.0, 2048) == 0
+    assert orc.stop_level(0.0, v, 1080, 1000.0, 0.5, 2048) == 0
+    assert orc.stop_level(2.0, v, 1080, -5.0, 0.5, 2048) == 0
+    assert orc.stop_level(1e6, v, 1080, 1000.0, 0.5, 33) == 5
+
+
+def _box_height(mip, N, L, u, v):
+    """Height of the level-L box field at texel coordinates (u, v)."""
+    P = 1
+    while P < N - 1:
+        P <<= 1
+    off = sum((P >> k) ** 2 for k in range(L))
+    PL = P >> L
+    ni = np.clip(np.floor(u / (1 << L)).astype(int), 0, PL - 1)
+    nj = np.clip(np.floor(v / (1 << L)).astype(int), 0, PL - 1)
+    ok = (u >= 0) & (u <= N - 1) & (v >= 0) & (v <= N - 1)
+    return np.where(ok, mip[off + nj * PL + ni].astype(np.float64), -np.inf)
+
+
+@pytest.mark.parametrize("seed,L", [(0, 1), (1, 2), (2, 3)])
+def test_coarse_stop_matches_box_field_marching(orc, tiny, seed, L):
+    """With stop level L the first hit is the first point where the ray comes
+    down to the level-L box field (the max mipmap's level-L entries as flat box
+    tops), found here by dense marching plus bisection; and it never lies
+    beyond the bilinear surface's first hit (the boxes bound the surface)."""
+    N = 33
+    tex, cas = _one_cascade_scene(N, seed)
+    cas.stop_level = L
+    mip = orc.maxmip(tex)
+    eyes = [(32.0, -25.0, 70.0), (-10.0, 30.0, 45.0), (30.0, 30.0, 90.0)]
+    fwds = [(0.1, 1.0, -0.6), (1.0, 0.2, -0.35), (0.2, 0.3, -1.0)]
+    cam = _scene_camera(tiny, eyes[seed], fwds[seed])
+    t, hit, _, _ = orc.raycast(cam, tiny.tree, [cas], [tex])
+    cas.stop_level = 0
+    t0, hit0, _, _ = orc.raycast(cam, tiny.tree, [cas], [tex])
+    py, px = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    eye, d = _look_at_rays(cam, tiny.tree, px.ravel().astype(float), py.ravel().astype(float))
+    fd = d @ (np.array(cam.forward) / np.linalg.norm(cam.forward))
+    ts = np.linspace(0.0, 400.0, 40001)
+    agree = skipped = 0
+    for q in range(d.shape[0]):
+        tt = ts[ts >= cam.znear / fd[q]]
+        P = eye + tt[:, None] * d[q]
+        f = _box_height(mip, N, L, P[:, 0] / cas.h, P[:, 1] / cas.h) - P[:, 2]
+        pos = np.nonzero(f >= 0)[0]
+        if pos.size == 0:
+            fin = np.isfinite(f)
+            if fin.any() and f[fin].max() > -1e-3:
+                skipped += 1
+                continue
+            assert hit[q] == 0
+            agree += 1
+            continue
+        k = pos[0]
+        if k == 0 or not np.isfinite(f[k - 1]):
+            skipped += 1              # starts under the boxes / enters the texture under them
+            continue
+        lo, hi = tt[k - 1], tt[k]
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            Pm = eye + mid * d[q]
+            fm = _box_height(mip, N, L, np.array([Pm[0] / cas.h]), np.array([Pm[1] / cas.h]))[0] - Pm[2]
+            lo, hi = (mid, hi) if fm < 0 else (lo, mid)
+        assert hit[q] == 1, q
+        assert t[q] == pytest.approx(0.5 * (lo + hi), abs=1e-7 * hi + 1e-9), q
+        agree += 1
+    assert agree > 0.97 * d.shape[0] and skipped < 0.03 * d.shape[0]
+    both = (hit > 0) & (hit0 > 0)
+    assert both.sum() > 100 and np.all(hit[hit0 > 0] > 0)
+    assert np.all(t[both] <= t0[both] + 1e-9 * t0[both])
+    assert np.mean(t[both] < t0[both] * (1 - 1e-6)) > 0.3     # the coarse surface is really coarser

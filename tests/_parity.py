@@ -4,7 +4,10 @@ cascade descriptors into oracle inputs, and the comparison rules.
 Tolerances (FP32 path):
   heights   |v_gpu - v_ref| <= 1e-5 * max(|v_ref|, A), A = largest |cell value|
   ray t     |t_gpu - t_ref| <= 1e-4 * (length of the ray segment inside the
-            first-hit cascade)
+            first-hit cascade), or 4 FP32 ulps of t where that is larger: t is
+            an FP32 number, which cannot come closer than half an ulp to the
+            exact hit, so a segment shorter than 2.4e-3 t would ask for more
+            than its precision
   hit/miss  at most 0.1 % of pixels differ, and only at silhouettes: pixels
             whose 3x3 reference neighbourhood mixes hit and miss, or whose
             reference t jumps by more than 5 % inside it
@@ -34,6 +37,7 @@ import numpy as np
 
 HEIGHT_REL = 1e-5
 RAY_REL = 1e-4
+T_ULPS = 4 * 2.0 ** -24   # four FP32 ulps of t, relative
 HIT_MISMATCH = 1e-3
 GRAZE_REL = 2e-6
 
@@ -51,6 +55,7 @@ class RC:
     def __init__(self, info):
         self.ox, self.oy, self.h = info.ox, info.oy, info.texel
         self.near, self.far_ext, self.N = info.near, info.far_ext, info.N
+        self.stop_level = getattr(info, "stop_level", 0)
 
 
 def mask_from_spans(spans: np.ndarray, N: int) -> np.ndarray:
@@ -107,10 +112,16 @@ def surface_bracket(orc, cam, tree, rcs, texs, px, py, delta, water_texs=None):
     return tuple(out)
 
 
+def ray_scale(seg, t):
+    """The length the ray tolerance is relative to: the first-hit cascade's
+    segment, at least T_ULPS * t / RAY_REL (see the module docstring)."""
+    return np.maximum(np.nan_to_num(seg, nan=0.0), T_ULPS / RAY_REL * np.abs(np.nan_to_num(t, nan=0.0)))
+
+
 def bracketed(gt, gh, seg, tu, hu, td, hd):
     """True where the result lies between the raised and the lowered
     surface's answers (within the ray tolerance)."""
-    tol = RAY_REL * np.nan_to_num(seg, nan=0.0)
+    tol = RAY_REL * ray_scale(seg, gt)
     hit_ok = (gh > 0) & (hu > 0) & (gt >= tu - tol) & ((hd == 0) | (gt <= td + tol))
     miss_ok = (gh == 0) & (hd == 0)
     return hit_ok | miss_ok
@@ -159,7 +170,7 @@ def check_rays(gt, gh, ot, oh, seg, shape=None, silhouette=None, bracket=None):
         silhouette = silhouettes(oh.reshape(shape), ot.reshape(shape)).ravel()
     both = (gh > 0) & (oh > 0)
     err = np.zeros(gt.size)
-    err[both] = np.abs(gt[both] - ot[both]) / seg[both]
+    err[both] = np.abs(gt[both] - ot[both]) / ray_scale(seg[both], ot[both])
     explained = np.zeros(gt.size, bool)
     if bracket is not None:
         idx = np.nonzero(mism | (both & (err > RAY_REL)))[0]

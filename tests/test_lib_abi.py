@@ -140,7 +140,8 @@ def test_call_order_and_buffer_checks(hfmod, tiny):
     # no persistent buffer bound yet
     assert lib.hf_discretize_cascades(ctx, 0, None) == hfmod.HF_ERR_STATE
     for bad_cam in (cam.with_(vfov=0.0), cam.with_(texel_ladder=-1), cam.with_(texel_ladder=65),
-                    cam.with_(texel_ladder=2, cascade_size=3)):
+                    cam.with_(texel_ladder=2, cascade_size=3), cam.with_(lod_pixels=-1.0),
+                    cam.with_(lod_pixels=float("nan")), cam.with_(lod_pixels=2e6)):
         bad = camera_struct(bad_cam)
         assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
     bad = camera_struct(cam)
@@ -197,7 +198,7 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
     ctx = _tiny_ctx(hfmod, tiny)
     cells = orc.Cells(tiny.tree)
     W = tiny.tree.width
-    checked = 0
+    checked = stops = 0
     for trial in range(300):
         yaw, pitch = rng.uniform(0, 2 * math.pi), rng.uniform(-1.5, 0.3)
         fwd = (math.cos(pitch) * math.cos(yaw), math.cos(pitch) * math.sin(yaw), math.sin(pitch))
@@ -213,6 +214,8 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
                                     overlap_frac=float(rng.uniform(0, 0.2)))
         if trial % 3 == 0:
             cam = cam.with_(texel_ladder=int(rng.integers(1, 9)), cascade_size=max(cam.cascade_size, 4))
+        if trial % 2 == 0:
+            cam = cam.with_(lod_pixels=float(rng.choice([0.5, 1.0, 2.0, 8.0, 64.0])))
         assert _set_camera_fake(hfmod, ctx, cam, cam.n_cascades, cam.cascade_size) == 0
         ov = orc.fit(cam, tiny.tree, cells)
         for c in range(cam.n_cascades):
@@ -220,6 +223,9 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
             oc = ov.cas[c]
             assert (li.snap_x, li.snap_y, li.snap_k) == (oc.snap_x, oc.snap_y, oc.snap_k), (trial, c)
             assert (li.n_poly == 0) == (oc.n_poly == 0), (trial, c)
+            assert li.stop_level == orc.stop_level(cam.lod_pixels, cam.vfov, cam.height, li.near, li.texel,
+                                                   cam.cascade_size), (trial, c)
+            stops += li.stop_level > 0
             if li.n_poly:
                 lp, op = li.polygon(), oc.polygon()
                 # every vertex of one polygon is a vertex of the other
@@ -227,7 +233,7 @@ def test_fit_fuzz_against_oracle(hfmod, orc, tiny):
                 d2 = np.min(np.linalg.norm(op[:, None] - lp[None], axis=2), axis=1)
                 assert d1.max() < 1e-7 * W and d2.max() < 1e-7 * W, (trial, c)
                 checked += 1
-    assert checked > 300
+    assert checked > 300 and stops > 20
     hfmod.hf_destroy(ctx)
 
 
@@ -261,6 +267,14 @@ def test_water_layer_flags_and_sizes(hfmod, tiny):
     p1, v1 = hfmod.hf_query_bytes(wet, 3, 256)
     assert p1 - p0 >= 4 * t.n_leaves and p1 - p0 < 4 * t.n_leaves + 256
     assert v1 - v0 == 3 * 256 * 256 * 4
+    # the coarse-level stop is defined for the terrain alone
+    from paper_2201_10887_gb300.renderer import camera_struct
+    cam = tiny.cameras[0].with_(lod_pixels=2.0)
+    need = hfmod.hf_query_bytes(wet, cam.n_cascades, cam.cascade_size)[1]
+    assert hfmod.lib().hf_set_camera(wet, 0, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
+                                     ct.c_size_t(need)) == hfmod.HF_ERR_ARG
+    assert hfmod.lib().hf_set_camera(plain, 0, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
+                                     ct.c_size_t(need)) == 0
     for d in (plain, wet):
         hfmod.hf_destroy(d)
     for args in ((0, -1, 2, 0), (1, -1, 1, 0), (2, -1, 1, 0), (0, -1, 0, 7), (1, -1, 0, 1), (2, -1, 0, 1)):

@@ -484,6 +484,8 @@ def run_ours(args, rank, world, local_rank):
             scene, cams, sched[:min(len(sched), 240)], args.warmup, dev, flush, stream,
             variants=(("wendland_c2", {"kernel": 1}),))
         line["temporal_reuse"] = time_temporal_reuse(scene, args.warmup, dev, flush, stream)
+        line["coarse_stop"] = time_coarse_stop(scene, cams, sched[:min(len(sched), 120)], args.warmup, dev,
+                                               flush, stream)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
@@ -632,6 +634,62 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
         res["lattice_follow_reuse_two_in_flight_ms"] = p0.elapsed_time(p1) / n
         res["frames"] = n
         out[f"flight_{n_frames}_frames"] = res
+    r.close()
+    del r
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(1.0, 2.0, 4.0)):
+    """The coarse-level stop (hf_camera.lod_pixels) on the main line's frames:
+    frame and ray-cast time (L2 flushed between frames), node visits per ray,
+    and how far the image moves from the exact surface: the share of hit
+    pixels whose t changed and the mean and 99th percentile of |dt| / t."""
+    import numpy as np
+    import torch
+    from paper_2201_10887_gb300 import Renderer
+    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
+    frames = sorted(set(sched))[:24]
+    exact = {}
+    for f in frames:
+        t, h = r.render(cams[f])
+        exact[f] = (t.cpu().numpy().ravel().copy(), h.cpu().numpy().ravel().copy())
+    out = {}
+    for lod in lods:
+        cl = [c.with_(lod_pixels=lod) for c in cams]
+        for f in sched[:warmup]:
+            r.render(cl[f])
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in sched]
+        for k, f in enumerate(sched):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            r.set_camera(cl[f])
+            r.discretize()
+            r.build_maxmip()
+            ev[k][1].record(stream)
+            r.raycast()
+            ev[k][2].record(stream)
+        torch.cuda.synchronize(dev)
+        changed, rel = [], []
+        visits = 0
+        for f in frames:
+            t, h = r.render(cl[f])
+            t, h = t.cpu().numpy().ravel(), h.cpu().numpy().ravel()
+            t0, h0 = exact[f]
+            both = (h > 0) & (h0 > 0)
+            d = np.abs(t[both] - t0[both]) / t0[both]
+            changed.append(np.mean(d > 1e-6))
+            rel.append(d)
+            visits += r.ray_stats()["visits"]
+        rel = np.concatenate(rel)
+        levels = [r.cascade(0, c).stop_level for c in range(cams[frames[-1]].n_cascades)]
+        out[f"lod_{lod:g}"] = {"frame_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in ev),
+                               "raycast_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in ev),
+                               "visits_per_ray": visits / (len(frames) * cams[0].width * cams[0].height),
+                               "changed_hit_pixels": float(np.mean(changed)),
+                               "mean_rel_dt": float(rel.mean()), "p99_rel_dt": float(np.percentile(rel, 99)),
+                               "stop_levels_last_frame": levels}
+    r.sync()
     r.close()
     del r
     torch.cuda.empty_cache()

@@ -130,7 +130,14 @@ typedef struct {
  * multiple of h_m, so texel (i, j) sits on the lattice point (snap_x + i,
  * snap_y + j) of spacing h_m whatever the camera's position.  The lattice
  * fit needs cascade_size >= 4; its texels are up to 2^(1/n) coarser than
- * the stable fit's.  reserved must be 0. */
+ * the stable fit's.  reserved must be 0.
+ * lod_pixels > 0 turns on the coarse-level stop (after the LOD-dependent early
+ * ray termination the paper cites): in cascade c the ray stops at the box tops
+ * of max-mipmap level L_c instead of descending to the bilinear patches, L_c
+ * being the largest level whose nodes, 2^L texels wide, span at most
+ * lod_pixels pixels (2 tan(vfov / 2) / height of the distance each) at the
+ * cascade's near depth (hf_cascade_info.stop_level).  0 is the paper's exact
+ * surface; not available with the water layer. */
 typedef struct {
     double eye[3];
     double forward[3];
@@ -141,6 +148,7 @@ typedef struct {
     double split_lambda, overlap_frac;
     int32_t texel_ladder;
     int32_t reserved;
+    double lod_pixels;
 } hf_camera;
 
 /* Fitted cascade (Section 3) plus the device buffers bound to it. */
@@ -161,6 +169,8 @@ typedef struct {
     float* water_tex;                            /* device, N*N FP32 water surface, -inf where dry or invisible; NULL without the water layer */
     int32_t texel_ladder;                        /* the camera's texel_ladder (0 = stable fit) */
     int32_t reuse_source;                        /* cascade of the earlier frame the last hf_discretize_reuse copied from, -1 = none */
+    int32_t stop_level;                          /* coarse-level stop (hf_camera.lod_pixels): 0 = exact bilinear surface */
+    int32_t reserved;
 } hf_cascade_info;
 
 typedef struct hf_ctx hf_ctx;

@@ -255,6 +255,8 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
         const double cm = dom.c_min;
         c.texel_ladder = cam.texel_ladder;
         c.reuse_source = -1;
+        c.stop_level = 0;
+        c.reserved = 0;
         double x0 = 0.0, x1 = 0.0, y0 = 0.0, y1 = 0.0;
         if (c.n_poly >= 3) {
             x0 = x1 = poly[0].x;
@@ -316,6 +318,19 @@ int fit_cascades(const hf_camera& cam, const double eye_local[3], const FitDomai
         c.oy = double(c.snap_y) * cm;
         c.extent = 2.0 * double(c.snap_k) * cm;
         c.texel = c.extent / double(N - 1);
+    }
+    // coarse-level stop: per cascade the largest max-mip level whose nodes span
+    // at most lod_pixels pixels at the cascade's near depth
+    const double pitch = 2.0 * std::tan(0.5 * cam.vfov) / double(cam.height);
+    int K = 0;
+    while ((int64_t(1) << K) < int64_t(N) - 1) ++K;
+    for (int k = 0; k < C && cam.lod_pixels > 0.0; ++k) {
+        hf_cascade_info& c = out->cas[k];
+        const double span = cam.lod_pixels * pitch * c.near_depth;
+        if (!(span > 0.0)) continue;
+        int L = 0;
+        while (L < K && c.texel * double(int64_t(2) << L) <= span * (1.0 + 1e-9)) ++L;
+        c.stop_level = L;
     }
     return HF_OK;
 }

@@ -310,6 +310,7 @@ int check_camera(const hf_camera& c) {
     if (c.texel_ladder < 0 || c.texel_ladder > 64) return fail(HF_ERR_ARG, "texel_ladder must be 0..64");
     if (c.texel_ladder > 0 && c.cascade_size < 4) return fail(HF_ERR_ARG, "the lattice fit needs cascade_size >= 4");
     if (c.reserved != 0) return fail(HF_ERR_ARG, "hf_camera.reserved must be 0");
+    if (!(c.lod_pixels >= 0.0 && c.lod_pixels <= 1e6)) return fail(HF_ERR_ARG, "lod_pixels must be in [0, 1e6]");
     return HF_OK;
 }
 
@@ -670,6 +671,8 @@ int set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, 
     if (slot < 0 || slot >= HF_MAX_VIEWS) return fail(HF_ERR_ARG, "view slot %d out of range", slot);
     const hf_camera& c = *cam;
     if (int rc = check_camera(c)) return rc;
+    if (c.lod_pixels > 0.0 && ctx->rbf.water)
+        return fail(HF_ERR_ARG, "the coarse-level stop is not available with the water layer");
     if (reinterpret_cast<uintptr_t>(dev_view) & 255) return fail(HF_ERR_ARG, "view buffer must be 256-byte aligned");
     const size_t need = per_view_bytes(c.n_cascades, c.cascade_size, ctx->rbf.water != 0);
     if (bytes < need) return fail(HF_ERR_NOMEM, "view buffer has %zu bytes, %zu needed", bytes, need);
@@ -944,6 +947,7 @@ RayParams ray_params(const ViewSlot* v, bool water) {
         rc.near_d = float(ci.near_depth);
         rc.far_ext = float(ci.far_ext_depth);
         rc.budget = 8 * (2 * N + 8) * (rc.K + 2);
+        rc.stop_level = std::min(ci.stop_level, rc.K);
         int64_t off = 0;
         for (int L = 0; L < kMaxLevels; ++L) {
             rc.lvl_off[L] = int32_t(off);

@@ -156,6 +156,7 @@ struct RayCascade {
     float h, inv_h;
     float near_d, far_ext;  // projected-depth band
     int32_t budget;         // bound on walk steps: 8 (2 N + 8) (K + 2)
+    int32_t stop_level;     // coarse-level stop: the walk ends at this level's box tops (0 = patches)
     int32_t lvl_off[kMaxLevels];  // first float of mip level k
 };
 

@@ -1044,7 +1044,8 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const float slack = 2e-6f * fabsf(top);
     int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
-    int k = min(K, kRayStartLevel);
+    const int L = c.stop_level;  // coarse-level stop: no node below this level is visited
+    int k = max(min(K, kRayStartLevel), L);
     float t = ta;
     const int budget = c.budget;
     for (int it = 0; it < budget; ++it) {
@@ -1056,9 +1057,15 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
         const float mx = ldc<COH>(mip + off[k] + nj * (P >> k) + ni);
         if (COUNT) ++visits;
         if (zmin <= __fadd_rn(mx, slack)) {
-            if (k > 0) {
+            if (k > L) {
                 --k;
                 continue;
+            }
+            if (k > 0) {  // coarse-level stop: the ray meets this node's box top
+                const float z0 = fmaf(t, r.dz, ez);
+                t_hit = (z0 <= mx || !zneg) ? t : fminf(fmaf(mx - z0, d.rdz, t), te);
+                on_water = false;
+                return true;
             }
             if (ci <= N - 2 && cj <= N - 2) {
                 if (COUNT) ++tests;

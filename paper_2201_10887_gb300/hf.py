@@ -57,7 +57,8 @@ class hf_camera(ct.Structure):
                 ("vfov", ct.c_double), ("znear", ct.c_double), ("zfar", ct.c_double),
                 ("width", ct.c_int32), ("height", ct.c_int32), ("n_cascades", ct.c_int32),
                 ("cascade_size", ct.c_int32), ("split_lambda", ct.c_double),
-                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int32), ("reserved", ct.c_int32)]
+                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int32), ("reserved", ct.c_int32),
+                ("lod_pixels", ct.c_double)]
 
 
 class hf_cascade_info(ct.Structure):
@@ -68,7 +69,8 @@ class hf_cascade_info(ct.Structure):
                 ("ox", ct.c_double), ("oy", ct.c_double), ("extent", ct.c_double),
                 ("texel", ct.c_double), ("tex", ct.c_void_p), ("mip", ct.c_void_p),
                 ("spans", ct.c_void_p), ("mip_floats", ct.c_int64),
-                ("water_tex", ct.c_void_p), ("texel_ladder", ct.c_int32), ("reuse_source", ct.c_int32)]
+                ("water_tex", ct.c_void_p), ("texel_ladder", ct.c_int32), ("reuse_source", ct.c_int32),
+                ("stop_level", ct.c_int32), ("reserved", ct.c_int32)]
 
     @property
     def h(self) -> float:

@@ -30,6 +30,7 @@ class Camera:
     split_lambda: float = 1.0
     overlap_frac: float = 0.05
     texel_ladder: int = 0         # 0: stable fit; n > 0: lattice fit, n texel sizes per octave
+    lod_pixels: float = 0.0       # 0: exact surface; > 0: coarse-level stop at this many pixels
 
     def with_(self, **kw) -> "Camera":
         return replace(self, **kw)

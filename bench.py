@@ -640,7 +640,7 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
     return out
 
 
-def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(1.0, 2.0, 4.0)):
+def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(2.0, 4.0, 8.0, 16.0)):
     """The coarse-level stop (hf_camera.lod_pixels) on the main line's frames:
     frame and ray-cast time (L2 flushed between frames), node visits per ray,
     and how far the image moves from the exact surface: the share of hit

@@ -948,6 +948,7 @@ RayParams ray_params(const ViewSlot* v, bool water) {
         rc.far_ext = float(ci.far_ext_depth);
         rc.budget = 8 * (2 * N + 8) * (rc.K + 2);
         rc.stop_level = std::min(ci.stop_level, rc.K);
+        if (rc.stop_level > 0) rp.coarse = 1;
         int64_t off = 0;
         for (int L = 0; L < kMaxLevels; ++L) {
             rc.lvl_off[L] = int32_t(off);

@@ -163,6 +163,7 @@ struct RayCascade {
 struct RayParams {
     int32_t C, W, H;
     int32_t water;           // 1: rays meet the terrain or the water surface, whichever comes first
+    int32_t coarse;          // 1: some cascade has a coarse-level stop (RayCascade.stop_level > 0)
     float ez;                // eye height (m)
     float F[3], R[3], U[3];  // camera basis
     float px_a, px_b, py_a, py_b;  // screen coordinates: s = fma(pixel, a, b), s in [-tan, tan]

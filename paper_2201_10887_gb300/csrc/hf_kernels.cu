@@ -1013,7 +1013,7 @@ struct RayDir {
 // zero component takes the non-positive branch, which leaves the walk as it
 // would be: the exit time along it is infinite, and the clamp of the other
 // coordinate returns the current cell.
-template <bool COUNT, bool COH, bool UNION, int SIGNS>
+template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE>
 __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
                                               float ez, float ta, float tb, float& t_hit, bool& on_water,
                                               DevStatus* status, uint32_t pixel, unsigned& visits, unsigned& tests) {
@@ -1044,7 +1044,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const float slack = 2e-6f * fabsf(top);
     int ci = min(max(int(floorf(fmaf(ta, r.du, r.eu))), 0), N - 2);
     int cj = min(max(int(floorf(fmaf(ta, r.dv, r.ev))), 0), N - 2);
-    const int L = c.stop_level;  // coarse-level stop: no node below this level is visited
+    const int L = COARSE ? c.stop_level : 0;  // coarse-level stop: no node below this level is visited
     int k = max(min(K, kRayStartLevel), L);
     float t = ta;
     const int budget = c.budget;
@@ -1061,7 +1061,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
                 --k;
                 continue;
             }
-            if (k > 0) {  // coarse-level stop: the ray meets this node's box top
+            if (COARSE && k > 0) {  // coarse-level stop: the ray meets this node's box top
                 const float z0 = fmaf(t, r.dz, ez);
                 t_hit = (z0 <= mx || !zneg) ? t : fminf(fmaf(mx - z0, d.rdz, t), te);
                 on_water = false;
@@ -1156,7 +1156,7 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayD
 // Section 5: the blend runs linearly in projected depth across the overlap
 // band of cascades c and c+1 when both are hit); 0x80 marks a first-hit
 // cascade whose hit is on the water surface.
-template <bool COUNT, bool COH, bool UNION, int SIGNS>
+template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE>
 __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_off)[kMaxLevels], const RayDir& d,
                                               DevStatus* status, uint32_t pix, unsigned& visits, unsigned& tests,
                                               float& t, int& hit) {
@@ -1167,7 +1167,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
         float ta, tb, tc;
         bool wet = false;
         if (!cascade_interval(cc, d, ta, tb)) continue;
-        if (!trace_cascade<COUNT, COH, UNION, SIGNS>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
+        if (!trace_cascade<COUNT, COH, UNION, SIGNS, COARSE>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
             continue;
         hit = (1 + c) | (wet ? 0x80 : 0);
         t = tc;
@@ -1178,7 +1178,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
                 float ta2, tb2, t2;
                 bool wet2 = false;
                 if (cascade_interval(cn, d, ta2, tb2) &&
-                    trace_cascade<COUNT, COH, UNION, SIGNS>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
+                    trace_cascade<COUNT, COH, UNION, SIGNS, COARSE>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
                                                      visits, tests)) {
                     const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
                     t = fmaf(al, t2 - tc, tc);
@@ -1188,7 +1188,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
     }
 }
 
-template <bool COUNT, bool COH, bool WATER = false>
+template <bool COUNT, bool COH, bool WATER = false, bool COARSE = false>
 __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_off)[kMaxLevels], DevStatus* status,
                                               int x, int y, unsigned& visits, unsigned& tests) {
     if (x >= p.W || y >= p.H) return;
@@ -1214,14 +1214,14 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
     int hit;
     float t;
     switch ((d.dx > 0.f ? 1 : 0) | (d.dy > 0.f ? 2 : 0) | (d.dz < 0.f ? 4 : 0)) {
-    case 0: cast_cascades<COUNT, COH, WATER, 0>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 1: cast_cascades<COUNT, COH, WATER, 1>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 2: cast_cascades<COUNT, COH, WATER, 2>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 3: cast_cascades<COUNT, COH, WATER, 3>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 4: cast_cascades<COUNT, COH, WATER, 4>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 5: cast_cascades<COUNT, COH, WATER, 5>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 6: cast_cascades<COUNT, COH, WATER, 6>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    default: cast_cascades<COUNT, COH, WATER, 7>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 0: cast_cascades<COUNT, COH, WATER, 0, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 1: cast_cascades<COUNT, COH, WATER, 1, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 2: cast_cascades<COUNT, COH, WATER, 2, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 3: cast_cascades<COUNT, COH, WATER, 3, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 4: cast_cascades<COUNT, COH, WATER, 4, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 5: cast_cascades<COUNT, COH, WATER, 5, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 6: cast_cascades<COUNT, COH, WATER, 6, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    default: cast_cascades<COUNT, COH, WATER, 7, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
     }
     if (!COUNT) {
         p.t_out[pix] = t;
@@ -1244,7 +1244,7 @@ __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_o
 // (8 and 64 registers for the walk over both surfaces).  A CTA covers 16 x 8
 // pixels, each warp an 8 x 4 patch of them: neighbouring rays in a square
 // patch take more of the same steps than in a 16 x 2 strip (2 % faster).
-template <bool COUNT, bool WATER>
+template <bool COUNT, bool WATER, bool COARSE>
 __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
     wait_for_predecessor();
     __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
@@ -1252,7 +1252,7 @@ __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_con
     load_level_offsets<false>(p, s_off, t, 128);
     __syncthreads();
     unsigned visits = 0, tests = 0;
-    raycast_pixel<COUNT, false, WATER>(p, s_off, status, blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7),
+    raycast_pixel<COUNT, false, WATER, COARSE>(p, s_off, status, blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7),
                                        blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3), visits, tests);
     if (COUNT) {
         visits = __reduce_add_sync(0xffffffffu, visits);
@@ -1268,8 +1268,10 @@ template <bool COUNT>
 int launch_raycast_t(const RayParams& p, DevStatus* status, void* stream) {
     dim3 grid((p.W + 15) / 16, (p.H + 7) / 8);
     if (p.water)
-        return launch_dependent(k_raycast<COUNT, true>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
-    return launch_dependent(k_raycast<COUNT, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
+        return launch_dependent(k_raycast<COUNT, true, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
+    if (p.coarse)
+        return launch_dependent(k_raycast<COUNT, false, true>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
+    return launch_dependent(k_raycast<COUNT, false, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
 }
 
 int launch_raycast(const RayParams& p, DevStatus* status, void* stream) {
@@ -1373,7 +1375,10 @@ __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const Batch
     const int x = (local % I.ray_tiles_x) * tw + int(threadIdx.x) % tw;
     const int y = (local / I.ray_tiles_x) * th + int(threadIdx.x) / tw;
     unsigned visits = 0, tests = 0;
-    raycast_pixel<false, COH>(I.ray, off, I.status, x, y, visits, tests);
+    if (I.ray.coarse)
+        raycast_pixel<false, COH, false, true>(I.ray, off, I.status, x, y, visits, tests);
+    else
+        raycast_pixel<false, COH>(I.ray, off, I.status, x, y, visits, tests);
 }
 
 // Units are taken in chunks of kChunk; completions of consecutive units of

@@ -38,7 +38,8 @@ def _setup(torch_cuda):
     rt = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     for slot, cam in enumerate([tiny.cameras[0].with_(n_cascades=3, cascade_size=160, width=97, height=61),
                                 tiny.cameras[0].with_(n_cascades=2, cascade_size=100, forward=(0.4, 0.9, -0.5)),
-                                tiny.cameras[0].with_(n_cascades=2, cascade_size=120, texel_ladder=4)]):
+                                tiny.cameras[0].with_(n_cascades=2, cascade_size=120, texel_ladder=4),
+                                tiny.cameras[0].with_(n_cascades=3, cascade_size=128, lod_pixels=16.0)]):
         views.append((rt, slot))
         cams.append(cam)
     return views, cams

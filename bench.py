@@ -492,10 +492,14 @@ def run_ours(args, rank, world, local_rank):
             import oracle
             oracle.build()
             cells = oracle.Cells(scene.tree)
-            res = oracle_frame_sample(scene, cams[sched[0]], cells, args.cpu_s, seed=0)
-            line["cpu_baseline"] = {"value": res["frame_ms"], "unit": "ms", "cores": oracle.threads(),
-                                    "kind": "oracle",
-                                    "sample": _oracle_sample_text(res) + f"; frame {sched[0]}"}
+            picks = sorted({0, len(cams) // 2, len(cams) - 1})  # first, middle and last frame of the flight
+            res = [oracle_frame_sample(scene, cams[f], cells, args.cpu_s / len(picks), seed=k)
+                   for k, f in enumerate(picks)]
+            line["cpu_baseline"] = {"value": statistics.mean(x["frame_ms"] for x in res), "unit": "ms",
+                                    "cores": oracle.threads(), "kind": "oracle",
+                                    "per_frame_ms": {str(f): x["frame_ms"] for f, x in zip(picks, res)},
+                                    "sample": _oracle_sample_text(res[0]) + "; mean over frames "
+                                              + ", ".join(str(f) for f in picks)}
         print(json.dumps(line), flush=True)
     r.close()
 

@@ -57,7 +57,7 @@ def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True, 
     assert terr <= RAY_REL, terr
     # the reported first-hit cascade agrees where both hit
     both = (gh > 0) & (oh > 0)
-    assert np.mean(gh[both] != oh[both]) < 1e-3
+    assert not both.any() or np.mean(gh[both] != oh[both]) < 1e-3
     r.close()
     return worst, terr, int((oh > 0).sum())
 

@@ -76,7 +76,7 @@ def _water_frame(orc, scene, cam, depth, texel_sample=None, seed=0):
     n_mis, n_bad = check_water_flags(orc, cam, scene.tree, rcs, texs, wtexs, gh, oh, seg)
     assert n_bad == 0, (n_mis, n_bad)
     both = (gh > 0) & (oh > 0) & ((gh & 0x80) == (oh & 0x80))
-    assert np.mean((gh[both] & 0x7F) != (oh[both] & 0x7F)) < 1e-3    # first-hit cascade
+    assert not both.any() or np.mean((gh[both] & 0x7F) != (oh[both] & 0x7F)) < 1e-3    # first-hit cascade
     r.close()
     return float(np.mean((oh & 0x80) > 0)), float(np.mean(oh > 0))
 

@@ -251,3 +251,15 @@ def test_reuse_dem_flight(torch_cuda):
     cams = [c.with_(texel_ladder=4) for c in s.cameras[600:604]]
     frac = _run_flight(torch_cuda, s, cams, check_rays=False)
     assert frac > 0.8, frac
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_reuse_random_flights(torch_cuda, tiny, seed):
+    """Seeded random flights (step, turn, ladder, cascade count and size,
+    with or without hysteresis): every frame equals a fresh one bit for bit
+    and the carried-over counts match the host's count."""
+    rng = np.random.default_rng(900 + seed)
+    cams = _flight(tiny.cameras[0], 4, step=(float(rng.uniform(-30, 30)), float(rng.uniform(-30, 30))),
+                   yaw_deg=float(rng.uniform(-3, 3)), ladder=int(rng.choice([1, 2, 4, 8])),
+                   n_cascades=int(rng.integers(1, 5)), cascade_size=int(rng.integers(40, 200)))
+    _run_flight(torch_cuda, tiny, cams, follow=bool(seed % 2))

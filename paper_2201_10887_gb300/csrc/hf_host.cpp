@@ -48,7 +48,8 @@ int cuda_fail(int e, const char* what) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bits of x rounded to nearest even in BF16 / FP16 (normal FP16 results only).
+// Bits of x rounded to nearest even in BF16 / FP16.  f16_bits returns
+// UINT32_MAX unless the rounded result is a normal FP16 number.
 uint32_t bf16_bits(float x) {
     uint32_t u;
     std::memcpy(&u, &x, 4);
@@ -65,6 +66,7 @@ uint32_t f16_bits(float x) {
         m = 0;
         ++e;
     }
+    if (e < 1 || e > 30) return std::numeric_limits<uint32_t>::max();
     return sign | (uint32_t(e) << 10) | m;
 }
 
@@ -529,7 +531,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         const float kM = float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
         const uint32_t kMb = f16 ? f16_bits(kM) : bf16_bits(kM);
         const int shift = f16 ? 10 : 7, emask = f16 ? 31 : 255;
-        const int eM = int((kMb >> shift) & uint32_t(emask));
+        const int eM = kMb == std::numeric_limits<uint32_t>::max() ? 0 : int((kMb >> shift) & uint32_t(emask));
         if (eM >= emask || eM - 2 * (M - lmin) < 1)
             return fail(HF_ERR_ARG, "the %s exponent scales of levels %d..%d leave the normal range",
                         f16 ? "FP16" : "BF16", lmin, M);

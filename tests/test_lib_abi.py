@@ -254,6 +254,21 @@ def test_reduced_precision_offset_limits(hfmod, tiny):
     assert e.value.code == hfmod.HF_ERR_ARG and "BF16" in str(e.value)
 
 
+@pytest.mark.parametrize("sigma", [60.0, 120.0, 180.0, 400.0, 1e-4])
+def test_reduced_precision_exponent_scale_range(hfmod, tiny, sigma):
+    """The FP16 exponent scale -log2(e) / (8 sigma^2) per squared half-cell
+    must be a normal FP16 number at every level: sigmas that push it below
+    2^-14 (sigma > ~54 cells) or above 65504 are rejected, whatever the bits
+    of the out-of-range value would wrap to.  FP32 takes them all."""
+    t = tiny.tree
+    lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    hfmod.hf_destroy(hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(sigma, 3.0, 0, -1)))
+    with pytest.raises(hfmod.HFError) as e:
+        hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(sigma, 3.0, 1, -1))
+    assert e.value.code == hfmod.HF_ERR_ARG and "normal range" in str(e.value)
+
+
 def test_water_layer_flags_and_sizes(hfmod, tiny):
     """The water layer: FP32 only, flag 0/1; it adds 4 bytes per
     leaf to the persistent buffer and a second texture per cascade (one

@@ -14,7 +14,8 @@
  *
  * Conventions
  *   - Every function returns HF_OK (0) or a negative HF_ERR_* code; no C++
- *     exception crosses this boundary.  hf_last_error() describes the most
+ *     exception crosses this boundary (each entry point catches them and
+ *     returns HF_ERR_HOST).  hf_last_error() describes the most
  *     recent failure of the calling thread.
  *   - The library never allocates device memory.  The caller allocates the
  *     sizes hf_query_bytes() reports and keeps ownership; buffers must stay
@@ -50,7 +51,9 @@ enum {
     HF_ERR_NOMEM = -3,   /* a caller buffer is smaller than required */
     HF_ERR_CUDA = -4,    /* a CUDA runtime call or kernel launch failed */
     HF_ERR_TIMEOUT = -5, /* a bounded device-side loop gave up; results are invalid */
-    HF_ERR_DATA = -6     /* device-side consistency check failed */
+    HF_ERR_DATA = -6,    /* device-side consistency check failed */
+    HF_ERR_HOST = -7     /* host-side failure: host memory for the library's own tables
+                            or worker threads could not be had; nothing was launched */
 };
 
 enum { HF_PREC_FP32 = 0, HF_PREC_FP16 = 1, HF_PREC_BF16 = 2 };

@@ -32,13 +32,16 @@ struct ApiRange {
 
 thread_local std::string g_err;
 
-int fail(int code, const char* fmt, ...) {
+int fail(int code, const char* fmt, ...) noexcept {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    g_err = buf;
+    try {
+        g_err = buf;
+    } catch (...) {  // no host memory left for the message: keep the code
+    }
     return code;
 }
 
@@ -384,285 +387,307 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
 
 int hfi::set_cuda_error(int e, const char* what) { return cuda_fail(e, what); }
 
+int hfi::exception_status(const char* where) noexcept {
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        return fail(HF_ERR_HOST, "%s: out of host memory", where);
+    } catch (const std::exception& x) {
+        return fail(HF_ERR_HOST, "%s: %s", where, x.what());
+    } catch (...) {
+        return fail(HF_ERR_HOST, "%s: unknown host exception", where);
+    }
+}
+
 extern "C" {
 
 const char* hf_last_error(void) { return g_err.c_str(); }
 
 int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int64_t n_leaves,
                        const hf_rbf_params* rbf, hf_ctx** out) {
-    ApiRange range_("hf_create_quadtree");
-    if (!desc || !rbf || !out) return fail(HF_ERR_ARG, "null argument");
-    if (n_leaves < 1 || !leaves) return fail(HF_ERR_ARG, "no leaves");
-    const hf_quadtree_desc& d = *desc;
-    if (!(std::isfinite(d.origin_x) && std::isfinite(d.origin_y) && std::isfinite(d.root_cell) &&
-          d.root_cell > 0.0))
-        return fail(HF_ERR_ARG, "origin / root_cell must be finite, root_cell > 0");
-    if (d.root_nx < 1 || d.root_ny < 1) return fail(HF_ERR_ARG, "root grid must be at least 1x1");
-    if (d.max_level < 0 || d.max_level > HF_MAX_LEVEL)
-        return fail(HF_ERR_ARG, "max_level must be in [0, %d]", HF_MAX_LEVEL);
-    const int M = d.max_level;
-    const int64_t fnx = int64_t(d.root_nx) << M, fny = int64_t(d.root_ny) << M;
-    if (fnx > (int64_t(1) << 30) || fny > (int64_t(1) << 30) || fnx * fny > (int64_t(1) << 34))
-        return fail(HF_ERR_ARG, "finest grid %lld x %lld too large", (long long)fnx, (long long)fny);
-    if (!(std::isfinite(rbf->sigma) && rbf->sigma > 0.0 && std::isfinite(rbf->radius) && rbf->radius > 0.0))
-        return fail(HF_ERR_ARG, "sigma and radius must be finite and > 0");
-    if (rbf->precision < HF_PREC_FP32 || rbf->precision > HF_PREC_BF16)
-        return fail(HF_ERR_ARG, "unknown precision %d", rbf->precision);
-    if (rbf->bucket_level > M) return fail(HF_ERR_ARG, "bucket_level %d > max_level %d", rbf->bucket_level, M);
-    if (rbf->water != 0 && rbf->water != 1) return fail(HF_ERR_ARG, "water must be 0 or 1");
-    if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->kernel != HF_RBF_WENDLAND_C2)
-        return fail(HF_ERR_ARG, "unknown RBF kernel %d", rbf->kernel);
-    if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->precision != HF_PREC_FP32)
-        return fail(HF_ERR_ARG, "the Wendland kernel needs FP32 precision");
-    if (rbf->water && rbf->precision != HF_PREC_FP32)
-        return fail(HF_ERR_ARG, "the water layer needs FP32 precision");
+    return guarded("hf_create_quadtree", [&]() -> int {
+        ApiRange range_("hf_create_quadtree");
+        if (!desc || !rbf || !out) return fail(HF_ERR_ARG, "null argument");
+        if (n_leaves < 1 || !leaves) return fail(HF_ERR_ARG, "no leaves");
+        const hf_quadtree_desc& d = *desc;
+        if (!(std::isfinite(d.origin_x) && std::isfinite(d.origin_y) && std::isfinite(d.root_cell) &&
+              d.root_cell > 0.0))
+            return fail(HF_ERR_ARG, "origin / root_cell must be finite, root_cell > 0");
+        if (d.root_nx < 1 || d.root_ny < 1) return fail(HF_ERR_ARG, "root grid must be at least 1x1");
+        if (d.max_level < 0 || d.max_level > HF_MAX_LEVEL)
+            return fail(HF_ERR_ARG, "max_level must be in [0, %d]", HF_MAX_LEVEL);
+        const int M = d.max_level;
+        const int64_t fnx = int64_t(d.root_nx) << M, fny = int64_t(d.root_ny) << M;
+        if (fnx > (int64_t(1) << 30) || fny > (int64_t(1) << 30) || fnx * fny > (int64_t(1) << 34))
+            return fail(HF_ERR_ARG, "finest grid %lld x %lld too large", (long long)fnx, (long long)fny);
+        if (!(std::isfinite(rbf->sigma) && rbf->sigma > 0.0 && std::isfinite(rbf->radius) && rbf->radius > 0.0))
+            return fail(HF_ERR_ARG, "sigma and radius must be finite and > 0");
+        if (rbf->precision < HF_PREC_FP32 || rbf->precision > HF_PREC_BF16)
+            return fail(HF_ERR_ARG, "unknown precision %d", rbf->precision);
+        if (rbf->bucket_level > M) return fail(HF_ERR_ARG, "bucket_level %d > max_level %d", rbf->bucket_level, M);
+        if (rbf->water != 0 && rbf->water != 1) return fail(HF_ERR_ARG, "water must be 0 or 1");
+        if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->kernel != HF_RBF_WENDLAND_C2)
+            return fail(HF_ERR_ARG, "unknown RBF kernel %d", rbf->kernel);
+        if (rbf->kernel != HF_RBF_GAUSSIAN && rbf->precision != HF_PREC_FP32)
+            return fail(HF_ERR_ARG, "the Wendland kernel needs FP32 precision");
+        if (rbf->water && rbf->precision != HF_PREC_FP32)
+            return fail(HF_ERR_ARG, "the water layer needs FP32 precision");
 
-    std::unique_ptr<hf_ctx> ctx(new hf_ctx);
-    ctx->desc = d;
-    ctx->rbf = *rbf;
-    ctx->M = M;
-    ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 1) : rbf->bucket_level;
-    ctx->n_leaves = n_leaves;
-    ctx->c_fin = d.root_cell / double(int64_t(1) << M);
-    ctx->width = d.root_cell * d.root_nx;
-    ctx->height = d.root_cell * d.root_ny;
+        std::unique_ptr<hf_ctx> ctx(new hf_ctx);
+        ctx->desc = d;
+        ctx->rbf = *rbf;
+        ctx->M = M;
+        ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 1) : rbf->bucket_level;
+        ctx->n_leaves = n_leaves;
+        ctx->c_fin = d.root_cell / double(int64_t(1) << M);
+        ctx->width = d.root_cell * d.root_nx;
+        ctx->height = d.root_cell * d.root_ny;
 
-    // occupancy, duplicates, ranges
-    HostBitmaps& lf = ctx->leaves;
-    lf.init(d.root_nx, d.root_ny, M);
-    int lmin = M, lmax = 0;
-    float vmin = INFINITY, vmax = -INFINITY;
-    int64_t area = 0;
-    for (int64_t k = 0; k < n_leaves; ++k) {
-        const hf_leaf& l = leaves[k];
-        if (l.level < 0 || l.level > M) return fail(HF_ERR_ARG, "leaf %lld: level %d out of range", (long long)k, l.level);
-        if (l.ix < 0 || l.iy < 0 || l.ix >= lf.nx[l.level] || l.iy >= lf.ny[l.level])
-            return fail(HF_ERR_ARG, "leaf %lld: index (%d, %d) outside level %d", (long long)k, l.ix, l.iy, l.level);
-        if (!std::isfinite(l.value)) return fail(HF_ERR_ARG, "leaf %lld: value not finite", (long long)k);
-        if (lf.test(l.level, l.ix, l.iy)) return fail(HF_ERR_ARG, "leaf %lld: duplicate cell", (long long)k);
-        lf.set(l.level, l.ix, l.iy);
-        lmin = std::min(lmin, l.level);
-        lmax = std::max(lmax, l.level);
-        vmin = std::min(vmin, l.value);
-        vmax = std::max(vmax, l.value);
-        area += int64_t(1) << (2 * (M - l.level));
-    }
-    // no leaf may lie inside another; with the area sum this is an exact tiling
-    for (int64_t k = 0; k < n_leaves; ++k) {
-        const hf_leaf& l = leaves[k];
-        for (int A = 0; A < l.level; ++A)
-            if (lf.test(A, l.ix >> (l.level - A), l.iy >> (l.level - A)))
-                return fail(HF_ERR_ARG, "leaf %lld lies inside a coarser leaf", (long long)k);
-    }
-    if (area != fnx * fny) return fail(HF_ERR_ARG, "leaves do not cover the domain (gap)");
-    lf.finalize();
-    ctx->c_min = d.root_cell / double(int64_t(1) << lmax);
-    ctx->c_max = d.root_cell / double(int64_t(1) << lmin);
-    ctx->zmin = vmin;
-    ctx->zmax = vmax;
-    ++ctx->data_version;
-    if (rbf->water) ctx->depth.assign(size_t(n_leaves), 0.f);
-
-    // records in (level, iy, ix) order: centre, weight scale, value
-    const double log2e = 1.4426950408889634;
-    ctx->perm.resize(size_t(n_leaves));
-    ctx->recs.resize(size_t(n_leaves));
-    for (int64_t k = 0; k < n_leaves; ++k) {
-        const hf_leaf& l = leaves[k];
-        const int64_t s = lf.rank(l.level, l.ix, l.iy);
-        const double c = d.root_cell / double(int64_t(1) << l.level);
-        ctx->perm[size_t(k)] = s;
-        // exponent scale of the weight (see rbf_weight in hf_kernels.cu)
-        const double scale = rbf->kernel == HF_RBF_WENDLAND_C2 ? 1.0 / (rbf->radius * c * rbf->radius * c)
-                                                               : -log2e / (2.0 * rbf->sigma * rbf->sigma * c * c);
-        ctx->recs[size_t(s)] = make_float4(float((l.ix + 0.5) * c), float((l.iy + 0.5) * c), float(scale), l.value);
-    }
-
-    // buckets: leaves at or below level B, coarser leaves split down to B
-    HostBitmaps& bk = ctx->buckets;
-    bk.init(d.root_nx, d.root_ny, M);
-    const int B = ctx->B;
-    for (int64_t k = 0; k < n_leaves; ++k) {
-        const hf_leaf& l = leaves[k];
-        if (l.level >= B) {
-            bk.set(l.level, l.ix, l.iy);
-        } else {
-            const int sh = B - l.level;
-            for (int64_t y = int64_t(l.iy) << sh; y < (int64_t(l.iy) + 1) << sh; ++y)
-                for (int64_t x = int64_t(l.ix) << sh; x < (int64_t(l.ix) + 1) << sh; ++x) bk.set(B, x, y);
+        // occupancy, duplicates, ranges
+        HostBitmaps& lf = ctx->leaves;
+        lf.init(d.root_nx, d.root_ny, M);
+        int lmin = M, lmax = 0;
+        float vmin = INFINITY, vmax = -INFINITY;
+        int64_t area = 0;
+        for (int64_t k = 0; k < n_leaves; ++k) {
+            const hf_leaf& l = leaves[k];
+            if (l.level < 0 || l.level > M) return fail(HF_ERR_ARG, "leaf %lld: level %d out of range", (long long)k, l.level);
+            if (l.ix < 0 || l.iy < 0 || l.ix >= lf.nx[l.level] || l.iy >= lf.ny[l.level])
+                return fail(HF_ERR_ARG, "leaf %lld: index (%d, %d) outside level %d", (long long)k, l.ix, l.iy, l.level);
+            if (!std::isfinite(l.value)) return fail(HF_ERR_ARG, "leaf %lld: value not finite", (long long)k);
+            if (lf.test(l.level, l.ix, l.iy)) return fail(HF_ERR_ARG, "leaf %lld: duplicate cell", (long long)k);
+            lf.set(l.level, l.ix, l.iy);
+            lmin = std::min(lmin, l.level);
+            lmax = std::max(lmax, l.level);
+            vmin = std::min(vmin, l.value);
+            vmax = std::max(vmax, l.value);
+            area += int64_t(1) << (2 * (M - l.level));
         }
-    }
-    bk.finalize();
-    ctx->n_buckets = bk.base[M + 1];
+        // no leaf may lie inside another; with the area sum this is an exact tiling
+        for (int64_t k = 0; k < n_leaves; ++k) {
+            const hf_leaf& l = leaves[k];
+            for (int A = 0; A < l.level; ++A)
+                if (lf.test(A, l.ix >> (l.level - A), l.iy >> (l.level - A)))
+                    return fail(HF_ERR_ARG, "leaf %lld lies inside a coarser leaf", (long long)k);
+        }
+        if (area != fnx * fny) return fail(HF_ERR_ARG, "leaves do not cover the domain (gap)");
+        lf.finalize();
+        ctx->c_min = d.root_cell / double(int64_t(1) << lmax);
+        ctx->c_max = d.root_cell / double(int64_t(1) << lmin);
+        ctx->zmin = vmin;
+        ctx->zmax = vmax;
+        ++ctx->data_version;
+        if (rbf->water) ctx->depth.assign(size_t(n_leaves), 0.f);
 
-    // reach of a level-L centre, R c_L plus a margin covering FP32 rounding of
-    // texel positions, in units of half a finest cell
-    const double ext = std::max(ctx->width, ctx->height);
-    const double ulp = std::ldexp(1.0, std::ilogb(ext) - 23);
-    const double margin = std::max(1e-3 * ctx->c_fin, 8.0 * ulp);
-    const double q = 0.5 * ctx->c_fin;
-    for (int L = 0; L <= M; ++L)
-        ctx->reach_q[L] = (rbf->radius * (d.root_cell / double(int64_t(1) << L)) + margin) / q;
+        // records in (level, iy, ix) order: centre, weight scale, value
+        const double log2e = 1.4426950408889634;
+        ctx->perm.resize(size_t(n_leaves));
+        ctx->recs.resize(size_t(n_leaves));
+        for (int64_t k = 0; k < n_leaves; ++k) {
+            const hf_leaf& l = leaves[k];
+            const int64_t s = lf.rank(l.level, l.ix, l.iy);
+            const double c = d.root_cell / double(int64_t(1) << l.level);
+            ctx->perm[size_t(k)] = s;
+            // exponent scale of the weight (see rbf_weight in hf_kernels.cu)
+            const double scale = rbf->kernel == HF_RBF_WENDLAND_C2 ? 1.0 / (rbf->radius * c * rbf->radius * c)
+                                                                   : -log2e / (2.0 * rbf->sigma * rbf->sigma * c * c);
+            ctx->recs[size_t(s)] = make_float4(float((l.ix + 0.5) * c), float((l.iy + 0.5) * c), float(scale), l.value);
+        }
 
-    std::vector<int64_t> counts(size_t(ctx->n_buckets), 0);
-    const int nt = std::max(1, std::min(64, int(std::thread::hardware_concurrency())));
-    count_lists_host(ctx->enum_tables(false), ctx->lookup_tables(false), counts.data(), nt);
-    ctx->offsets.resize(size_t(ctx->n_buckets) + 1);
-    int64_t run = 0;
-    for (int64_t b = 0; b < ctx->n_buckets; ++b) {
-        ctx->offsets[size_t(b)] = run;
-        run += counts[size_t(b)];
-    }
-    ctx->offsets[size_t(ctx->n_buckets)] = run;
-    ctx->n_cand = run;
-    if (rbf->precision != HF_PREC_FP32) {
-        // bucket-relative offsets must be exact small integers in the 16-bit type
-        double rmax = 0.0;
+        // buckets: leaves at or below level B, coarser leaves split down to B
+        HostBitmaps& bk = ctx->buckets;
+        bk.init(d.root_nx, d.root_ny, M);
+        const int B = ctx->B;
+        for (int64_t k = 0; k < n_leaves; ++k) {
+            const hf_leaf& l = leaves[k];
+            if (l.level >= B) {
+                bk.set(l.level, l.ix, l.iy);
+            } else {
+                const int sh = B - l.level;
+                for (int64_t y = int64_t(l.iy) << sh; y < (int64_t(l.iy) + 1) << sh; ++y)
+                    for (int64_t x = int64_t(l.ix) << sh; x < (int64_t(l.ix) + 1) << sh; ++x) bk.set(B, x, y);
+            }
+        }
+        bk.finalize();
+        ctx->n_buckets = bk.base[M + 1];
+
+        // reach of a level-L centre, R c_L plus a margin covering FP32 rounding of
+        // texel positions, in units of half a finest cell
+        const double ext = std::max(ctx->width, ctx->height);
+        const double ulp = std::ldexp(1.0, std::ilogb(ext) - 23);
+        const double margin = std::max(1e-3 * ctx->c_fin, 8.0 * ulp);
+        const double q = 0.5 * ctx->c_fin;
         for (int L = 0; L <= M; ++L)
-            if (lf.base[L + 1] > lf.base[L]) rmax = std::max(rmax, ctx->reach_q[L]);
-        const double span = rmax + double(int64_t(1) << (M - ctx->B + 1)) + 1.0;
-        const double limit = rbf->precision == HF_PREC_FP16 ? 1024.0 : 256.0;
-        if (span > limit)
-            return fail(HF_ERR_ARG, "candidate offsets span %.0f half-cells, more than the %s path holds exactly (%.0f)",
-                        span, rbf->precision == HF_PREC_FP16 ? "FP16" : "BF16", limit);
-        // exponent scales per squared half-cell: the finest level's is -log2(e) / (8 sigma^2);
-        // level L's lowers the exponent by 2 (M - L), which must stay a normal number
-        const bool f16 = rbf->precision == HF_PREC_FP16;
-        const float kM = float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
-        const uint32_t kMb = f16 ? f16_bits(kM) : bf16_bits(kM);
-        const int shift = f16 ? 10 : 7, emask = f16 ? 31 : 255;
-        const int eM = kMb == std::numeric_limits<uint32_t>::max() ? 0 : int((kMb >> shift) & uint32_t(emask));
-        if (eM >= emask || eM - 2 * (M - lmin) < 1)
-            return fail(HF_ERR_ARG, "the %s exponent scales of levels %d..%d leave the normal range",
-                        f16 ? "FP16" : "BF16", lmin, M);
-        const uint32_t step = 2u << shift;
-        const uint32_t kb = kMb - uint32_t(M) * step;  // level 0's bits, modulo 2^32
-        ctx->kb2 = kb * 0x10001u;
-        ctx->pair_offsets.resize(size_t(ctx->n_buckets) + 1);
-        int64_t pr = 0;
+            ctx->reach_q[L] = (rbf->radius * (d.root_cell / double(int64_t(1) << L)) + margin) / q;
+
+        std::vector<int64_t> counts(size_t(ctx->n_buckets), 0);
+        const int nt = std::max(1, std::min(64, int(std::thread::hardware_concurrency())));
+        count_lists_host(ctx->enum_tables(false), ctx->lookup_tables(false), counts.data(), nt);
+        ctx->offsets.resize(size_t(ctx->n_buckets) + 1);
+        int64_t run = 0;
         for (int64_t b = 0; b < ctx->n_buckets; ++b) {
-            ctx->pair_offsets[size_t(b)] = pr;
-            pr += (counts[size_t(b)] + 1) / 2;
+            ctx->offsets[size_t(b)] = run;
+            run += counts[size_t(b)];
         }
-        ctx->pair_offsets[size_t(ctx->n_buckets)] = pr;
-        ctx->n_pairs = pr;
-    }
-    ctx->lay = ctx->layout();
-    *out = ctx.release();
-    g_err.clear();
-    return HF_OK;
+        ctx->offsets[size_t(ctx->n_buckets)] = run;
+        ctx->n_cand = run;
+        if (rbf->precision != HF_PREC_FP32) {
+            // bucket-relative offsets must be exact small integers in the 16-bit type
+            double rmax = 0.0;
+            for (int L = 0; L <= M; ++L)
+                if (lf.base[L + 1] > lf.base[L]) rmax = std::max(rmax, ctx->reach_q[L]);
+            const double span = rmax + double(int64_t(1) << (M - ctx->B + 1)) + 1.0;
+            const double limit = rbf->precision == HF_PREC_FP16 ? 1024.0 : 256.0;
+            if (span > limit)
+                return fail(HF_ERR_ARG, "candidate offsets span %.0f half-cells, more than the %s path holds exactly (%.0f)",
+                            span, rbf->precision == HF_PREC_FP16 ? "FP16" : "BF16", limit);
+            // exponent scales per squared half-cell: the finest level's is -log2(e) / (8 sigma^2);
+            // level L's lowers the exponent by 2 (M - L), which must stay a normal number
+            const bool f16 = rbf->precision == HF_PREC_FP16;
+            const float kM = float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
+            const uint32_t kMb = f16 ? f16_bits(kM) : bf16_bits(kM);
+            const int shift = f16 ? 10 : 7, emask = f16 ? 31 : 255;
+            const int eM = kMb == std::numeric_limits<uint32_t>::max() ? 0 : int((kMb >> shift) & uint32_t(emask));
+            if (eM >= emask || eM - 2 * (M - lmin) < 1)
+                return fail(HF_ERR_ARG, "the %s exponent scales of levels %d..%d leave the normal range",
+                            f16 ? "FP16" : "BF16", lmin, M);
+            const uint32_t step = 2u << shift;
+            const uint32_t kb = kMb - uint32_t(M) * step;  // level 0's bits, modulo 2^32
+            ctx->kb2 = kb * 0x10001u;
+            ctx->pair_offsets.resize(size_t(ctx->n_buckets) + 1);
+            int64_t pr = 0;
+            for (int64_t b = 0; b < ctx->n_buckets; ++b) {
+                ctx->pair_offsets[size_t(b)] = pr;
+                pr += (counts[size_t(b)] + 1) / 2;
+            }
+            ctx->pair_offsets[size_t(ctx->n_buckets)] = pr;
+            ctx->n_pairs = pr;
+        }
+        ctx->lay = ctx->layout();
+        *out = ctx.release();
+        g_err.clear();
+        return HF_OK;
+    });
 }
 
 int hf_query_bytes(const hf_ctx* ctx, int32_t n_cascades, int32_t cascade_size,
                    size_t* persistent_bytes, size_t* view_bytes) {
-    if (!ctx) return fail(HF_ERR_ARG, "null context");
-    if (persistent_bytes) *persistent_bytes = ctx->lay.total;
-    if (view_bytes) {
-        if (n_cascades < 1 || n_cascades > HF_MAX_CASCADES || cascade_size < 2 || cascade_size > kMaxCascadeSize)
-            return fail(HF_ERR_ARG, "cascades must be 1..%d of side 2..%d", HF_MAX_CASCADES, kMaxCascadeSize);
-        *view_bytes = per_view_bytes(n_cascades, cascade_size, ctx->rbf.water != 0);
-    }
-    return HF_OK;
+    return guarded("hf_query_bytes", [&]() -> int {
+        if (!ctx) return fail(HF_ERR_ARG, "null context");
+        if (persistent_bytes) *persistent_bytes = ctx->lay.total;
+        if (view_bytes) {
+            if (n_cascades < 1 || n_cascades > HF_MAX_CASCADES || cascade_size < 2 || cascade_size > kMaxCascadeSize)
+                return fail(HF_ERR_ARG, "cascades must be 1..%d of side 2..%d", HF_MAX_CASCADES, kMaxCascadeSize);
+            *view_bytes = per_view_bytes(n_cascades, cascade_size, ctx->rbf.water != 0);
+        }
+        return HF_OK;
+    });
 }
 
 int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* stream) {
-    ApiRange range_("hf_bind_persistent");
-    if (!ctx || !dev_persistent) return fail(HF_ERR_ARG, "null argument");
-    if (reinterpret_cast<uintptr_t>(dev_persistent) & 255) return fail(HF_ERR_ARG, "buffer must be 256-byte aligned");
-    if (bytes < ctx->lay.total)
-        return fail(HF_ERR_NOMEM, "persistent buffer has %zu bytes, %zu needed", bytes, ctx->lay.total);
-    cudaStream_t s = cudaStream_t(stream);
-    char* dev = static_cast<char*>(dev_persistent);
-    const PersistentLayout& l = ctx->lay;
-    int e = cudaMemsetAsync(dev + l.status, 0, sizeof(DevStatus), s);
-    if (!e) e = cudaMemcpyAsync(dev + l.lbits, ctx->leaves.bits.data(), ctx->leaves.bits.size() * 8, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(dev + l.lprefix, ctx->leaves.prefix.data(), ctx->leaves.prefix.size() * 4, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(dev + l.bbits, ctx->buckets.bits.data(), ctx->buckets.bits.size() * 8, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(dev + l.bprefix, ctx->buckets.prefix.data(), ctx->buckets.prefix.size() * 4, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(dev + l.recs, ctx->recs.data(), ctx->recs.size() * 16, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(dev + l.offsets, ctx->offsets.data(), ctx->offsets.size() * 8, cudaMemcpyHostToDevice, s);
-    if (!e && ctx->rbf.precision != HF_PREC_FP32)
-        e = cudaMemcpyAsync(dev + l.pair_offsets, ctx->pair_offsets.data(), ctx->pair_offsets.size() * 8,
-                            cudaMemcpyHostToDevice, s);
-    if (!e && ctx->rbf.water)
-        e = cudaMemcpyAsync(dev + l.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
-    if (e) return cuda_fail(e, "upload of the quadtree");
-    ctx->dev = dev;
-    ctx->dev_bytes = bytes;
-    e = launch_fill_lists(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
-    if (e) return cuda_fail(e, "influence-list kernel launch");
-    if (ctx->rbf.precision != HF_PREC_FP32) {
-        e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
-                                ctx->rbf.precision, stream);
-        if (e) return cuda_fail(e, "compact-list kernel launch");
-    }
-    e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(e, "influence-list build");
-    DevStatus st;
-    e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
-    if (e) return cuda_fail(e, "status read-back");
-    if (st.flags) {
-        ctx->dev = nullptr;
-        return fail(HF_ERR_DATA, "influence-list build disagreed with the host count at bucket %u", st.detail);
-    }
-    return HF_OK;
+    return guarded("hf_bind_persistent", [&]() -> int {
+        ApiRange range_("hf_bind_persistent");
+        if (!ctx || !dev_persistent) return fail(HF_ERR_ARG, "null argument");
+        if (reinterpret_cast<uintptr_t>(dev_persistent) & 255) return fail(HF_ERR_ARG, "buffer must be 256-byte aligned");
+        if (bytes < ctx->lay.total)
+            return fail(HF_ERR_NOMEM, "persistent buffer has %zu bytes, %zu needed", bytes, ctx->lay.total);
+        cudaStream_t s = cudaStream_t(stream);
+        char* dev = static_cast<char*>(dev_persistent);
+        const PersistentLayout& l = ctx->lay;
+        int e = cudaMemsetAsync(dev + l.status, 0, sizeof(DevStatus), s);
+        if (!e) e = cudaMemcpyAsync(dev + l.lbits, ctx->leaves.bits.data(), ctx->leaves.bits.size() * 8, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dev + l.lprefix, ctx->leaves.prefix.data(), ctx->leaves.prefix.size() * 4, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dev + l.bbits, ctx->buckets.bits.data(), ctx->buckets.bits.size() * 8, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dev + l.bprefix, ctx->buckets.prefix.data(), ctx->buckets.prefix.size() * 4, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dev + l.recs, ctx->recs.data(), ctx->recs.size() * 16, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemcpyAsync(dev + l.offsets, ctx->offsets.data(), ctx->offsets.size() * 8, cudaMemcpyHostToDevice, s);
+        if (!e && ctx->rbf.precision != HF_PREC_FP32)
+            e = cudaMemcpyAsync(dev + l.pair_offsets, ctx->pair_offsets.data(), ctx->pair_offsets.size() * 8,
+                                cudaMemcpyHostToDevice, s);
+        if (!e && ctx->rbf.water)
+            e = cudaMemcpyAsync(dev + l.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
+        if (e) return cuda_fail(e, "upload of the quadtree");
+        ctx->dev = dev;
+        ctx->dev_bytes = bytes;
+        e = launch_fill_lists(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
+        if (e) return cuda_fail(e, "influence-list kernel launch");
+        if (ctx->rbf.precision != HF_PREC_FP32) {
+            e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
+                                    ctx->rbf.precision, stream);
+            if (e) return cuda_fail(e, "compact-list kernel launch");
+        }
+        e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail(e, "influence-list build");
+        DevStatus st;
+        e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
+        if (e) return cuda_fail(e, "status read-back");
+        if (st.flags) {
+            ctx->dev = nullptr;
+            return fail(HF_ERR_DATA, "influence-list build disagreed with the host count at bucket %u", st.detail);
+        }
+        return HF_OK;
+    });
 }
 
 int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* stream) {
-    ApiRange range_("hf_update_values");
-    if (!ctx || !values) return fail(HF_ERR_ARG, "null argument");
-    if (n_values != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld values", (long long)ctx->n_leaves);
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    for (int64_t k = 0; k < n_values; ++k)  // validate before touching any state
-        if (!std::isfinite(values[k])) return fail(HF_ERR_ARG, "value %lld not finite", (long long)k);
-    ctx->staged.resize(size_t(n_values));
-    float vmin = INFINITY, vmax = -INFINITY;
-    for (int64_t k = 0; k < n_values; ++k) {
-        const int64_t s = ctx->perm[size_t(k)];
-        ctx->staged[size_t(s)] = values[k];
-        ctx->recs[size_t(s)].w = values[k];
-        vmin = std::min(vmin, values[k]);
-        vmax = std::max(vmax, values[k]);
-    }
-    ctx->zmin = vmin;
-    ctx->zmax = vmax;
-    ++ctx->data_version;
-    for (size_t k = 0; k < ctx->depth.size(); ++k)
-        if (ctx->depth[k] > 0.f) ctx->zmax = std::max(double(ctx->zmax), double(ctx->recs[k].w) + ctx->depth[k]);
-    cudaStream_t s = cudaStream_t(stream);
-    int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
-                              cudaMemcpyHostToDevice, s);
-    if (!e && ctx->rbf.precision != HF_PREC_FP32)  // the compact lists carry copies of the values
-        e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
-                                ctx->rbf.precision, stream);
-    if (!e) e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(e, "value upload");
-    return HF_OK;
+    return guarded("hf_update_values", [&]() -> int {
+        ApiRange range_("hf_update_values");
+        if (!ctx || !values) return fail(HF_ERR_ARG, "null argument");
+        if (n_values != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld values", (long long)ctx->n_leaves);
+        if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+        for (int64_t k = 0; k < n_values; ++k)  // validate before touching any state
+            if (!std::isfinite(values[k])) return fail(HF_ERR_ARG, "value %lld not finite", (long long)k);
+        ctx->staged.resize(size_t(n_values));
+        float vmin = INFINITY, vmax = -INFINITY;
+        for (int64_t k = 0; k < n_values; ++k) {
+            const int64_t s = ctx->perm[size_t(k)];
+            ctx->staged[size_t(s)] = values[k];
+            ctx->recs[size_t(s)].w = values[k];
+            vmin = std::min(vmin, values[k]);
+            vmax = std::max(vmax, values[k]);
+        }
+        ctx->zmin = vmin;
+        ctx->zmax = vmax;
+        ++ctx->data_version;
+        for (size_t k = 0; k < ctx->depth.size(); ++k)
+            if (ctx->depth[k] > 0.f) ctx->zmax = std::max(double(ctx->zmax), double(ctx->recs[k].w) + ctx->depth[k]);
+        cudaStream_t s = cudaStream_t(stream);
+        int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
+                                  cudaMemcpyHostToDevice, s);
+        if (!e && ctx->rbf.precision != HF_PREC_FP32)  // the compact lists carry copies of the values
+            e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
+                                    ctx->rbf.precision, stream);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail(e, "value upload");
+        return HF_OK;
+    });
 }
 
 int hf_update_water(hf_ctx* ctx, const float* depths, int64_t n_depths, void* stream) {
-    ApiRange range_("hf_update_water");
-    if (!ctx || !depths) return fail(HF_ERR_ARG, "null argument");
-    if (!ctx->rbf.water) return fail(HF_ERR_STATE, "context was created without the water layer");
-    if (n_depths != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld depths", (long long)ctx->n_leaves);
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    for (int64_t k = 0; k < n_depths; ++k)
-        if (!(std::isfinite(depths[k]) && depths[k] >= 0.f))
-            return fail(HF_ERR_ARG, "depth %lld must be finite and >= 0", (long long)k);
-    double zmax = -INFINITY;
-    for (int64_t k = 0; k < n_depths; ++k) {
-        const int64_t s = ctx->perm[size_t(k)];
-        ctx->depth[size_t(s)] = depths[k];
-    }
-    for (int64_t s = 0; s < n_depths; ++s)
-        zmax = std::max(zmax, double(ctx->recs[size_t(s)].w) + (ctx->depth[size_t(s)] > 0.f ? ctx->depth[size_t(s)] : 0.0));
-    ctx->zmax = zmax;
-    ++ctx->data_version;
-    cudaStream_t s = cudaStream_t(stream);
-    int e = cudaMemcpyAsync(ctx->dev + ctx->lay.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(e, "depth upload");
-    return HF_OK;
+    return guarded("hf_update_water", [&]() -> int {
+        ApiRange range_("hf_update_water");
+        if (!ctx || !depths) return fail(HF_ERR_ARG, "null argument");
+        if (!ctx->rbf.water) return fail(HF_ERR_STATE, "context was created without the water layer");
+        if (n_depths != ctx->n_leaves) return fail(HF_ERR_ARG, "expected %lld depths", (long long)ctx->n_leaves);
+        if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+        for (int64_t k = 0; k < n_depths; ++k)
+            if (!(std::isfinite(depths[k]) && depths[k] >= 0.f))
+                return fail(HF_ERR_ARG, "depth %lld must be finite and >= 0", (long long)k);
+        double zmax = -INFINITY;
+        for (int64_t k = 0; k < n_depths; ++k) {
+            const int64_t s = ctx->perm[size_t(k)];
+            ctx->depth[size_t(s)] = depths[k];
+        }
+        for (int64_t s = 0; s < n_depths; ++s)
+            zmax = std::max(zmax, double(ctx->recs[size_t(s)].w) + (ctx->depth[size_t(s)] > 0.f ? ctx->depth[size_t(s)] : 0.0));
+        ctx->zmax = zmax;
+        ++ctx->data_version;
+        cudaStream_t s = cudaStream_t(stream);
+        int e = cudaMemcpyAsync(ctx->dev + ctx->lay.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail(e, "depth upload");
+        return HF_OK;
+    });
 }
 
 namespace {
@@ -717,23 +742,27 @@ int set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, 
 }  // namespace
 
 int hf_set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes) {
-    ApiRange range_("hf_set_camera");
-    return set_camera(ctx, slot, cam, dev_view, bytes, nullptr);
+    return guarded("hf_set_camera", [&]() -> int {
+        ApiRange range_("hf_set_camera");
+        return set_camera(ctx, slot, cam, dev_view, bytes, nullptr);
+    });
 }
 
 int hf_set_camera_follow(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, size_t bytes,
                          int32_t prev_slot) {
-    ApiRange range_("hf_set_camera_follow");
-    if (!ctx || !cam) return fail(HF_ERR_ARG, "null argument");
-    const ViewSlot* p = get_view(ctx, prev_slot);
-    if (!p || p->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera to follow", prev_slot);
-    int64_t follow[HF_MAX_CASCADES];
-    for (int k = 0; k < HF_MAX_CASCADES; ++k)  // no step to keep: never one above the fitted one
-        follow[k] = std::numeric_limits<int64_t>::min();
-    if (p->cam.texel_ladder == cam->texel_ladder && cam->texel_ladder > 0)
-        for (int k = 0; k < p->cam.n_cascades; ++k)
-            if (p->fit.cas[k].n_poly >= 3) follow[k] = p->fit.cas[k].snap_k;
-    return set_camera(ctx, slot, cam, dev_view, bytes, follow);
+    return guarded("hf_set_camera_follow", [&]() -> int {
+        ApiRange range_("hf_set_camera_follow");
+        if (!ctx || !cam) return fail(HF_ERR_ARG, "null argument");
+        const ViewSlot* p = get_view(ctx, prev_slot);
+        if (!p || p->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera to follow", prev_slot);
+        int64_t follow[HF_MAX_CASCADES];
+        for (int k = 0; k < HF_MAX_CASCADES; ++k)  // no step to keep: never one above the fitted one
+            follow[k] = std::numeric_limits<int64_t>::min();
+        if (p->cam.texel_ladder == cam->texel_ladder && cam->texel_ladder > 0)
+            for (int k = 0; k < p->cam.n_cascades; ++k)
+                if (p->fit.cas[k].n_poly >= 3) follow[k] = p->fit.cas[k].snap_k;
+        return set_camera(ctx, slot, cam, dev_view, bytes, follow);
+    });
 }
 
 namespace {
@@ -842,65 +871,71 @@ int reuse_source(const ViewSlot* v, int k, const ViewSlot* p, ViewSlot::Reuse* r
 }  // namespace
 
 int hf_discretize_cascades(hf_ctx* ctx, int32_t slot, void* stream) {
-    ApiRange range_("hf_discretize_cascades");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    for (int k = 0; k < HF_MAX_CASCADES; ++k) {
-        v->reuse[k] = ViewSlot::Reuse();
-        v->fit.cas[k].reuse_source = -1;
-    }
-    return discretize_view(ctx, v, stream);
+    return guarded("hf_discretize_cascades", [&]() -> int {
+        ApiRange range_("hf_discretize_cascades");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+        if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+        for (int k = 0; k < HF_MAX_CASCADES; ++k) {
+            v->reuse[k] = ViewSlot::Reuse();
+            v->fit.cas[k].reuse_source = -1;
+        }
+        return discretize_view(ctx, v, stream);
+    });
 }
 
 int hf_discretize_reuse(hf_ctx* ctx, int32_t slot, int32_t prev_slot, void* stream) {
-    ApiRange range_("hf_discretize_reuse");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    if (prev_slot == slot) return fail(HF_ERR_ARG, "a slot cannot reuse its own texels");
-    const ViewSlot* p = get_view(ctx, prev_slot);
-    if (!p || p->stage < 2) return fail(HF_ERR_STATE, "view slot %d holds no discretized frame", prev_slot);
-    if (v->dev < p->dev + p->bytes && p->dev < v->dev + v->bytes)
-        return fail(HF_ERR_ARG, "view slots %d and %d share buffer memory", slot, prev_slot);
-    const bool same_data = p->data_version == ctx->data_version;
-    for (int k = 0; k < HF_MAX_CASCADES; ++k) {
-        v->reuse[k] = ViewSlot::Reuse();
-        v->fit.cas[k].reuse_source = -1;
-    }
-    for (int k = 0; k < v->cam.n_cascades && same_data; ++k) {
-        ViewSlot::Reuse r;
-        const int q = reuse_source(v, k, p, &r);
-        if (q < 0) continue;
-        v->reuse[k] = r;
-        v->fit.cas[k].reuse_source = q;
-    }
-    return discretize_view(ctx, v, stream);
+    return guarded("hf_discretize_reuse", [&]() -> int {
+        ApiRange range_("hf_discretize_reuse");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!v || v->stage < 1) return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+        if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+        if (prev_slot == slot) return fail(HF_ERR_ARG, "a slot cannot reuse its own texels");
+        const ViewSlot* p = get_view(ctx, prev_slot);
+        if (!p || p->stage < 2) return fail(HF_ERR_STATE, "view slot %d holds no discretized frame", prev_slot);
+        if (v->dev < p->dev + p->bytes && p->dev < v->dev + v->bytes)
+            return fail(HF_ERR_ARG, "view slots %d and %d share buffer memory", slot, prev_slot);
+        const bool same_data = p->data_version == ctx->data_version;
+        for (int k = 0; k < HF_MAX_CASCADES; ++k) {
+            v->reuse[k] = ViewSlot::Reuse();
+            v->fit.cas[k].reuse_source = -1;
+        }
+        for (int k = 0; k < v->cam.n_cascades && same_data; ++k) {
+            ViewSlot::Reuse r;
+            const int q = reuse_source(v, k, p, &r);
+            if (q < 0) continue;
+            v->reuse[k] = r;
+            v->fit.cas[k].reuse_source = q;
+        }
+        return discretize_view(ctx, v, stream);
+    });
 }
 
 int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
-    ApiRange range_("hf_build_maxmip");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
-    const int C = v->cam.n_cascades, N = v->cam.cascade_size;
-    MipParams mp;
-    std::memset(&mp, 0, sizeof(mp));
-    mp.C = C;
-    mp.max_P = mip_pow2(N);
-    mp.max_K = mip_levels(mp.max_P);
-    mp.two = ctx->rbf.water;
-    for (int k = 0; k < C; ++k) {
-        mp.cas[k].tex = v->tex[k];
-        mp.cas[k].wtex = v->wtex[k];
-        mp.cas[k].mip = v->mip[k];
-        mp.cas[k].N = N;
-        mp.cas[k].P = mp.max_P;
-        mp.cas[k].K = mp.max_K;
-    }
-    int e = launch_maxmip(mp, stream);
-    if (e) return cuda_fail(e, "max-mip kernel launch");
-    v->stage = 3;
-    return HF_OK;
+    return guarded("hf_build_maxmip", [&]() -> int {
+        ApiRange range_("hf_build_maxmip");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
+        const int C = v->cam.n_cascades, N = v->cam.cascade_size;
+        MipParams mp;
+        std::memset(&mp, 0, sizeof(mp));
+        mp.C = C;
+        mp.max_P = mip_pow2(N);
+        mp.max_K = mip_levels(mp.max_P);
+        mp.two = ctx->rbf.water;
+        for (int k = 0; k < C; ++k) {
+            mp.cas[k].tex = v->tex[k];
+            mp.cas[k].wtex = v->wtex[k];
+            mp.cas[k].mip = v->mip[k];
+            mp.cas[k].N = N;
+            mp.cas[k].P = mp.max_P;
+            mp.cas[k].K = mp.max_K;
+        }
+        int e = launch_maxmip(mp, stream);
+        if (e) return cuda_fail(e, "max-mip kernel launch");
+        v->stage = 3;
+        return HF_OK;
+    });
 }
 
 namespace {
@@ -983,61 +1018,67 @@ int check_kernel_output(const void* p, const char* what) {
 }  // namespace
 
 int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
-    ApiRange range_("hf_raycast");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
-    if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
-    if (int rc = check_kernel_output(t_dev, "t output")) return rc;
-    if (int rc = check_kernel_output(hit_dev, "hit output")) return rc;
-    RayParams rp = ray_params(v, ctx->rbf.water != 0);
-    rp.t_out = t_dev;
-    rp.hit_out = hit_dev;
-    int e = launch_raycast(rp, ctx->d_status(), stream);
-    if (e) return cuda_fail(e, "ray-cast kernel launch");
-    return HF_OK;
+    return guarded("hf_raycast", [&]() -> int {
+        ApiRange range_("hf_raycast");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
+        if (!t_dev || !hit_dev) return fail(HF_ERR_ARG, "null output buffer");
+        if (int rc = check_kernel_output(t_dev, "t output")) return rc;
+        if (int rc = check_kernel_output(hit_dev, "hit output")) return rc;
+        RayParams rp = ray_params(v, ctx->rbf.water != 0);
+        rp.t_out = t_dev;
+        rp.hit_out = hit_dev;
+        int e = launch_raycast(rp, ctx->d_status(), stream);
+        if (e) return cuda_fail(e, "ray-cast kernel launch");
+        return HF_OK;
+    });
 }
 
 int hf_ray_stats(hf_ctx* ctx, int32_t slot, int64_t* visits, int64_t* patch_tests, void* stream) {
-    ApiRange range_("hf_ray_stats");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!visits || !patch_tests) return fail(HF_ERR_ARG, "null argument");
-    if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
-    cudaStream_t s = cudaStream_t(stream);
-    DevStatus* st = ctx->d_status();
-    int e = cudaMemsetAsync(st->ray_counters, 0, sizeof(st->ray_counters), s);
-    if (!e) e = launch_raycast_count(ray_params(v, ctx->rbf.water != 0), st, stream);
-    if (e) return cuda_fail(e, "ray counting pass launch");
-    unsigned long long c[2];
-    e = cudaMemcpyAsync(c, st->ray_counters, sizeof(c), cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(e, "ray counting pass");
-    *visits = int64_t(c[0]);
-    *patch_tests = int64_t(c[1]);
-    return HF_OK;
+    return guarded("hf_ray_stats", [&]() -> int {
+        ApiRange range_("hf_ray_stats");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!visits || !patch_tests) return fail(HF_ERR_ARG, "null argument");
+        if (!v || v->stage < 3) return fail(HF_ERR_STATE, "view slot %d has no max mipmap", slot);
+        cudaStream_t s = cudaStream_t(stream);
+        DevStatus* st = ctx->d_status();
+        int e = cudaMemsetAsync(st->ray_counters, 0, sizeof(st->ray_counters), s);
+        if (!e) e = launch_raycast_count(ray_params(v, ctx->rbf.water != 0), st, stream);
+        if (e) return cuda_fail(e, "ray counting pass launch");
+        unsigned long long c[2];
+        e = cudaMemcpyAsync(c, st->ray_counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail(e, "ray counting pass");
+        *visits = int64_t(c[0]);
+        *patch_tests = int64_t(c[1]);
+        return HF_OK;
+    });
 }
 
 int hf_view_stats(hf_ctx* ctx, int32_t slot, hf_view_stats_t* out, void* stream) {
-    ApiRange range_("hf_view_stats");
-    ViewSlot* v = get_view(ctx, slot);
-    if (!out) return fail(HF_ERR_ARG, "null argument");
-    if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
-    cudaStream_t s = cudaStream_t(stream);
-    DevStatus* st = ctx->d_status();
-    int e = cudaMemsetAsync(st->counters, 0, sizeof(st->counters), s);
-    if (!e) e = launch_stats(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), st, stream);
-    if (e) return cuda_fail(e, "counting pass launch");
-    unsigned long long c[4 * HF_MAX_CASCADES];
-    e = cudaMemcpyAsync(c, st->counters, sizeof(c), cudaMemcpyDeviceToHost, s);
-    if (!e) e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(e, "counting pass");
-    std::memset(out, 0, sizeof(*out));
-    for (int k = 0; k < v->cam.n_cascades; ++k) {
-        out->visible_texels[k] = int64_t(c[k]);
-        out->candidates[k] = int64_t(c[HF_MAX_CASCADES + k]);
-        out->influencers[k] = int64_t(c[2 * HF_MAX_CASCADES + k]);
-        out->reused_texels[k] = int64_t(c[3 * HF_MAX_CASCADES + k]);
-    }
-    return HF_OK;
+    return guarded("hf_view_stats", [&]() -> int {
+        ApiRange range_("hf_view_stats");
+        ViewSlot* v = get_view(ctx, slot);
+        if (!out) return fail(HF_ERR_ARG, "null argument");
+        if (!v || v->stage < 2) return fail(HF_ERR_STATE, "view slot %d is not discretized", slot);
+        cudaStream_t s = cudaStream_t(stream);
+        DevStatus* st = ctx->d_status();
+        int e = cudaMemsetAsync(st->counters, 0, sizeof(st->counters), s);
+        if (!e) e = launch_stats(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), st, stream);
+        if (e) return cuda_fail(e, "counting pass launch");
+        unsigned long long c[4 * HF_MAX_CASCADES];
+        e = cudaMemcpyAsync(c, st->counters, sizeof(c), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail(e, "counting pass");
+        std::memset(out, 0, sizeof(*out));
+        for (int k = 0; k < v->cam.n_cascades; ++k) {
+            out->visible_texels[k] = int64_t(c[k]);
+            out->candidates[k] = int64_t(c[HF_MAX_CASCADES + k]);
+            out->influencers[k] = int64_t(c[2 * HF_MAX_CASCADES + k]);
+            out->reused_texels[k] = int64_t(c[3 * HF_MAX_CASCADES + k]);
+        }
+        return HF_OK;
+    });
 }
 
 namespace {
@@ -1077,199 +1118,215 @@ int g_persistent_blocks[64][2] = {};
 
 int hf_batch_query_bytes(const hf_batch_item* items, int32_t n, int32_t flags, size_t* device_bytes,
                          size_t* host_bytes) {
-    (void)flags;
-    BatchPlan plan;
-    int rc = plan_batch(items, n, &plan);
-    if (rc) return rc;
-    if (device_bytes) *device_bytes = plan.total;
-    if (host_bytes) *host_bytes = plan.counters_off;
-    return HF_OK;
+    return guarded("hf_batch_query_bytes", [&]() -> int {
+        (void)flags;
+        BatchPlan plan;
+        int rc = plan_batch(items, n, &plan);
+        if (rc) return rc;
+        if (device_bytes) *device_bytes = plan.total;
+        if (host_bytes) *host_bytes = plan.counters_off;
+        return HF_OK;
+    });
 }
 
 int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes) {
-    ApiRange range_("hf_batch_prepare");
-    BatchPlan plan;
-    int rc = plan_batch(items, n, &plan);
-    if (rc) return rc;
-    if (!host_buf) return fail(HF_ERR_ARG, "null host buffer");
-    if (host_bytes < plan.counters_off)
-        return fail(HF_ERR_NOMEM, "batch host buffer has %zu bytes, %zu needed", host_bytes, plan.counters_off);
-    if (flags & ~int32_t(kBatchRaysInside | kBatchRayTileMask | kBatchWarp16x2 | kBatchPersistent))
-        return fail(HF_ERR_ARG, "unknown batch flags");
-    if ((flags & kBatchRaysInside) && !(flags & kBatchPersistent))
-        return fail(HF_ERR_ARG, "HF_BATCH_RAYS_INSIDE needs HF_BATCH_PERSISTENT");
-    if (((flags & kBatchRayTileMask) >> 1) == 3) return fail(HF_ERR_ARG, "choose one ray tile shape");
-    for (int32_t i = 0; i < n; ++i) {
-        if (int rc2 = check_kernel_output(items[i].t_dev, "batch item t output")) return rc2;
-        if (int rc2 = check_kernel_output(items[i].hit_dev, "batch item hit output")) return rc2;
-    }
-    int dev = 0;
-    int e = cudaGetDevice(&dev);
-    if (e) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(HF_ERR_ARG, "device index %d", dev);
-    if (!g_persistent_blocks[dev][0]) {
-        e = batch_persistent_blocks(&g_persistent_blocks[dev][0], &g_persistent_blocks[dev][1]);
-        if (e) return cuda_fail(e, "occupancy query");
-    }
-    char* hb = static_cast<char*>(host_buf);
-    std::memset(hb, 0, plan.counters_off);
-    BatchHeader& h = *reinterpret_cast<BatchHeader*>(hb);
-    BatchItem* bi = reinterpret_cast<BatchItem*>(hb + plan.items_off);
-    BatchCascade* bc = reinterpret_cast<BatchCascade*>(hb + plan.cascades_off);
-    h.n_items = n;
-    h.n_cascades = plan.n_cascades;
-    h.flags = flags;
-    const int shape = (flags & kBatchRayTileMask) >> 1;
-    h.ray_tile_w = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
-    h.ray_tile_h = 256 / h.ray_tile_w;
-    h.persistent_blocks = g_persistent_blocks[dev][0];
-    h.persistent_blocks_rays = g_persistent_blocks[dev][1];
-    h.items_off = int64_t(plan.items_off);
-    h.cascades_off = int64_t(plan.cascades_off);
-    h.counters_off = int64_t(plan.counters_off);
-    h.desc_bytes = int64_t(plan.counters_off);
-    h.total_bytes = int64_t(plan.total);
-    int kc = 0, units[kPhases] = {0, 0, 0, 0, 0};
-    for (int32_t i = 0; i < n; ++i) {
-        hf_ctx* ctx = items[i].ctx;
-        ViewSlot* v = get_view(ctx, items[i].view_slot);
-        const int C = v->cam.n_cascades, N = v->cam.cascade_size, P = mip_pow2(N);
-        BatchItem& I = bi[i];
-        I.ray = ray_params(v, false);
-        I.ray.t_out = items[i].t_dev;
-        I.ray.hit_out = items[i].hit_dev;
-        I.lt = ctx->lookup_tables(true);
-        I.lv = ctx->lists();
-        if (ctx->rbf.precision != HF_PREC_FP32) I.cv = ctx->compact();
-        I.status = ctx->d_status();
-        I.dom_w = ctx->width;
-        I.dom_h = ctx->height;
-        I.eps_frac = 1e-6;
-        for (int k = 0; k < HF_MAX_CASCADES; ++k) {  // batched frames compute every texel
-            v->reuse[k] = ViewSlot::Reuse();
-            v->fit.cas[k].reuse_source = -1;
+    return guarded("hf_batch_prepare", [&]() -> int {
+        ApiRange range_("hf_batch_prepare");
+        BatchPlan plan;
+        int rc = plan_batch(items, n, &plan);
+        if (rc) return rc;
+        if (!host_buf) return fail(HF_ERR_ARG, "null host buffer");
+        if (host_bytes < plan.counters_off)
+            return fail(HF_ERR_NOMEM, "batch host buffer has %zu bytes, %zu needed", host_bytes, plan.counters_off);
+        if (flags & ~int32_t(kBatchRaysInside | kBatchRayTileMask | kBatchWarp16x2 | kBatchPersistent))
+            return fail(HF_ERR_ARG, "unknown batch flags");
+        if ((flags & kBatchRaysInside) && !(flags & kBatchPersistent))
+            return fail(HF_ERR_ARG, "HF_BATCH_RAYS_INSIDE needs HF_BATCH_PERSISTENT");
+        if (((flags & kBatchRayTileMask) >> 1) == 3) return fail(HF_ERR_ARG, "choose one ray tile shape");
+        for (int32_t i = 0; i < n; ++i) {
+            if (int rc2 = check_kernel_output(items[i].t_dev, "batch item t output")) return rc2;
+            if (int rc2 = check_kernel_output(items[i].hit_dev, "batch item hit output")) return rc2;
         }
-        const DiscParams dp = disc_params(ctx, v);
-        I.K = dp.K;
-        I.precision = ctx->rbf.precision;
-        I.first_cascade = kc;
-        I.n_cascades = C;
-        I.ray_tiles_x = (v->cam.width + h.ray_tile_w - 1) / h.ray_tile_w;
-        I.ray_units = I.ray_tiles_x * ((v->cam.height + h.ray_tile_h - 1) / h.ray_tile_h);
-        I.ray_unit_base = units[kPhaseRays];
-        units[kPhaseRays] += I.ray_units;
-        for (int k = 0; k < C; ++k, ++kc) {
-            BatchCascade& B = bc[kc];
-            fill_prep_cascade(v, k, B.prep);
-            B.disc = dp.cas[k];
-            B.mip.tex = v->tex[k];
-            B.mip.mip = v->mip[k];
-            B.mip.N = N;
-            B.mip.P = P;
-            B.mip.K = mip_levels(P);
-            B.item = i;
-            B.tiles_x = (N + 31) / 32;
-            B.mip_blocks_x = (P + 63) / 64;
-            B.n_units[kPhaseRows] = (N + 255) / 256;
-            h.max_rows_units = std::max(h.max_rows_units, B.n_units[kPhaseRows]);
-            B.n_units[kPhaseTexels] = B.tiles_x * ((N + 7) / 8);
-            B.n_units[kPhaseMipLo] = B.mip_blocks_x * B.mip_blocks_x;
-            B.n_units[kPhaseMipHi] = 1;
-            for (int ph = 0; ph < 4; ++ph) {
-                B.unit_base[ph] = units[ph];
-                units[ph] += B.n_units[ph];
+        int dev = 0;
+        int e = cudaGetDevice(&dev);
+        if (e) return cuda_fail(e, "cudaGetDevice");
+        if (dev < 0 || dev >= 64) return fail(HF_ERR_ARG, "device index %d", dev);
+        if (!g_persistent_blocks[dev][0]) {
+            e = batch_persistent_blocks(&g_persistent_blocks[dev][0], &g_persistent_blocks[dev][1]);
+            if (e) return cuda_fail(e, "occupancy query");
+        }
+        char* hb = static_cast<char*>(host_buf);
+        std::memset(hb, 0, plan.counters_off);
+        BatchHeader& h = *reinterpret_cast<BatchHeader*>(hb);
+        BatchItem* bi = reinterpret_cast<BatchItem*>(hb + plan.items_off);
+        BatchCascade* bc = reinterpret_cast<BatchCascade*>(hb + plan.cascades_off);
+        h.n_items = n;
+        h.n_cascades = plan.n_cascades;
+        h.flags = flags;
+        const int shape = (flags & kBatchRayTileMask) >> 1;
+        h.ray_tile_w = shape == 1 ? 32 : (shape == 2 ? 8 : 16);
+        h.ray_tile_h = 256 / h.ray_tile_w;
+        h.persistent_blocks = g_persistent_blocks[dev][0];
+        h.persistent_blocks_rays = g_persistent_blocks[dev][1];
+        h.items_off = int64_t(plan.items_off);
+        h.cascades_off = int64_t(plan.cascades_off);
+        h.counters_off = int64_t(plan.counters_off);
+        h.desc_bytes = int64_t(plan.counters_off);
+        h.total_bytes = int64_t(plan.total);
+        int kc = 0, units[kPhases] = {0, 0, 0, 0, 0};
+        for (int32_t i = 0; i < n; ++i) {
+            hf_ctx* ctx = items[i].ctx;
+            ViewSlot* v = get_view(ctx, items[i].view_slot);
+            const int C = v->cam.n_cascades, N = v->cam.cascade_size, P = mip_pow2(N);
+            BatchItem& I = bi[i];
+            I.ray = ray_params(v, false);
+            I.ray.t_out = items[i].t_dev;
+            I.ray.hit_out = items[i].hit_dev;
+            I.lt = ctx->lookup_tables(true);
+            I.lv = ctx->lists();
+            if (ctx->rbf.precision != HF_PREC_FP32) I.cv = ctx->compact();
+            I.status = ctx->d_status();
+            I.dom_w = ctx->width;
+            I.dom_h = ctx->height;
+            I.eps_frac = 1e-6;
+            for (int k = 0; k < HF_MAX_CASCADES; ++k) {  // batched frames compute every texel
+                v->reuse[k] = ViewSlot::Reuse();
+                v->fit.cas[k].reuse_source = -1;
             }
+            const DiscParams dp = disc_params(ctx, v);
+            I.K = dp.K;
+            I.precision = ctx->rbf.precision;
+            I.first_cascade = kc;
+            I.n_cascades = C;
+            I.ray_tiles_x = (v->cam.width + h.ray_tile_w - 1) / h.ray_tile_w;
+            I.ray_units = I.ray_tiles_x * ((v->cam.height + h.ray_tile_h - 1) / h.ray_tile_h);
+            I.ray_unit_base = units[kPhaseRays];
+            units[kPhaseRays] += I.ray_units;
+            for (int k = 0; k < C; ++k, ++kc) {
+                BatchCascade& B = bc[kc];
+                fill_prep_cascade(v, k, B.prep);
+                B.disc = dp.cas[k];
+                B.mip.tex = v->tex[k];
+                B.mip.mip = v->mip[k];
+                B.mip.N = N;
+                B.mip.P = P;
+                B.mip.K = mip_levels(P);
+                B.item = i;
+                B.tiles_x = (N + 31) / 32;
+                B.mip_blocks_x = (P + 63) / 64;
+                B.n_units[kPhaseRows] = (N + 255) / 256;
+                h.max_rows_units = std::max(h.max_rows_units, B.n_units[kPhaseRows]);
+                B.n_units[kPhaseTexels] = B.tiles_x * ((N + 7) / 8);
+                B.n_units[kPhaseMipLo] = B.mip_blocks_x * B.mip_blocks_x;
+                B.n_units[kPhaseMipHi] = 1;
+                for (int ph = 0; ph < 4; ++ph) {
+                    B.unit_base[ph] = units[ph];
+                    units[ph] += B.n_units[ph];
+                }
+            }
+            v->stage = 3;
+            v->data_version = ctx->data_version;
         }
-        v->stage = 3;
-        v->data_version = ctx->data_version;
-    }
-    // global unit numbering: phase after phase
-    int base = 0;
-    for (int ph = 0; ph < kPhases; ++ph) {
-        h.phase_base[ph] = base;
-        base += units[ph];
-    }
-    h.phase_base[kPhases] = base;
-    for (int k = 0; k < plan.n_cascades; ++k)
-        for (int ph = 0; ph < 4; ++ph) bc[k].unit_base[ph] += h.phase_base[ph];
-    return HF_OK;
+        // global unit numbering: phase after phase
+        int base = 0;
+        for (int ph = 0; ph < kPhases; ++ph) {
+            h.phase_base[ph] = base;
+            base += units[ph];
+        }
+        h.phase_base[kPhases] = base;
+        for (int k = 0; k < plan.n_cascades; ++k)
+            for (int ph = 0; ph < 4; ++ph) bc[k].unit_base[ph] += h.phase_base[ph];
+        return HF_OK;
+    });
 }
 
 int hf_batch_launch(const void* host_buf, void* dev_buf, size_t dev_bytes, void* stream) {
-    ApiRange range_("hf_batch_launch");
-    if (!host_buf || !dev_buf) return fail(HF_ERR_ARG, "null buffer");
-    if (reinterpret_cast<uintptr_t>(dev_buf) & 255) return fail(HF_ERR_ARG, "device buffer must be 256-byte aligned");
-    const BatchHeader& h = *static_cast<const BatchHeader*>(host_buf);
-    if (h.n_items < 1 || h.total_bytes <= 0) return fail(HF_ERR_ARG, "host buffer holds no prepared batch");
-    if (dev_bytes < size_t(h.total_bytes))
-        return fail(HF_ERR_NOMEM, "batch device buffer has %zu bytes, %lld needed", dev_bytes, (long long)h.total_bytes);
-    cudaStream_t s = cudaStream_t(stream);
-    char* db = static_cast<char*>(dev_buf);
-    int e = cudaMemcpyAsync(db, host_buf, size_t(h.desc_bytes), cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemsetAsync(db + h.counters_off, 0, size_t(h.total_bytes - h.counters_off), s);
-    if (e) return cuda_fail(e, "batch descriptor upload");
-    e = launch_batch(h, dev_buf, stream);
-    if (e) return cuda_fail(e, "batch kernel launch");
-    return HF_OK;
+    return guarded("hf_batch_launch", [&]() -> int {
+        ApiRange range_("hf_batch_launch");
+        if (!host_buf || !dev_buf) return fail(HF_ERR_ARG, "null buffer");
+        if (reinterpret_cast<uintptr_t>(dev_buf) & 255) return fail(HF_ERR_ARG, "device buffer must be 256-byte aligned");
+        const BatchHeader& h = *static_cast<const BatchHeader*>(host_buf);
+        if (h.n_items < 1 || h.total_bytes <= 0) return fail(HF_ERR_ARG, "host buffer holds no prepared batch");
+        if (dev_bytes < size_t(h.total_bytes))
+            return fail(HF_ERR_NOMEM, "batch device buffer has %zu bytes, %lld needed", dev_bytes, (long long)h.total_bytes);
+        cudaStream_t s = cudaStream_t(stream);
+        char* db = static_cast<char*>(dev_buf);
+        int e = cudaMemcpyAsync(db, host_buf, size_t(h.desc_bytes), cudaMemcpyHostToDevice, s);
+        if (!e) e = cudaMemsetAsync(db + h.counters_off, 0, size_t(h.total_bytes - h.counters_off), s);
+        if (e) return cuda_fail(e, "batch descriptor upload");
+        e = launch_batch(h, dev_buf, stream);
+        if (e) return cuda_fail(e, "batch kernel launch");
+        return HF_OK;
+    });
 }
 
 int hf_frame_batch(const hf_batch_item* items, int32_t n, int32_t flags, void* host_buf, size_t host_bytes,
                    void* dev_buf, size_t dev_bytes, void* stream) {
-    ApiRange range_("hf_frame_batch");
-    int rc = hf_batch_prepare(items, n, flags, host_buf, host_bytes);
-    if (rc) return rc;
-    return hf_batch_launch(host_buf, dev_buf, dev_bytes, stream);
+    return guarded("hf_frame_batch", [&]() -> int {
+        ApiRange range_("hf_frame_batch");
+        int rc = hf_batch_prepare(items, n, flags, host_buf, host_bytes);
+        if (rc) return rc;
+        return hf_batch_launch(host_buf, dev_buf, dev_bytes, stream);
+    });
 }
 
 int hf_get_cascade(const hf_ctx* ctx, int32_t slot, int32_t c, hf_cascade_info* out) {
-    if (!ctx || !out) return fail(HF_ERR_ARG, "null argument");
-    if (slot < 0 || slot >= HF_MAX_VIEWS || !ctx->views[slot] || ctx->views[slot]->stage < 1)
-        return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
-    const ViewSlot& v = *ctx->views[slot];
-    if (c < 0 || c >= v.cam.n_cascades) return fail(HF_ERR_ARG, "cascade %d out of range", c);
-    *out = v.fit.cas[c];
-    return HF_OK;
+    return guarded("hf_get_cascade", [&]() -> int {
+        if (!ctx || !out) return fail(HF_ERR_ARG, "null argument");
+        if (slot < 0 || slot >= HF_MAX_VIEWS || !ctx->views[slot] || ctx->views[slot]->stage < 1)
+            return fail(HF_ERR_STATE, "view slot %d has no camera", slot);
+        const ViewSlot& v = *ctx->views[slot];
+        if (c < 0 || c >= v.cam.n_cascades) return fail(HF_ERR_ARG, "cascade %d out of range", c);
+        *out = v.fit.cas[c];
+        return HF_OK;
+    });
 }
 
 int hf_sync(hf_ctx* ctx, void* stream) {
-    ApiRange range_("hf_sync");
-    if (!ctx) return fail(HF_ERR_ARG, "null context");
-    int e = cudaStreamSynchronize(cudaStream_t(stream));
-    if (e) return cuda_fail(e, "stream synchronize");
-    e = cudaGetLastError();
-    if (e) return cuda_fail(e, "pending CUDA error");
-    if (!ctx->dev) return HF_OK;
-    DevStatus st;
-    e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
-    if (e) return cuda_fail(e, "status read-back");
-    if (st.flags) {
-        e = cudaMemset(ctx->d_status(), 0, 8);
-        if (e) return cuda_fail(e, "status reset");
-        if (st.flags & kStatusTimeout)
-            return fail(HF_ERR_TIMEOUT, "a bounded device loop gave up (a ray walk over its step budget or a "
-                        "batch wait over its poll limit; detail %u)", st.detail);
-        return fail(HF_ERR_DATA, "device consistency check failed (item %u)", st.detail);
-    }
-    return HF_OK;
+    return guarded("hf_sync", [&]() -> int {
+        ApiRange range_("hf_sync");
+        if (!ctx) return fail(HF_ERR_ARG, "null context");
+        int e = cudaStreamSynchronize(cudaStream_t(stream));
+        if (e) return cuda_fail(e, "stream synchronize");
+        e = cudaGetLastError();
+        if (e) return cuda_fail(e, "pending CUDA error");
+        if (!ctx->dev) return HF_OK;
+        DevStatus st;
+        e = cudaMemcpy(&st, ctx->d_status(), 8, cudaMemcpyDeviceToHost);
+        if (e) return cuda_fail(e, "status read-back");
+        if (st.flags) {
+            e = cudaMemset(ctx->d_status(), 0, 8);
+            if (e) return cuda_fail(e, "status reset");
+            if (st.flags & kStatusTimeout)
+                return fail(HF_ERR_TIMEOUT, "a bounded device loop gave up (a ray walk over its step budget or a "
+                            "batch wait over its poll limit; detail %u)", st.detail);
+            return fail(HF_ERR_DATA, "device consistency check failed (item %u)", st.detail);
+        }
+        return HF_OK;
+    });
 }
 
 int hf_selftest_wait_timeout(hf_ctx* ctx, int32_t polls, void* stream) {
-    if (!ctx) return fail(HF_ERR_ARG, "null context");
-    if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
-    if (polls < 1 || polls > (1 << 20)) return fail(HF_ERR_ARG, "polls must be 1..2^20");
-    int e = launch_selftest_wait(ctx->d_status(), polls, stream);
-    if (e) return cuda_fail(e, "self-test launch");
-    return HF_OK;
+    return guarded("hf_selftest_wait_timeout", [&]() -> int {
+        if (!ctx) return fail(HF_ERR_ARG, "null context");
+        if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
+        if (polls < 1 || polls > (1 << 20)) return fail(HF_ERR_ARG, "polls must be 1..2^20");
+        int e = launch_selftest_wait(ctx->d_status(), polls, stream);
+        if (e) return cuda_fail(e, "self-test launch");
+        return HF_OK;
+    });
 }
 
 int hf_measure_unit_rates(double* ex2_per_s, double* ffma_per_s, int32_t* sm_count, void* stream) {
-    ApiRange range_("hf_measure_unit_rates");
-    if (!ex2_per_s || !ffma_per_s || !sm_count) return fail(HF_ERR_ARG, "null argument");
-    int sms = 0;
-    int e = measure_unit_rates(ex2_per_s, ffma_per_s, &sms, stream);
-    if (e) return cuda_fail(e, "unit-rate kernels");
-    *sm_count = sms;
-    return HF_OK;
+    return guarded("hf_measure_unit_rates", [&]() -> int {
+        ApiRange range_("hf_measure_unit_rates");
+        if (!ex2_per_s || !ffma_per_s || !sm_count) return fail(HF_ERR_ARG, "null argument");
+        int sms = 0;
+        int e = measure_unit_rates(ex2_per_s, ffma_per_s, &sms, stream);
+        if (e) return cuda_fail(e, "unit-rate kernels");
+        *sm_count = sms;
+        return HF_OK;
+    });
 }
 
 void hf_destroy(hf_ctx* ctx) { delete ctx; }

@@ -251,6 +251,22 @@ int noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* t
 // Records a CUDA failure as the calling thread's last error; returns HF_ERR_CUDA.
 int set_cuda_error(int e, const char* what);
 
+// Status of the exception being handled (called from a catch block only):
+// HF_ERR_HOST with its description.
+int exception_status(const char* where) noexcept;
+
+// Runs an entry point's body and turns any C++ exception it throws (host
+// allocation, thread creation) into HF_ERR_HOST, so that none crosses the
+// C ABI.
+template <class F>
+int guarded(const char* where, F&& body) noexcept {
+    try {
+        return body();
+    } catch (...) {
+        return exception_status(where);
+    }
+}
+
 // Host-side count of each bucket's candidates (same enumeration as the fill
 // kernel, in exact integer arithmetic).  Bitmaps must hold host pointers.
 void count_lists_host(const EnumTables& et, const LookupTables& lt, int64_t* counts,

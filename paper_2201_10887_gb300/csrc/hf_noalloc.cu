@@ -40,22 +40,24 @@ int scratch_on_current_device(char** out) {
 
 extern "C" int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* const* tex_out,
                                      hf_cascade_info* info_out, void* stream) {
-    char* scratch = nullptr;
-    int rc = scratch_on_current_device(&scratch);
-    if (rc != HF_OK) return rc;
-    hfi::PrepParams pp;
-    hfi::DiscParams dp;
-    hfi::LookupTables lt;
-    hfi::ListsView lv;
-    hfi::DevStatus* status = nullptr;
-    rc = hfi::noalloc_discretize_params(ctx, cam, tex_out, scratch, HF_NOALLOC_SCRATCH_BYTES, info_out,
-                                        &pp, &dp, &lt, &lv, &status);
-    if (rc != HF_OK) return rc;
-    // every span and coordinate read below is written first on the same
-    // stream, so nothing in the scratch needs clearing between calls
-    int e = hfi::launch_prep(pp, stream);
-    if (e != cudaSuccess) return hfi::set_cuda_error(e, "visible-row kernel launch (allocation-free path)");
-    e = hfi::launch_discretize(dp, lt, lv, status, stream);
-    if (e != cudaSuccess) return hfi::set_cuda_error(e, "discretization kernel launch (allocation-free path)");
-    return HF_OK;
+    return hfi::guarded("hf_discretize_noalloc", [&]() -> int {
+        char* scratch = nullptr;
+        int rc = scratch_on_current_device(&scratch);
+        if (rc != HF_OK) return rc;
+        hfi::PrepParams pp;
+        hfi::DiscParams dp;
+        hfi::LookupTables lt;
+        hfi::ListsView lv;
+        hfi::DevStatus* status = nullptr;
+        rc = hfi::noalloc_discretize_params(ctx, cam, tex_out, scratch, HF_NOALLOC_SCRATCH_BYTES, info_out,
+                                            &pp, &dp, &lt, &lv, &status);
+        if (rc != HF_OK) return rc;
+        // every span and coordinate read below is written first on the same
+        // stream, so nothing in the scratch needs clearing between calls
+        int e = hfi::launch_prep(pp, stream);
+        if (e != cudaSuccess) return hfi::set_cuda_error(e, "visible-row kernel launch (allocation-free path)");
+        e = hfi::launch_discretize(dp, lt, lv, status, stream);
+        if (e != cudaSuccess) return hfi::set_cuda_error(e, "discretization kernel launch (allocation-free path)");
+        return HF_OK;
+    });
 }

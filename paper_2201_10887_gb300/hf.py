@@ -15,13 +15,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhf.so")
 
-HF_OK, HF_ERR_ARG, HF_ERR_STATE, HF_ERR_NOMEM, HF_ERR_CUDA, HF_ERR_TIMEOUT, HF_ERR_DATA = 0, -1, -2, -3, -4, -5, -6
+HF_OK, HF_ERR_ARG, HF_ERR_STATE, HF_ERR_NOMEM, HF_ERR_CUDA, HF_ERR_TIMEOUT, HF_ERR_DATA, HF_ERR_HOST = 0, -1, -2, -3, -4, -5, -6, -7
 HF_PREC_FP32, HF_PREC_FP16, HF_PREC_BF16 = 0, 1, 2
 HF_RBF_GAUSSIAN, HF_RBF_WENDLAND_C2 = 0, 1
 HF_MAX_LEVEL, HF_MAX_CASCADES, HF_MAX_POLY, HF_MAX_VIEWS = 15, 8, 32, 256
 
 ERROR_NAMES = {HF_ERR_ARG: "HF_ERR_ARG", HF_ERR_STATE: "HF_ERR_STATE", HF_ERR_NOMEM: "HF_ERR_NOMEM",
-               HF_ERR_CUDA: "HF_ERR_CUDA", HF_ERR_TIMEOUT: "HF_ERR_TIMEOUT", HF_ERR_DATA: "HF_ERR_DATA"}
+               HF_ERR_CUDA: "HF_ERR_CUDA", HF_ERR_TIMEOUT: "HF_ERR_TIMEOUT", HF_ERR_DATA: "HF_ERR_DATA",
+               HF_ERR_HOST: "HF_ERR_HOST"}
 
 LEAF_DTYPE = np.dtype([("level", "<i4"), ("ix", "<i4"), ("iy", "<i4"), ("value", "<f4")])
 

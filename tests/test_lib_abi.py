@@ -346,3 +346,37 @@ def test_fit_follow_against_oracle(hfmod, orc, tiny):
         assert lib.hf_set_camera_follow(ctx, 2, ct.byref(camera_struct(a)), ct.c_void_p(1 << 30),
                                         ct.c_size_t(1 << 30), bad_prev) == hfmod.HF_ERR_STATE
     hfmod.hf_destroy(ctx)
+
+
+_HOST_FAILURE_SCRIPT = r"""
+import resource, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2201_10887_gb300 import hf
+n = 1024
+iy, ix = np.divmod(np.arange(n * n, dtype=np.int64), n)
+lv = hf.leaves_array(np.zeros(n * n, np.int32), ix.astype(np.int32), iy.astype(np.int32), np.zeros(n * n, np.float32))
+desc = hf.hf_quadtree_desc(0.0, 0.0, 10.0, n, n, 0)
+rbf = hf.hf_rbf_params(1.5, 3.0, 0, -1)
+vm = [int(l.split()[1]) * 1024 for l in open("/proc/self/status") if l.startswith("VmSize:")][0]
+resource.setrlimit(resource.RLIMIT_AS, (vm + (8 << 20), resource.getrlimit(resource.RLIMIT_AS)[1]))
+try:
+    hf.hf_create_quadtree(desc, lv, rbf)
+    print("created")
+except hf.HFError as e:
+    print("code", e.code, str(e)[:120])
+"""
+
+
+def test_host_failure_is_a_status_not_an_exception(hfmod):
+    """A host allocation that fails inside an entry point (here: the
+    library's tables for a million leaves under an address-space limit a few
+    megabytes above the process's size) comes back as HF_ERR_HOST with a
+    message; no C++ exception crosses the C ABI, so the process goes on."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _HOST_FAILURE_SCRIPT, ROOT], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.startswith("code %d" % hfmod.HF_ERR_HOST), r.stdout
+    assert "hf_create_quadtree" in r.stdout

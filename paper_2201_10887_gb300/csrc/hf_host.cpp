@@ -409,6 +409,8 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         ApiRange range_("hf_create_quadtree");
         if (!desc || !rbf || !out) return fail(HF_ERR_ARG, "null argument");
         if (n_leaves < 1 || !leaves) return fail(HF_ERR_ARG, "no leaves");
+        if (n_leaves > std::numeric_limits<int32_t>::max())  // list entries are 32-bit leaf indices
+            return fail(HF_ERR_ARG, "more than 2^31 - 1 leaves");
         const hf_quadtree_desc& d = *desc;
         if (!(std::isfinite(d.origin_x) && std::isfinite(d.origin_y) && std::isfinite(d.root_cell) &&
               d.root_cell > 0.0))

@@ -380,3 +380,18 @@ def test_host_failure_is_a_status_not_an_exception(hfmod):
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.startswith("code %d" % hfmod.HF_ERR_HOST), r.stdout
     assert "hf_create_quadtree" in r.stdout
+
+
+def test_leaf_count_limit(hfmod, tiny):
+    """List entries are 32-bit leaf indices: a count of 2^31 leaves is
+    refused before the leaf array is read."""
+    t = tiny.tree
+    lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
+    desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    rbf = hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1)
+    lib = ct.CDLL(hfmod.LIB_PATH)
+    lib.hf_last_error.restype = ct.c_char_p
+    ctx = ct.c_void_p()
+    rc = lib.hf_create_quadtree(ct.byref(desc), lv.ctypes.data_as(ct.c_void_p), ct.c_int64(2 ** 31),
+                                ct.byref(rbf), ct.byref(ctx))
+    assert rc == hfmod.HF_ERR_ARG and b"2^31" in lib.hf_last_error() and not ctx.value

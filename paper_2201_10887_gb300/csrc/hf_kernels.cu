@@ -1359,6 +1359,16 @@ union BatchShared {
     int off[HF_MAX_CASCADES][kMaxLevels];
 };
 
+// Word-wise copy of a descriptor by the whole CTA (the structs are plain data
+// of whole 4-byte words).
+template <class T>
+__device__ __forceinline__ void cta_copy(T* dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "descriptor size must be whole words");
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int w = threadIdx.x; w < int(sizeof(T) / 4); w += blockDim.x) d[w] = s[w];
+}
+
 template <bool COH>
 __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const BatchItem* items, const BatchCascade* cas,
                                                const uint32_t* done, int u, int (*off)[kMaxLevels]) {
@@ -1368,17 +1378,23 @@ __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const Batch
         for (int c = 0; c < I.n_cascades; ++c)
             wait_count(done + 4 * (I.first_cascade + c) + kPhaseMipHi, 1u, I.status, uint32_t(u));
     }
-    load_level_offsets<COH>(I.ray, off, threadIdx.x, blockDim.x);
+    // the item's ray parameters, staged once per unit: the walk then reads
+    // them from shared memory rather than through the descriptor buffer
+    __shared__ RayParams s_ray;
+    __syncthreads();  // the previous unit of this CTA is done with s_ray and off
+    cta_copy(&s_ray, &I.ray);
+    __syncthreads();
+    load_level_offsets<COH>(s_ray, off, threadIdx.x, blockDim.x);
     __syncthreads();
     const int local = u - h->phase_base[kPhaseRays] - I.ray_unit_base;
     const int tw = h->ray_tile_w, th = h->ray_tile_h;
     const int x = (local % I.ray_tiles_x) * tw + int(threadIdx.x) % tw;
     const int y = (local / I.ray_tiles_x) * th + int(threadIdx.x) / tw;
     unsigned visits = 0, tests = 0;
-    if (I.ray.coarse)
-        raycast_pixel<false, COH, false, true>(I.ray, off, I.status, x, y, visits, tests);
+    if (s_ray.coarse)
+        raycast_pixel<false, COH, false, true>(s_ray, off, I.status, x, y, visits, tests);
     else
-        raycast_pixel<false, COH>(I.ray, off, I.status, x, y, visits, tests);
+        raycast_pixel<false, COH>(s_ray, off, I.status, x, y, visits, tests);
 }
 
 // Units are taken in chunks of kChunk; completions of consecutive units of
@@ -1538,6 +1554,9 @@ __global__ void __launch_bounds__(128) k_bat_rows(const uint8_t* __restrict__ bu
     if (t < C.prep.N) prep_row(C.prep, I.dom_w, I.dom_h, I.eps_frac, t);
 }
 
+// The CTA's cascade, its item's tables and the tile origin are looked up
+// once and staged in shared memory; the texel code then reads them from
+// there (uniform across the CTA) instead of through the descriptor buffer.
 __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict__ buf) {
     wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
@@ -1545,16 +1564,28 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
     __shared__ LookupTables s_lt;
     __shared__ DiscCascade s_disc;
-    const int u = h->phase_base[kPhaseTexels] + int(blockIdx.x);
-    const int k = find_cascade(cas, h->n_cascades, kPhaseTexels, u);
-    const BatchCascade& C = cas[k];
-    const BatchItem& I = items[C.item];
+    __shared__ ListsView s_lv;
+    __shared__ CompactView s_cv;
+    __shared__ int s_k, s_i0, s_j0;
     if (threadIdx.x == 0) {
-        s_lt = I.lt;
-        s_disc = C.disc;
+        const int u = h->phase_base[kPhaseTexels] + int(blockIdx.x);
+        const int k = find_cascade(cas, h->n_cascades, kPhaseTexels, u);
+        const int local = u - cas[k].unit_base[kPhaseTexels], tx = cas[k].tiles_x;
+        s_k = k;
+        s_i0 = (local % tx) * 32;
+        s_j0 = (local / tx) * 8;
     }
     __syncthreads();
-    const int local = u - C.unit_base[kPhaseTexels];
+    const BatchCascade& C = cas[s_k];
+    const BatchItem& I = items[C.item];
+    cta_copy(&s_lt, &I.lt);
+    cta_copy(&s_disc, &C.disc);
+    cta_copy(&s_lv, &I.lv);
+    cta_copy(&s_cv, &I.cv);
+    const float K = I.K;
+    const int precision = I.precision;
+    DevStatus* const status = I.status;
+    __syncthreads();
     int di, dj;
     if (h->flags & kBatchWarp16x2) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1563,13 +1594,13 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
     } else {
         tile_texel(threadIdx.x, di, dj);
     }
-    const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
-    if (I.precision == HF_PREC_FP32)
-        discretize_texel<false>(s_disc, I.K, s_lt, I.lv, I.status, i, j);
-    else if (I.precision == HF_PREC_FP16)
-        discretize_texel_mixed<F16Ops, false>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+    const int i = s_i0 + di, j = s_j0 + dj;
+    if (precision == HF_PREC_FP32)
+        discretize_texel<false>(s_disc, K, s_lt, s_lv, status, i, j);
+    else if (precision == HF_PREC_FP16)
+        discretize_texel_mixed<F16Ops, false>(s_disc, K, s_lt, s_cv, status, i, j);
     else
-        discretize_texel_mixed<BF16Ops, false>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+        discretize_texel_mixed<BF16Ops, false>(s_disc, K, s_lt, s_cv, status, i, j);
 }
 
 __global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ buf) {
@@ -1577,11 +1608,20 @@ __global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ b
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
     const BatchCascade* cas = reinterpret_cast<const BatchCascade*>(buf + h->cascades_off);
     __shared__ float sm[16][17];
-    const int u = h->phase_base[kPhaseMipLo] + int(blockIdx.x);
-    const int k = find_cascade(cas, h->n_cascades, kPhaseMipLo, u);
-    const BatchCascade& C = cas[k];
-    const int local = u - C.unit_base[kPhaseMipLo];
-    mip_lo_block<false>(C.mip, local % C.mip_blocks_x, local / C.mip_blocks_x, sm);
+    __shared__ MipCascade s_mip;
+    __shared__ int s_k, s_bx, s_by;
+    if (threadIdx.x == 0) {
+        const int u = h->phase_base[kPhaseMipLo] + int(blockIdx.x);
+        const int k = find_cascade(cas, h->n_cascades, kPhaseMipLo, u);
+        const int local = u - cas[k].unit_base[kPhaseMipLo], bx = cas[k].mip_blocks_x;
+        s_k = k;
+        s_bx = local % bx;
+        s_by = local / bx;
+    }
+    __syncthreads();
+    cta_copy(&s_mip, &cas[s_k].mip);
+    __syncthreads();
+    mip_lo_block<false>(s_mip, s_bx, s_by, sm);
 }
 
 __global__ void __launch_bounds__(1024) k_bat_miphi(const uint8_t* __restrict__ buf) {

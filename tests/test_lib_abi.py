@@ -395,3 +395,15 @@ def test_leaf_count_limit(hfmod, tiny):
     rc = lib.hf_create_quadtree(ct.byref(desc), lv.ctypes.data_as(ct.c_void_p), ct.c_int64(2 ** 31),
                                 ct.byref(rbf), ct.byref(ctx))
     assert rc == hfmod.HF_ERR_ARG and b"2^31" in lib.hf_last_error() and not ctx.value
+
+
+def test_status_codes_match_the_header(hfmod):
+    """The binding's status constants and names are the header's enum."""
+    txt = open(os.path.join(ROOT, "include", "hf.h")).read()
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"^\s*(HF_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", txt, re.M)}
+    assert "HF_ERR_HOST" in codes and len(codes) >= 8
+    for name, value in codes.items():
+        assert getattr(hfmod, name) == value, name
+        if value:
+            assert hfmod.ERROR_NAMES[value] == name
+    assert set(hfmod.ERROR_NAMES) == {v for v in codes.values() if v}

@@ -63,7 +63,7 @@ class hf_camera(ct.Structure):
 
 
 class hf_cascade_info(ct.Structure):
-    _fields_ = [("near", ct.c_double), ("far", ct.c_double), ("far_ext", ct.c_double),
+    _fields_ = [("near_depth", ct.c_double), ("far_depth", ct.c_double), ("far_ext_depth", ct.c_double),
                 ("n_poly", ct.c_int32), ("N", ct.c_int32),
                 ("poly", (ct.c_double * 2) * HF_MAX_POLY), ("aabb", ct.c_double * 4),
                 ("snap_x", ct.c_int64), ("snap_y", ct.c_int64), ("snap_k", ct.c_int64),
@@ -72,6 +72,18 @@ class hf_cascade_info(ct.Structure):
                 ("spans", ct.c_void_p), ("mip_floats", ct.c_int64),
                 ("water_tex", ct.c_void_p), ("texel_ladder", ct.c_int32), ("reuse_source", ct.c_int32),
                 ("stop_level", ct.c_int32), ("reserved", ct.c_int32)]
+
+    @property
+    def near(self) -> float:
+        return self.near_depth
+
+    @property
+    def far(self) -> float:
+        return self.far_depth
+
+    @property
+    def far_ext(self) -> float:
+        return self.far_ext_depth
 
     @property
     def h(self) -> float:

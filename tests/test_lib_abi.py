@@ -407,3 +407,40 @@ def test_status_codes_match_the_header(hfmod):
         if value:
             assert hfmod.ERROR_NAMES[value] == name
     assert set(hfmod.ERROR_NAMES) == {v for v in codes.values() if v}
+
+
+def test_struct_layouts_match_the_header(hfmod, tmp_path):
+    """Every ctypes structure of the binding (and the leaf record dtype) has
+    the size and field offsets the C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = [hfmod.hf_quadtree_desc, hfmod.hf_rbf_params, hfmod.hf_camera, hfmod.hf_cascade_info,
+               hfmod.hf_view_stats_t, hfmod.hf_batch_item]
+    lines = ['#include <stdio.h>', '#include "hf.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f in st._fields_:
+            lines.append(f'printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines.append('printf("hf_leaf size %zu\\n", sizeof(hf_leaf));')
+    for f in hfmod.LEAF_DTYPE.names:
+        lines.append(f'printf("hf_leaf {f} %zu\\n", offsetof(hf_leaf, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "size")] == ct.sizeof(st), n
+        for f in st._fields_:
+            assert got[(n, f[0])] == getattr(st, f[0]).offset, (n, f[0])
+    assert got[("hf_leaf", "size")] == hfmod.LEAF_DTYPE.itemsize
+    for f in hfmod.LEAF_DTYPE.names:
+        assert got[("hf_leaf", f)] == hfmod.LEAF_DTYPE.fields[f][1], f

@@ -15,7 +15,7 @@ def _table1():
     rows = []
     for line in open(GOLDEN):
         if line.strip() and not line.startswith("#"):
-            name, ex, ey, cmin, cmax, cells = line.split()
+            name, ex, ey, cmin, cmax, cells = line.split()[:6]
             rows.append((name, float(ex), float(ey), float(cmin), float(cmax), float(cells) * 1e6))
     return rows
 
@@ -24,6 +24,17 @@ def test_table1_fixture():
     rows = _table1()
     assert [r[0] for r in rows] == ["Marchfeld", "Petzenkirchen", "Wachau", "Florence"]
     assert all(r[4] == 96 for r in rows)
+
+
+def test_paper_context_quotes_table1():
+    """The bench line's paper context is Table 1's timings, frame = sum."""
+    import bench
+    ctx = bench.paper_context()
+    assert "GTX 1080" in ctx["hardware"]
+    f = ctx["scenarios"]["Florence"]
+    assert (f["approximation_ms"], f["ray_casting_ms"]) == (1.5, 2.8)
+    assert f["frame_ms"] == 4.3
+    assert ctx["scenarios"]["Petzenkirchen"]["frame_ms"] == 25.1
 
 
 def test_dem_stand_in_has_the_papers_shape():

@@ -327,7 +327,10 @@ int hf_ray_stats(hf_ctx* ctx, int32_t view_slot, int64_t* visits, int64_t* patch
  * not exceed 16384 (HF_ERR_ARG otherwise); nothing is allocated.  The array is
  * loaded on every device that loads the library and stays until exit.  The
  * first call on a device looks the array's address up, so make that first
- * call before capturing any stream.  All calls share the array: calls that
+ * call before capturing any stream.  The address is kept for the life of the
+ * process: it stays valid only while the device's primary context lives, so a
+ * caller that resets the device (cudaDeviceReset) must not call this entry
+ * point afterwards.  All calls share the array: calls that
  * overlap on the GPU (e.g. on two streams at once) race and must be ordered
  * by the caller.  If info_out is not NULL it receives the cam->n_cascades
  * fitted cascades (device pointers other than tex are NULL).  The context's

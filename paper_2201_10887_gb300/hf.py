@@ -269,10 +269,35 @@ def hf_view_stats(ctx, slot: int, n_cascades: int, stream=None) -> dict:
             "reused_texels": list(st.reused_texels)[:n_cascades]}
 
 
+def check_noalloc_outputs(cam: hf_camera, tex_out, device_index: int) -> None:
+    """Raise ValueError unless tex_out holds exactly cam.n_cascades contiguous
+    float32 tensors of at least cascade_size^2 elements on CUDA device
+    `device_index`.  The C entry point reads one pointer per cascade and the
+    kernel writes N*N floats through each, so a short list or a small tensor
+    would be read or written past its end."""
+    import torch
+    n = int(cam.n_cascades)
+    if len(tex_out) != n:
+        raise ValueError(f"tex_out holds {len(tex_out)} tensors for {n} cascades")
+    need = int(cam.cascade_size) ** 2
+    for k, t in enumerate(tex_out):
+        if t.dtype != torch.float32:
+            raise ValueError(f"tex_out[{k}] is {t.dtype}, not torch.float32")
+        if not t.is_cuda or t.device.index != device_index:
+            raise ValueError(f"tex_out[{k}] is on {t.device}, not cuda:{device_index}")
+        if not t.is_contiguous():
+            raise ValueError(f"tex_out[{k}] is not contiguous")
+        if t.numel() < need:
+            raise ValueError(f"tex_out[{k}] has {t.numel()} elements, fewer than {need}")
+
+
 def hf_discretize_noalloc(ctx, cam: hf_camera, tex_out, stream=None):
     """Allocation-free discretization into caller-provided textures (one
-    contiguous CUDA float32 tensor of N*N elements per cascade); returns the
-    fitted cascades.  See include/hf.h for the limits and the shared scratch."""
+    contiguous CUDA float32 tensor of N*N elements per cascade, on the
+    current device); returns the fitted cascades.  See include/hf.h for the
+    limits and the shared scratch."""
+    import torch
+    check_noalloc_outputs(cam, tex_out, torch.cuda.current_device())
     n = len(tex_out)
     ptrs = (ct.c_void_p * n)(*[_dptr(t).value for t in tex_out])
     info = (hf_cascade_info * n)()

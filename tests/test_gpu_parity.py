@@ -6,8 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from _parity import (GRAZE_REL, HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, bracketed, check_mask, check_rays,
-                     frame_bracket, height_error, mask_from_spans, ocas, surface_bracket)
+from _parity import (GRAZE_REL, HEIGHT_REL, RAY_REL, RC, assert_rays, bracketed, check_mask, check_rays,
+                     excuse_cap, frame_bracket, height_error, mask_from_spans, mask_margin, ocas, surface_bracket)
 
 pytestmark = pytest.mark.gpu
 
@@ -36,14 +36,13 @@ def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True, 
         oc = ov.cas[c]
         assert (info.snap_x, info.snap_y, info.snap_k) == (oc.snap_x, oc.snap_y, oc.snap_k)
         spans = r.spans(0, c).cpu().numpy()
-        bad, vis = check_mask(orc, info, cells, spans)
+        bad, vis, near = check_mask(orc, info, cells, spans)
         assert bad == 0, f"cascade {c}: {bad} mask mismatches"
         tex = r.texture(0, c).cpu().numpy()
         ref = orc.texel_heights(ocas(orc, info), cells, scene.sigma, scene.radius,
                                 kernel=kernel).reshape(info.N, info.N)
         assert np.array_equal(np.isfinite(tex), mask_from_spans(spans, info.N))
-        both = np.isfinite(tex) & np.isfinite(ref)
-        worst = max(worst, height_error(np.where(both, tex, -np.inf), np.where(both, ref, -np.inf), amp))
+        worst = max(worst, height_error(tex, ref, amp, exempt=near))
         mip = r.mip(0, c).cpu().numpy()
         assert np.array_equal(mip, orc.maxmip(tex)), f"cascade {c}: max mip differs"
         texs.append(tex)
@@ -51,10 +50,10 @@ def _frame_parity(orc, torch_cuda, scene, cam, bucket_level=-1, full_rays=True, 
     assert worst <= HEIGHT_REL, worst
     ot, oh, seg, _ = orc.raycast(cam, scene.tree, rcs, texs)
     gt, gh = t.cpu().numpy().ravel(), hit.cpu().numpy().ravel()
-    frac, off, terr, _ = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
-                                    bracket=frame_bracket(orc, cam, scene.tree, rcs, texs, gt, gh, ot, seg, amp))
-    assert frac <= HIT_MISMATCH and off == 0, (frac, off)
-    assert terr <= RAY_REL, terr
+    res = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
+                     bracket=frame_bracket(orc, cam, scene.tree, rcs, texs, gt, gh, ot, seg, amp))
+    assert_rays(res, f"{cam.width}x{cam.height}, {cam.n_cascades} x {cam.cascade_size}^2")
+    terr = res.terr
     # the reported first-hit cascade agrees where both hit
     both = (gh > 0) & (oh > 0)
     assert not both.any() or np.mean(gh[both] != oh[both]) < 1e-3
@@ -176,7 +175,8 @@ def test_update_values(orc, torch_cuda, tiny):
     for c in range(2):
         info = r.cascade(0, c)
         ref = orc.texel_heights(ocas(orc, info), cells, tiny.sigma, tiny.radius).reshape(info.N, info.N)
-        assert height_error(r.texture(0, c).cpu().numpy(), ref, amp) <= HEIGHT_REL
+        _, margin = mask_margin(orc, info, cells)
+        assert height_error(r.texture(0, c).cpu().numpy(), ref, amp, exempt=margin <= 1e-7) <= HEIGHT_REL
     # a rejected update (a NaN in the middle) changes nothing
     from paper_2201_10887_gb300 import hf
     before = [r.texture(0, c).clone() for c in range(2)]
@@ -246,10 +246,12 @@ def test_maximum_cascades_and_size(orc, torch_cuda, tiny):
         tu, hu, td, hd = surface_bracket(orc, cam, tiny.tree, rcs, texs, px[idx], py[idx],
                                          GRAZE_REL * (tmax + amp))
         return bracketed(g_t[idx], g_h[idx], seg[idx], tu, hu, td, hd)
-    frac, off, terr, _ = check_rays(g_t, g_h, ot, oh, seg, silhouette=np.zeros(px.size, bool), bracket=bracket)
-    assert frac <= 2e-3 and off == 0, (frac, off)
+    res = check_rays(g_t, g_h, ot, oh, seg, silhouette=np.zeros(px.size, bool), bracket=bracket)
+    print(f"sampled rays: {res.n}, hit/miss differ {res.frac:.2e}, passed by backward error {res.excused}")
+    assert res.frac <= 2e-3 and res.off == 0, (res.frac, res.off)
     assert int(((g_h > 0) & (oh > 0)).sum()) > 500
-    assert terr <= RAY_REL, terr
+    assert res.terr <= RAY_REL, res.terr
+    assert res.excused <= excuse_cap(res.n), res.excused
     r.close()
 
 
@@ -274,7 +276,7 @@ def test_dem_frame_sampled(orc, torch_cuda, frame):
     for c in range(cam.n_cascades):
         info = r.cascade(0, c)
         spans = r.spans(0, c).cpu().numpy()
-        bad, vis = check_mask(orc, info, cells, spans)
+        bad, vis, _ = check_mask(orc, info, cells, spans)
         assert bad == 0
         tex = r.texture(0, c).cpu().numpy()
         assert np.array_equal(np.isfinite(tex), mask_from_spans(spans, info.N))
@@ -289,10 +291,9 @@ def test_dem_frame_sampled(orc, torch_cuda, frame):
         rcs.append(RC(info))
     gt, gh = t.cpu().numpy().ravel(), hit.cpu().numpy().ravel()
     ot, oh, seg, _ = orc.raycast(cam, s.tree, rcs, texs)
-    frac, off, terr, _ = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
-                                    bracket=frame_bracket(orc, cam, s.tree, rcs, texs, gt, gh, ot, seg, amp))
-    assert frac <= HIT_MISMATCH and off == 0, (frac, off)
-    assert terr <= RAY_REL, terr
+    res = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
+                     bracket=frame_bracket(orc, cam, s.tree, rcs, texs, gt, gh, ot, seg, amp))
+    assert_rays(res, f"dem frame {frame}")
     r.close()
 
 

@@ -8,8 +8,8 @@ _parity.py (water wet/dry, water flag)."""
 import numpy as np
 import pytest
 
-from _parity import (HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, check_mask, check_rays, check_water_flags,
-                     frame_bracket, mask_from_spans, ocas)
+from _parity import (HEIGHT_REL, RC, assert_rays, check_mask, check_rays, check_water_flags, frame_bracket,
+                     mask_from_spans, ocas)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def _water_frame(orc, scene, cam, depth, texel_sample=None, seed=0):
     for c in range(cam.n_cascades):
         info = r.cascade(0, c)
         spans = r.spans(0, c).cpu().numpy()
-        bad, vis = check_mask(orc, info, cells, spans)
+        bad, vis, _ = check_mask(orc, info, cells, spans)
         assert bad == 0
         tex = r.texture(0, c).cpu().numpy()
         wtex = r.water_texture(0, c).cpu().numpy()
@@ -68,11 +68,9 @@ def _water_frame(orc, scene, cam, depth, texel_sample=None, seed=0):
         rcs.append(RC(info))
     gt, gh = t.cpu().numpy().ravel(), hit.cpu().numpy().ravel()
     ot, oh, seg = orc.raycast_water(cam, scene.tree, rcs, texs, wtexs)
-    frac, off, terr, _ = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
-                                    bracket=frame_bracket(orc, cam, scene.tree, rcs, texs, gt, gh, ot, seg, amp,
-                                                          water_texs=wtexs))
-    assert frac <= HIT_MISMATCH and off == 0, (frac, off)
-    assert terr <= RAY_REL, terr
+    res = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
+                     bracket=frame_bracket(orc, cam, scene.tree, rcs, texs, gt, gh, ot, seg, amp, water_texs=wtexs))
+    assert_rays(res, "water layer")
     n_mis, n_bad = check_water_flags(orc, cam, scene.tree, rcs, texs, wtexs, gh, oh, seg)
     assert n_bad == 0, (n_mis, n_bad)
     both = (gh > 0) & (oh > 0) & ((gh & 0x80) == (oh & 0x80))

@@ -444,3 +444,38 @@ def test_struct_layouts_match_the_header(hfmod, tmp_path):
     assert got[("hf_leaf", "size")] == hfmod.LEAF_DTYPE.itemsize
     for f in hfmod.LEAF_DTYPE.names:
         assert got[("hf_leaf", f)] == hfmod.LEAF_DTYPE.fields[f][1], f
+
+
+def test_noalloc_binding_checks_outputs_before_calling(hfmod):
+    """hf_discretize_noalloc's binding refuses, before the library is called,
+    an output list whose length differs from the camera's cascade count and
+    tensors of the wrong type, device, layout or size: the C entry point
+    reads one pointer per cascade and writes N*N floats through each."""
+    import torch
+
+    class Out:       # stand-in for a CUDA tensor (no GPU here)
+        def __init__(self, n, dtype=torch.float32, cuda=True, index=0, contiguous=True):
+            self.n, self.dtype, self.is_cuda = n, dtype, cuda
+            self.device = torch.device("cuda", index) if cuda else torch.device("cpu")
+            self._contig = contiguous
+
+        def numel(self):
+            return self.n
+
+        def is_contiguous(self):
+            return self._contig
+
+    cam = hfmod.hf_camera()
+    cam.n_cascades, cam.cascade_size = 2, 64
+    good = [Out(64 * 64), Out(64 * 64 + 5)]
+    hfmod.check_noalloc_outputs(cam, good, 0)
+    bad = {"short list": [Out(64 * 64)],
+           "long list": good + [Out(64 * 64)],
+           "dtype": [Out(64 * 64), Out(64 * 64, dtype=torch.float64)],
+           "host tensor": [Out(64 * 64), Out(64 * 64, cuda=False)],
+           "other device": [Out(64 * 64), Out(64 * 64, index=1)],
+           "strided": [Out(64 * 64), Out(64 * 64, contiguous=False)],
+           "too small": [Out(64 * 64), Out(64 * 64 - 1)]}
+    for what, outs in bad.items():
+        with pytest.raises(ValueError):
+            hfmod.check_noalloc_outputs(cam, outs, 0)

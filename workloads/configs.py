@@ -100,28 +100,58 @@ def flood_config(seed: int = 2, n_frames: int = 120, wet_area: float = 0.2, **kw
     return s
 
 
+def _batch_tile(args) -> Scene:
+    seed, t, side, amp, n_c, n_tex, width, height, leaf_frac = args
+    levels = 4 if side >= 256 else 2
+    root_n = max(side >> levels, 1)
+    fbm = FBm(seed * 100 + t, amplitude=amp, wavelength=side * 10.0 / 4)
+    tree = curvature_quadtree(root_n, root_n, 10.0 * (1 << levels), levels, fbm,
+                              max(int(leaf_frac * side * side), root_n * root_n),
+                              seed * 100 + t)
+    cam = flight_path(tree, fbm, seed * 100 + t, 2, width, height, n_c, n_tex,
+                      split_lambda=0.5)[0]
+    return Scene(f"tile{t}", tree, fbm, RBF_SIGMA, RBF_RADIUS, [cam])
+
+
+def parallel_map(fn, items, workers: int | None = None) -> list:
+    """map(fn, items) over worker processes started with 'spawn' (safe after
+    CUDA has been initialised in the caller); in order, same results as a
+    plain map.  workers = 1 runs in this process."""
+    import os
+    items = list(items)
+    if workers is None:
+        workers = min(len(items), len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                      else (os.cpu_count() or 1))
+    if workers <= 1 or len(items) <= 1:
+        return [fn(x) for x in items]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items))
+
+
 def batch_config(seed: int = 4, n_tiles: int = 64, min_side: int = 256,
                  max_side: int = 4096, width: int = 960, height: int = 540,
-                 leaf_frac: float = 0.3) -> list:
+                 leaf_frac: float = 0.3, workers: int | None = None) -> list:
     """Independent tiles: finest side log-uniform in [min_side, max_side],
     10 m finest cells, curvature refinement to ``leaf_frac`` of the finest
-    count, 1-4 cascades of 512^2-2048^2 and one camera each."""
+    count, 1-4 cascades of 512^2-2048^2 and one camera each.  Tiles are
+    generated in parallel processes (the result does not depend on
+    ``workers``)."""
     rng = np.random.default_rng(seed)
-    scenes = []
+    jobs = []
     for t in range(n_tiles):
         side = int(2 ** np.round(rng.uniform(np.log2(min_side), np.log2(max_side))))
-        levels = 4 if side >= 256 else 2
-        root_n = max(side >> levels, 1)
-        fbm = FBm(seed * 100 + t, amplitude=float(rng.uniform(300, 2000)),
-                  wavelength=side * 10.0 / 4)
-        tree = curvature_quadtree(root_n, root_n, 10.0 * (1 << levels), levels, fbm,
-                                  max(int(leaf_frac * side * side), root_n * root_n),
-                                  seed * 100 + t)
+        amp = float(rng.uniform(300, 2000))
         n_c = int(rng.integers(1, 5))
         n_tex = int(2 ** rng.integers(9, 12))
-        cam = flight_path(tree, fbm, seed * 100 + t, 2, width, height, n_c, n_tex,
-                          split_lambda=0.5)[0]
-        scenes.append(Scene(f"tile{t}", tree, fbm, RBF_SIGMA, RBF_RADIUS, [cam]))
+        jobs.append((seed, t, side, amp, n_c, n_tex, width, height, leaf_frac))
+    # largest tiles first so that the pool ends together
+    order = sorted(range(n_tiles), key=lambda t: -jobs[t][2])
+    done = parallel_map(_batch_tile, [jobs[t] for t in order], workers)
+    scenes = [None] * n_tiles
+    for t, sc in zip(order, done):
+        scenes[t] = sc
     return scenes
 
 
@@ -134,11 +164,13 @@ class Request:
 
 def serve_config(seed: int = 5, blocks: int = 4, leaves_per_block: int = 2_500_000,
                  block_root: int = 128, rate: float = 200.0, duration: float = 2.0,
-                 cascade_size: int = 2048) -> tuple:
-    """(Scene, requests): the resident quadtree and the request stream."""
+                 cascade_size: int = 2048, workers: int | None = None) -> tuple:
+    """(Scene, requests): the resident quadtree and the request stream (the
+    blocks of the mosaic are refined in parallel processes)."""
     span = blocks * block_root * 320.0
     fbm = FBm(seed, amplitude=3000.0, wavelength=span / 8)
-    tree = tiled_curvature_quadtree(blocks, block_root, 320.0, 5, fbm, leaves_per_block, seed)
+    tree = tiled_curvature_quadtree(blocks, block_root, 320.0, 5, fbm, leaves_per_block, seed,
+                                    pmap=lambda f, xs: parallel_map(f, xs, workers))
     rng = np.random.default_rng(seed)
     n = int(rng.poisson(rate * duration))
     arrivals = np.sort(rng.uniform(0.0, duration, n))

@@ -168,20 +168,25 @@ def curvature_quadtree(root_nx: int, root_ny: int, root_cell: float, max_level: 
                    np.concatenate(iy_out), np.concatenate(val_out), seed, shuffle)
 
 
+def _mosaic_block(args):
+    block_root, root_cell, max_level, fbm, leaves_per_block, seed, blocks, bx, by = args
+    span = block_root * root_cell
+    t = curvature_quadtree(block_root, block_root, root_cell, max_level, fbm,
+                           leaves_per_block, seed + by * blocks + bx,
+                           fbm_offset=(bx * span, by * span))
+    shift = (block_root << t.level.astype(np.int64))
+    return t.level, t.ix + bx * shift, t.iy + by * shift, t.value
+
+
 def tiled_curvature_quadtree(blocks: int, block_root: int, root_cell: float, max_level: int,
-                             fbm: FBm, leaves_per_block: int, seed: int) -> Quadtree:
+                             fbm: FBm, leaves_per_block: int, seed: int, pmap=None) -> Quadtree:
     """A blocks x blocks mosaic of curvature-refined blocks of one continuous
     terrain (each block refined with its own threshold), for domains too
-    large to sample at the finest level at once."""
-    parts = []
-    span = block_root * root_cell
-    for by in range(blocks):
-        for bx in range(blocks):
-            t = curvature_quadtree(block_root, block_root, root_cell, max_level, fbm,
-                                   leaves_per_block, seed + by * blocks + bx,
-                                   fbm_offset=(bx * span, by * span))
-            shift = (block_root << t.level.astype(np.int64))
-            parts.append((t.level, t.ix + bx * shift, t.iy + by * shift, t.value))
+    large to sample at the finest level at once.  ``pmap(fn, items)`` maps
+    the blocks (e.g. over processes); default: in this process."""
+    jobs = [(block_root, root_cell, max_level, fbm, leaves_per_block, seed, blocks, bx, by)
+            for by in range(blocks) for bx in range(blocks)]
+    parts = (pmap or (lambda f, xs: [f(x) for x in xs]))(_mosaic_block, jobs)
     level = np.concatenate([p[0] for p in parts])
     ix = np.concatenate([p[1] for p in parts])
     iy = np.concatenate([p[2] for p in parts])

@@ -36,8 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "1080p frame ms (RBF discretize + ray cast), Grays/s, Gtexel/s; p99 latency"
 WORKLOAD = "dem: 4096^2-equivalent quadtree (10-160 m cells, 4.5 M leaves), 4x2048^2 FP32 cascades, 1920x1080, 120-frame flight"
 
-# Nominal sm_103a unit counts per SM and clock: FP32 lanes and MUFU (ex2) lanes.
-SMS = 152
+# Nominal sm_103a unit counts per SM (the SM count itself is read from the device).
 FP32_PER_SM = 128
 MUFU_PER_SM = 32   # ex2 lanes per SM on GB300 (twice earlier parts; hf_measure_unit_rates confirms)
 FP32_OPS_PER_TERM = 9   # 2 sub, d^2 (mul + fma), scale, -K, max, sum, fma
@@ -46,10 +45,13 @@ RAY_OPS_PER_TEST = 30   # bilinear coefficients, quadratic, root selection (+ 1 
 
 
 def frame_schedule(n_frames: int, steps: int, rank: int, world: int) -> list:
-    """Frames rendered by `rank`: each rank walks the flight path from its own
-    offset (weak scaling: the same number of frames per rank)."""
-    off = (rank * n_frames) // max(world, 1)
-    return [(off + k) % n_frames for k in range(steps)]
+    """Frames rendered by `rank`: `steps` frames per rank (weak scaling), all
+    ranks' frames together spread evenly over the whole flight path and
+    interleaved (position k world + rank of steps * world), so that any step
+    count samples the light start and the heavy end alike."""
+    world = max(world, 1)
+    total = max(steps, 1) * world
+    return [(((k * world + rank) * n_frames) // total) % n_frames for k in range(steps)]
 
 
 def reduce_max(value: float, world: int) -> float:
@@ -245,10 +247,46 @@ def oracle_frame_sample(scene, cam, cells, target_s: float, seed: int) -> dict:
 
 
 def _oracle_sample_text(res):
-    return (f"per frame: fit, masks and max mipmaps in full; Eq. 2 at {res['n_texels']} random "
-            f"visible texels (scaled to {res['visible_texels']}), {res['n_rays']} random pixels "
-            f"(scaled to 1920x1080) on generator-filled cascade textures; FP64, OpenMP; "
-            f"{res['sampled_s']:.1f} s of CPU work")
+    return (f"estimated from a sample, not a timed whole frame: per frame, fit, masks and max mipmaps "
+            f"timed in full; Eq. 2 at {res['n_texels']} random visible texels (scaled to "
+            f"{res['visible_texels']}), {res['n_rays']} random pixels (scaled to 1920x1080) on "
+            f"generator-filled cascade textures; FP64, OpenMP; {res['sampled_s']:.1f} s of CPU work")
+
+
+class _RC:
+    """Cascade parameters of the oracle's ray caster."""
+
+    def __init__(self, info):
+        self.ox, self.oy, self.h, self.near, self.far_ext, self.N = (
+            info.ox, info.oy, info.texel, info.near, info.far_ext, info.N)
+        self.stop_level = getattr(info, "stop_level", 0)
+
+
+def _oracle_cascade(oracle, info):
+    """The library's fitted cascade as the oracle's cascade record."""
+    c = oracle.CascadeC()
+    c.ox, c.oy, c.h, c.N, c.n_poly, c.E = info.ox, info.oy, info.texel, info.N, info.n_poly, info.extent
+    for k in range(info.n_poly):
+        c.poly[k][0], c.poly[k][1] = info.poly[k][0], info.poly[k][1]
+    return c
+
+
+def oracle_whole_frame(scene, cam, infos, cells) -> dict:
+    """The oracle on one whole frame, timed: Eq. 2 at every visible texel of
+    every cascade (fitted by the library, whose fit the tests hold equal to
+    the oracle's), the max mipmaps and every pixel's ray."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    texs, rcs = [], []
+    for info in infos:
+        ref = oracle.texel_heights(_oracle_cascade(oracle, info), cells, scene.sigma, scene.radius)
+        tex = np.where(np.isfinite(ref), ref, -np.inf).astype(np.float32).reshape(info.N, info.N)
+        oracle.maxmip(tex)
+        texs.append(tex)
+        rcs.append(_RC(info))
+    t, hit, seg, _ = oracle.raycast(cam, scene.tree, rcs, texs)
+    return {"frame_ms": 1e3 * (time.perf_counter() - t0), "textures": texs, "t": t, "hit": hit, "seg": seg}
 
 
 def run_reference(args, rank, world):
@@ -260,12 +298,13 @@ def run_reference(args, rank, world):
     oracle.build()
     scene = workloads.dem_config(n_frames=args.frames)
     cells = oracle.Cells(scene.tree)
-    frames = frame_schedule(args.frames, args.warmup + args.steps, 0, 1)
-    # Each measured step costs a couple of seconds of untimed set-up (fit, masks and
-    # textures of 4 x 2048^2 cascades) besides its timed sample, so at most 3 warm-up
-    # and 40 timed steps are run, the latter at evenly spaced positions of the schedule:
-    # the whole run stays within a few minutes for any --steps.
-    warm, timed = frames[: min(args.warmup, 3)], frames[args.warmup:]
+    # the GPU arm's frames (spread over the whole flight); each measured step costs a
+    # couple of seconds of untimed set-up (fit, masks and textures of 4 x 2048^2
+    # cascades) besides its timed sample, so at most 3 warm-up and 40 timed steps are
+    # run, the latter at evenly spaced positions of the schedule: the whole run stays
+    # within a few minutes for any --steps.
+    warm = frame_schedule(args.frames, min(args.warmup, 3), 0, 1)
+    timed = frame_schedule(args.frames, args.steps, 0, 1)
     cap = 40
     if len(timed) > cap:
         timed = [timed[i] for i in np.linspace(0, len(timed) - 1, cap).round().astype(int)]
@@ -284,7 +323,7 @@ def run_reference(args, rank, world):
             "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 1, "parallelism": "none",
                        "l2": "n/a (CPU)"},
             "p50_ms": statistics.median(per), "p99_ms": _pct(per, 99),
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "estimated": True,
                              "sample": _oracle_sample_text(last) + f"; {per_step_s:.2f} s target per step; "
                                        f"{len(per)} of {args.steps} timed steps measured (evenly spaced "
                                        f"over the frame schedule)"},
@@ -362,6 +401,19 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     r.sync()
+    # the host FP64 cascade fit itself (it overlaps the L2 flush in the timed
+    # frames): the C call alone, on the same frames, untimed by the events
+    import ctypes as ct
+    from paper_2201_10887_gb300 import hf as hfb
+    from paper_2201_10887_gb300.renderer import camera_struct as _cs
+    vbuf = r.views[0]["buf"]
+    fit_us = []
+    for f in sched:
+        cs = _cs(cams[f])
+        t0 = time.perf_counter()
+        rc = hfb.lib().hf_set_camera(r.ctx, 0, ct.byref(cs), ct.c_void_p(vbuf.data_ptr()), vbuf.numel())
+        fit_us.append(1e6 * (time.perf_counter() - t0))
+        assert rc == 0, hfb.hf_last_error()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     # kernel time of the discretization: from the end of the host fit (or of
     # the L2 flush, if that is later) to the end of the last texel
@@ -434,6 +486,10 @@ def run_ours(args, rank, world, local_rank):
     ptests = sum(work[f][4] for f in sched)
     peaks = load_peaks()
     fclk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    # measured unit rates and the device's SM count (the derived peaks use the latter)
+    from paper_2201_10887_gb300 import hf as hfmod
+    rates = hfmod.hf_measure_unit_rates()
+    SMS = int(rates["sms"]) or torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = min(MUFU_PER_SM * SMS * fclk, FP32_PER_SM * SMS * fclk / FP32_OPS_PER_TERM) / 1e9
     mip_bytes = C * (4 * N * N + 4 * ((4 * (1 << (N - 2).bit_length()) ** 2 - 1) // 3))
     kern = {
@@ -451,8 +507,6 @@ def run_ours(args, rank, world, local_rank):
                     "patch_tests_per_ray": ptests / (W * H * len(sched))},
     }
     # measured unit rates beside the derived peaks (the roofline stays on the derived ones)
-    from paper_2201_10887_gb300 import hf as hfmod
-    rates = hfmod.hf_measure_unit_rates()
     kern["discretize"]["peak_measured"] = min(rates["ex2_per_s"], rates["ffma_per_s"] / FP32_OPS_PER_TERM) / 1e9
     kern["raycast"]["peak_measured"] = rates["ffma_per_s"] / 1e9
     for v in kern.values():
@@ -466,8 +520,8 @@ def run_ours(args, rank, world, local_rank):
     kname = {"discretize": "k_discretize_f32", "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["achieved"] / d["peak"], "traffic": profiled_traffic(kname), "kernel": dom,
-                "peak_source": ("derived from unit counts at %d MHz" % int(fclk / 1e6)
-                                if d["bound"] == "alu" else peaks["source"])}
+                "peak_source": ("derived from unit counts, %d SMs (read from the device) at %d MHz"
+                                % (SMS, int(fclk / 1e6)) if d["bound"] == "alu" else peaks["source"])}
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": len(sched),
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": False,
@@ -478,6 +532,10 @@ def run_ours(args, rank, world, local_rank):
                    "frames": args.frames},
         "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
         "fit_wait_ms": statistics.mean(fit_gap_ms),
+        "fit_host_us": {"mean": statistics.mean(fit_us), "p50": statistics.median(fit_us), "max": max(fit_us),
+                        "note": "host FP64 cascade fit (hf_set_camera, the C call alone) on the same frames; in "
+                                "the timed frames it runs while the L2 flush executes, and fit_wait_ms is what "
+                                "the stream waited for it"},
         "grays_per_s": W * H * len(sched) / (sum(step_ms) * 1e-3) / 1e9,
         "gtexel_per_s": vis / (sum(disc_ms) * 1e-3) / 1e9,
         "kernel_grays_per_s": W * H * len(sched) / (sum(ray_ms) * 1e-3) / 1e9,
@@ -504,15 +562,24 @@ def run_ours(args, rank, world, local_rank):
                                          "frames overlap; no L2 flush between frames (throughput, not latency)"},
         "paper_context": paper_context(),
     }
+    kept = {}
+    err_frame = len(cams) // 2
     if not args.no_variants:
         line["precision_variants"] = time_precision_variants(scene, cams, sched[:min(len(sched), 240)],
-                                                             args.warmup, dev, flush, stream)
+                                                             args.warmup, dev, flush, stream,
+                                                             keep_frame=err_frame, kept=kept)
+        kept["fp32"] = frame_textures(r, cams[err_frame])
         line["interpolant_variants"] = time_precision_variants(
             scene, cams, sched[:min(len(sched), 240)], args.warmup, dev, flush, stream,
             variants=(("wendland_c2", {"kernel": 1}),))
         line["temporal_reuse"] = time_temporal_reuse(scene, args.warmup, dev, flush, stream)
         line["coarse_stop"] = time_coarse_stop(scene, cams, sched[:min(len(sched), 120)], args.warmup, dev,
                                                flush, stream)
+    if world == 1 and not args.no_blocks:
+        # the other workloads, short: terrain + water, 64-tile batched frames, serving
+        line["flood"] = flood_block(args, min(len(sched), 20), args.warmup)
+        line["batch"] = batch_block(args, min(len(sched), 10), min(args.warmup, 3))
+        line["serve"] = serve_block(args)
     if rank == 0:
         line["clocks"] = clk.summary()
         if world == 1 and not args.no_cpu_baseline:
@@ -523,19 +590,26 @@ def run_ours(args, rank, world, local_rank):
             res = [oracle_frame_sample(scene, cams[f], cells, args.cpu_s / len(picks), seed=k)
                    for k, f in enumerate(picks)]
             line["cpu_baseline"] = {"value": statistics.mean(x["frame_ms"] for x in res), "unit": "ms",
-                                    "cores": oracle.threads(), "kind": "oracle",
+                                    "cores": oracle.threads(), "kind": "oracle", "estimated": True,
                                     "per_frame_ms": {str(f): x["frame_ms"] for f, x in zip(picks, res)},
                                     "sample": _oracle_sample_text(res[0]) + "; mean over frames "
                                               + ", ".join(str(f) for f in picks)}
+            if kept:
+                errs, whole = precision_errors(args, scene, err_frame, kept, dev)
+                line["precision_variants"]["errors"] = errs
+                line["cpu_baseline"]["whole_frames_ms"] = {
+                    k: dict(v, note="timed, not estimated: every texel and every ray") for k, v in whole.items()}
         print(json.dumps(line), flush=True)
     r.close()
 
 
 def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream,
-                            variants=(("fp16", {"precision": 1}), ("bf16", {"precision": 2}))):
+                            variants=(("fp16", {"precision": 1}), ("bf16", {"precision": 2})),
+                            keep_frame=None, kept=None):
     """Frame and discretization time of variants of the discretization (by
     default the FP16x2 / BF16x2 paths) on the same frames (same timing method
-    as the main line)."""
+    as the main line).  With keep_frame, each variant's cascade textures of
+    that frame go to kept[name] as (cascade infos, host textures)."""
     import torch
     from paper_2201_10887_gb300 import Renderer
     out = {}
@@ -560,10 +634,93 @@ def time_precision_variants(scene, cams, sched, warmup, dev, flush, stream,
         out[name] = {"frame_ms": statistics.mean(e[0].elapsed_time(e[2]) for e in ev),
                      "discretize_ms": statistics.mean(e[3].elapsed_time(e[1]) for e in ev),
                      "frames": len(sched)}
+        if keep_frame is not None and kept is not None:
+            kept[name] = frame_textures(r, cams[keep_frame])
         r.close()
         del r
         torch.cuda.empty_cache()
     return out
+
+
+def frame_textures(r, cam) -> tuple:
+    """Render `cam` in view slot 0; (cascade infos, host copies of the cascade
+    textures)."""
+    r.render(cam)
+    r.sync()
+    infos = [r.cascade(0, c) for c in range(cam.n_cascades)]
+    return infos, [r.texture(0, c).cpu().numpy() for c in range(cam.n_cascades)]
+
+
+def precision_errors(args, dem, dem_frame, dem_kept, dev) -> tuple:
+    """Per-cascade height error and ray-hit error of the FP32, FP16x2 and
+    BF16x2 discretizations against the FP64 oracle, and the oracle's time on
+    the small workloads in full.  (a) The precision workload (the tiny scene
+    with its world origin at (5e6, 5e6) m, one 256^2 cascade, 320 x 240):
+    the oracle computes the whole frame (every texel, every ray), timed, and
+    each path's textures and rays are compared with it.  (b) A DEM frame at
+    full size: each path's textures at a seeded sample of visible texels
+    per cascade against the oracle there.  Also the tiny workload's whole
+    oracle frame, timed.  Returns (errors, oracle whole-frame times)."""
+    import numpy as np
+    import oracle
+    import workloads
+    from paper_2201_10887_gb300 import Renderer
+    oracle.build()
+    names = {0: "fp32", 1: "fp16", 2: "bf16"}
+    errors, timed = {}, {}
+
+    def height_err(g, o, amp):
+        both = np.isfinite(g) & np.isfinite(o)
+        if not both.any():
+            return 0.0
+        return float(np.max(np.abs(g[both].astype(np.float64) - o[both]) / np.maximum(np.abs(o[both]), amp)))
+
+    for wname, scene in (("tiny", workloads.tiny_config()), ("precision", workloads.precision_config())):
+        cam = scene.cameras[0]
+        cells = oracle.Cells(scene.tree)
+        amp = float(np.abs(cells.cv).max())
+        res = {}
+        for prec, pname in names.items():
+            r = Renderer(scene.tree, scene.sigma, scene.radius, precision=prec, device=dev)
+            t, hit = r.render(cam)
+            r.sync()
+            infos = [r.cascade(0, c) for c in range(cam.n_cascades)]
+            texs = [r.texture(0, c).cpu().numpy() for c in range(cam.n_cascades)]
+            res[pname] = (infos, texs, t.cpu().numpy().ravel(), hit.cpu().numpy().ravel())
+            r.close()
+        ref = oracle_whole_frame(scene, cam, res["fp32"][0], cells)
+        timed[wname] = {"frame_ms": ref["frame_ms"], "texels": int(sum(np.isfinite(x).sum() for x in ref["textures"])),
+                        "pixels": cam.width * cam.height}
+        if wname != "precision":
+            continue
+        for pname, (infos, texs, gt, gh) in res.items():
+            ot, oh, seg = ref["t"], ref["hit"], ref["seg"]
+            both = (gh > 0) & (oh > 0)
+            rel = np.abs(gt[both] - ot[both]) / np.maximum(seg[both], 1e-30)
+            errors.setdefault(pname, {})["precision_workload"] = {
+                "height_error_per_cascade": [height_err(g, o, amp) for g, o in zip(texs, ref["textures"])],
+                "ray_t_error_of_segment": {"median": float(np.median(rel)), "p99": float(np.percentile(rel, 99)),
+                                           "max": float(rel.max())},
+                "hit_miss_differ": float(np.mean((gh > 0) != (oh > 0)))}
+    # (b) the DEM frame: sampled texels per cascade, the same texels for every path
+    cells = oracle.Cells(dem.tree)
+    amp = float(np.abs(cells.cv).max())
+    rng = np.random.default_rng(60)
+    infos32, tex32 = dem_kept["fp32"]
+    for c, info in enumerate(infos32):
+        jj, ii = np.nonzero(np.isfinite(tex32[c]))
+        pick = rng.choice(jj.size, size=min(args.err_texels, jj.size), replace=False)
+        o = oracle.texel_heights(_oracle_cascade(oracle, info), cells, dem.sigma, dem.radius, ii[pick], jj[pick])
+        for pname, (infos, texs) in dem_kept.items():
+            assert (infos[c].snap_x, infos[c].snap_y, infos[c].snap_k) == (info.snap_x, info.snap_y, info.snap_k)
+            g = texs[c][jj[pick], ii[pick]]
+            errors.setdefault(pname, {}).setdefault(
+                "dem_frame", {"frame": dem_frame, "sampled_texels_per_cascade": int(pick.size),
+                              "height_error_per_cascade": []})["height_error_per_cascade"].append(height_err(g, o, amp))
+    errors["note"] = ("height error = max |v - v_oracle| / max(|v_oracle|, A), A the largest cell value; ray t "
+                      "error relative to the first-hit cascade's segment; the oracle is FP64; stated bounds: heights "
+                      "1e-5 (FP32), 2.5e-4 (FP16), 2e-3 (BF16) of A")
+    return errors, timed
 
 
 def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed=2):
@@ -727,7 +884,7 @@ def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(2.0, 
     return out
 
 
-def run_batch_workload(args):
+def batch_block(args, steps: int, warmup: int) -> dict:
     """64 independent tiles (finest side log-uniform in [256, 4096], 1-4
     cascades of 512^2-2048^2, one 960x540 view each), rendered per view, as
     one batched launch (autotuned shapes), and as a replayed CUDA graph."""
@@ -735,10 +892,10 @@ def run_batch_workload(args):
     import workloads
     from paper_2201_10887_gb300 import Batch, Renderer, autotune
     from paper_2201_10887_gb300.batch import describe
-    torch.cuda.set_device(0)
     t0 = time.perf_counter()
     scenes = workloads.batch_config(seed=4, n_tiles=args.tiles)
     t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
     rs, views, cams = [], [], []
     for sc in scenes:
         r = Renderer(sc.tree, sc.sigma, sc.radius)
@@ -746,6 +903,7 @@ def run_batch_workload(args):
         rs.append(r)
         views.append((r, 0))
         cams.append(sc.cameras[0])
+    t_ctx = time.perf_counter() - t0
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -768,71 +926,100 @@ def run_batch_workload(args):
             r.build_maxmip()
             r.raycast()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         per_view()
-    single = timed(per_view, args.steps)
+    single = timed(per_view, steps)
     batch = Batch(views)
     best, tune = autotune(batch, reps=2)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
-    batched = timed(batch.run, args.steps)
+    batched = timed(batch.run, steps)
     batch.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run()
-    graphed = timed(batch.run, args.steps)
+    graphed = timed(batch.run, steps)
     for r in rs:
         r.sync()
     texels = sum(c.n_cascades * c.cascade_size ** 2 for c in cams)
     rays = sum(c.width * c.height for c in cams)
-    line = {"metric": f"batched frame ms ({len(cams)} tiles, one 960x540 view each)",
-            "value": statistics.median(graphed), "unit": "ms", "higher_is_better": False,
-            "per_view_calls_ms": statistics.median(single), "batched_launch_ms": statistics.median(batched),
-            "graph_replay_ms": statistics.median(graphed), "p99_graph_ms": _pct(graphed, 99),
-            "autotuned": describe(best), "autotune_ms": {describe(k): v for k, v in tune.items()},
-            "tiles": len(cams), "cascade_texels": texels, "rays": rays,
-            "grays_per_s_graph": rays / (statistics.median(graphed) * 1e-3) / 1e9,
-            "leaves": sum(sc.tree.n_leaves for sc in scenes), "generation_s": t_gen,
-            "steps": args.steps, "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch: 64 tiles, finest side log-uniform 256-4096, 1-4 cascades of "
-                                   "512^2-2048^2, 960x540 per tile", "l2": "flushed between steps"}}
-    print(json.dumps(line), flush=True)
+    out = {"metric": f"batched frame ms ({len(cams)} tiles, one 960x540 view each)",
+           "value": statistics.median(graphed), "unit": "ms", "higher_is_better": False,
+           "per_view_calls_ms": statistics.median(single), "batched_launch_ms": statistics.median(batched),
+           "graph_replay_ms": statistics.median(graphed), "p99_graph_ms": _pct(graphed, 99),
+           "autotuned": describe(best), "autotune_ms": {describe(k): v for k, v in tune.items()},
+           "tiles": len(cams), "cascade_texels": texels, "rays": rays,
+           "gtexel_per_s_graph": texels / (statistics.median(graphed) * 1e-3) / 1e9,
+           "grays_per_s_graph": rays / (statistics.median(graphed) * 1e-3) / 1e9,
+           "leaves": sum(sc.tree.n_leaves for sc in scenes),
+           "persistent_gb": sum(r.persistent_bytes for r in rs) / 2 ** 30,
+           "generation_s": t_gen, "contexts_s": t_ctx, "steps": steps, "warmup": warmup,
+           "config": {"workload": "batch: 64 tiles, finest side log-uniform 256-4096, 1-4 cascades of "
+                                  "512^2-2048^2, 960x540 per tile", "l2": "flushed between steps (256 MB)"}}
+    del batch
+    for r in rs:
+        r.close()
+    del rs, views
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_serve_workload(args):
+def run_batch_workload(args):
+    import torch
+    torch.cuda.set_device(0)
+    d = batch_block(args, args.steps, args.warmup)
+    d.update({"dtype": "f32", "data": "synthetic"})
+    print(json.dumps(d), flush=True)
+
+
+def serve_block(args) -> dict:
     """Continuous-batching server over the resident 16384^2-equivalent
     quadtree; Poisson requests at 200/s of 720p / 1080p / 2160p with 2-6
     cascades of 2048^2; admission by a device-memory budget."""
     import torch
     import workloads
     from paper_2201_10887_gb300 import Renderer, Server
-    torch.cuda.set_device(0)
     t0 = time.perf_counter()
     scene, reqs = workloads.serve_config(duration=args.serve_s)
     t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
     r = Renderer(scene.tree, scene.sigma, scene.radius)
+    t_ctx = time.perf_counter() - t0
     srv = Server(r, int(args.serve_budget_gb * (1 << 30)), max_slots=64, n_streams=3, max_group=16)
     warm = [workloads.Request(q.rid, 0.0, q.camera) for q in reqs[:24]]
     srv.run(warm, realtime=False)
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         live = srv.run(reqs, realtime=True)
     burst = srv.run(reqs, realtime=False)
-    line = {"metric": "serving frame latency ms (p50/p99) and frames/s, Poisson 200/s",
-            "value": live["p99_ms"], "unit": "ms", "higher_is_better": False,
-            "p50_ms": live["p50_ms"], "p99_ms": live["p99_ms"], "mean_ms": live["mean_ms"],
-            "frames_per_s": live["frames_per_s"], "offered_rate": 200.0,
-            "groups": live["groups"], "mean_group": live["mean_group"],
-            "max_memory_used": live["max_memory_used"], "memory_budget": live["memory_budget"],
-            "burst_frames_per_s": burst["frames_per_s"], "burst_mean_group": burst["mean_group"],
-            "requests": len(reqs), "leaves": scene.tree.n_leaves, "generation_s": t_gen,
-            "clocks": clk.summary(), "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve: 16384^2-equivalent quadtree (6 levels), Poisson 200/s, "
-                                   "720p/1080p/2160p, 2-6 cascades of 2048^2",
-                       "latency": "arrival to result in pinned host memory"}}
-    print(json.dumps(line), flush=True)
+    out = {"metric": "serving frame latency ms (p50/p99) and frames/s, Poisson 200/s",
+           "value": live["p99_ms"], "unit": "ms", "higher_is_better": False,
+           "p50_ms": live["p50_ms"], "p99_ms": live["p99_ms"], "mean_ms": live["mean_ms"],
+           "frames_per_s": live["frames_per_s"], "offered_rate": 200.0,
+           "groups": live["groups"], "mean_group": live["mean_group"],
+           "max_memory_used": live["max_memory_used"], "memory_budget": live["memory_budget"],
+           "resident_persistent_gb": r.persistent_bytes / 2 ** 30,
+           "burst_frames_per_s": burst["frames_per_s"], "burst_mean_group": burst["mean_group"],
+           "requests": len(reqs), "leaves": scene.tree.n_leaves, "generation_s": t_gen, "context_s": t_ctx,
+           "clocks": clk.summary(),
+           "config": {"workload": "serve: 16384^2-equivalent quadtree (6 levels), Poisson 200/s, "
+                                  "720p/1080p/2160p, 2-6 cascades of 2048^2",
+                      "latency": "arrival to result in pinned host memory"}}
     r.close()
+    del srv, r
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_flood_workload(args):
+def run_serve_workload(args):
+    import torch
+    torch.cuda.set_device(0)
+    d = serve_block(args)
+    d.update({"dtype": "f32", "data": "synthetic"})
+    print(json.dumps(d), flush=True)
+
+
+def flood_block(args, steps: int, warmup: int) -> dict:
     """The DEM flight with the water layer: relative water depths on the same
     4.5 M cells (a level flood over 20 % of the area), terrain and water
     discretized in one pass, one max mipmap bounding both surfaces, rays that
@@ -841,15 +1028,14 @@ def run_flood_workload(args):
     import torch
     import workloads
     from paper_2201_10887_gb300 import Renderer
-    torch.cuda.set_device(0)
     scene = workloads.flood_config(n_frames=args.frames)
     cams = scene.cameras
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    sched = frame_schedule(args.frames, args.steps, 0, 1)
+    sched = frame_schedule(args.frames, steps, 0, 1)
 
     def timed(r):
-        for f in frame_schedule(args.frames, args.warmup, 0, 1):
+        for f in frame_schedule(args.frames, warmup, 0, 1):
             r.render(cams[f])
         r.sync()
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in sched]
@@ -873,7 +1059,7 @@ def run_flood_workload(args):
 
     rw = Renderer(scene.tree, scene.sigma, scene.radius, water=True)
     rw.update_water(scene.depth)
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         wet = timed(rw)
     water_px, hit_px = [], []
     for f in sorted(set(sched))[::4]:
@@ -886,8 +1072,10 @@ def run_flood_workload(args):
     r0 = Renderer(scene.tree, scene.sigma, scene.radius)
     dry = timed(r0)
     r0.close()
+    del r0, flush
+    torch.cuda.empty_cache()
     mean = statistics.mean
-    line = {"metric": "1080p frame ms, terrain + water (one RBF pass for both fields, one max mip bounding both, "
+    return {"metric": "1080p frame ms, terrain + water (one RBF pass for both fields, one max mip bounding both, "
                       "rays against the first surface met)",
             "value": mean(wet["frame"]), "unit": "ms", "higher_is_better": False,
             "p50_ms": statistics.median(wet["frame"]), "p99_ms": _pct(wet["frame"], 99),
@@ -895,12 +1083,18 @@ def run_flood_workload(args):
             "terrain_only": {"frame_ms": mean(dry["frame"]), **{k + "_ms": mean(v) for k, v in dry.items() if k != "frame"}},
             "water_pixel_fraction": mean(water_px), "hit_pixel_fraction": mean(hit_px),
             "wet_leaves": int((scene.depth > 0).sum()), "leaves": scene.tree.n_leaves,
-            "steps": len(sched), "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-            "clocks": clk.summary(), "paper_context": paper_context(),
+            "steps": len(sched), "warmup": warmup, "clocks": clk.summary(),
             "config": {"workload": "flood: dem (4.5 M leaves, 4x2048^2 cascades, 1920x1080, 120-frame flight) "
                                    "+ level flood depths over 20 % of the area",
                        "l2": "flushed between steps (256 MB write outside the step events)"}}
-    print(json.dumps(line), flush=True)
+
+
+def run_flood_workload(args):
+    import torch
+    torch.cuda.set_device(0)
+    d = flood_block(args, args.steps, args.warmup)
+    d.update({"dtype": "f32", "data": "synthetic", "paper_context": paper_context()})
+    print(json.dumps(d), flush=True)
 
 
 def main():
@@ -914,6 +1108,8 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=15.0, help="CPU seconds of the baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 timing")
+    ap.add_argument("--no-blocks", action="store_true", help="skip the flood, batch and serve blocks")
+    ap.add_argument("--err-texels", type=int, default=1500, help="sampled DEM texels per cascade (errors)")
     ap.add_argument("--workload", default="dem", choices=["dem", "batch", "serve", "flood"])
     ap.add_argument("--tiles", type=int, default=64)
     ap.add_argument("--serve-s", type=float, default=2.0, help="seconds of request stream")

@@ -43,12 +43,13 @@ def test_two_rank_schedule_and_max():
         assert p.exitcode == 0
     (r0, s0, m0), (r1, s1, m1) = out
     assert m0 == m1 == 15.0
-    assert s0 == list(range(10)) and s1 == list(range(60, 70))
+    assert s0 == list(range(0, 120, 12)) and s1 == list(range(6, 120, 12))
     assert not set(s0) & set(s1)
 
 
 def test_single_rank_is_identity():
     import bench
     assert bench.reduce_max(3.5, 1) == 3.5
-    assert bench.frame_schedule(120, 5, 0, 1) == [0, 1, 2, 3, 4]
-    assert bench.frame_schedule(4, 6, 0, 1) == [0, 1, 2, 3, 0, 1]
+    assert bench.frame_schedule(120, 5, 0, 1) == [0, 24, 48, 72, 96]
+    assert bench.frame_schedule(4, 6, 0, 1) == [0, 0, 1, 2, 2, 3]
+    assert sorted(set(bench.frame_schedule(120, 1200, 0, 1))) == list(range(120))

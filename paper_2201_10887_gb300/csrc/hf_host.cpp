@@ -203,13 +203,13 @@ struct hf_ctx {
         l.lprefix = o; o = align256(o + leaves.prefix.size() * 4);
         l.bbits = o; o = align256(o + buckets.bits.size() * 8);
         l.bprefix = o; o = align256(o + buckets.prefix.size() * 4);
-        l.recs = o; o = align256(o + size_t(n_leaves) * 16);
+        l.recs = o; o = align256(o + size_t(n_leaves + 1) * 16);  // + the null record
         l.offsets = o; o = align256(o + size_t(n_buckets + 1) * 8);
         l.idx = o; o = align256(o + size_t(n_cand) * 4);
         const bool compact = rbf.precision != HF_PREC_FP32;
         l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
         l.pairs = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
-        l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves) * 4 : 0));
+        l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves + 1) * 4 : 0));
         l.total = o;
         return l;
     }
@@ -250,6 +250,7 @@ struct hf_ctx {
         v.idx = reinterpret_cast<int32_t*>(dev + lay.idx);
         v.recs = reinterpret_cast<float4*>(dev + lay.recs);
         v.depth = rbf.water ? reinterpret_cast<const float*>(dev + lay.depth) : nullptr;
+        v.sentinel = int32_t(n_leaves);
         return v;
     }
 };
@@ -529,7 +530,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         int64_t run = 0;
         for (int64_t b = 0; b < ctx->n_buckets; ++b) {
             ctx->offsets[size_t(b)] = run;
-            run += counts[size_t(b)];
+            run += (counts[size_t(b)] + kListPad - 1) / kListPad * kListPad;  // padded to groups of four
         }
         ctx->offsets[size_t(ctx->n_buckets)] = run;
         ctx->n_cand = run;
@@ -608,6 +609,16 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
                                 cudaMemcpyHostToDevice, s);
         if (!e && ctx->rbf.water)
             e = cudaMemcpyAsync(dev + l.depth, ctx->depth.data(), ctx->depth.size() * 4, cudaMemcpyHostToDevice, s);
+        // the null record that pads the lists: centre far away (its squared
+        // distance stays finite), a weight scale of the kernel's sign, value 0
+        // and depth 0, so that its weight and its terms are exactly 0
+        static const float4 null_gauss = make_float4(1e18f, 1e18f, -1.f, 0.f);
+        static const float4 null_wend = make_float4(1e18f, 1e18f, 1.f, 0.f);
+        if (!e)
+            e = cudaMemcpyAsync(dev + l.recs + size_t(ctx->n_leaves) * 16,
+                                ctx->rbf.kernel == HF_RBF_WENDLAND_C2 ? &null_wend : &null_gauss, 16,
+                                cudaMemcpyHostToDevice, s);
+        if (!e && ctx->rbf.water) e = cudaMemsetAsync(dev + l.depth + size_t(ctx->n_leaves) * 4, 0, 4, s);
         if (e) return cuda_fail(e, "upload of the quadtree");
         ctx->dev = dev;
         ctx->dev_bytes = bytes;

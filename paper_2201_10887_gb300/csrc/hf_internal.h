@@ -58,11 +58,18 @@ struct LookupTables {
     int32_t nx_fin, ny_fin;
 };
 
+// Each bucket's list holds its candidates in ascending leaf order, padded to
+// a multiple of 4 entries with `sentinel` (= the leaf count), so that lists
+// start on 16-byte boundaries and are read four entries per load.  Record
+// `sentinel` is a null record whose weight is exactly 0 (centre far away,
+// value 0, depth 0), so padding adds nothing to the sums.
+constexpr int kListPad = 4;
 struct ListsView {
-    const int64_t* offsets;  // n_buckets + 1
-    int32_t* idx;            // candidate leaf indices, ascending within a bucket
-    float4* recs;            // per leaf: centre x, y (domain-local), -log2(e)/(2 sigma^2 c^2), value
-    const float* depth;      // per leaf water depth (water layer only, else null)
+    const int64_t* offsets;  // n_buckets + 1, multiples of kListPad
+    int32_t* idx;            // candidate leaf indices, ascending within a bucket, then padding
+    float4* recs;            // per leaf (+ the null record): centre x, y (domain-local), weight scale, value
+    const float* depth;      // per leaf (+ 0 for the null record) water depth (water layer only, else null)
+    int32_t sentinel;        // index of the null record = number of leaves
 };
 
 // Compact candidate lists of the reduced-precision discretization: per

@@ -218,7 +218,12 @@ __global__ void __launch_bounds__(256) k_fill_lists(const __grid_constant__ Fill
     const int64_t n = for_each_candidate(et, Lb, bx, by, [&](int64_t k, int64_t leaf) {
         if (k < cap) out[k] = int32_t(leaf);
     });
-    if (n != cap) report(a.status, kStatusData, uint32_t(id));
+    // the host sized the list as its count rounded up to kListPad
+    if (n > cap || cap - n >= kListPad) {
+        report(a.status, kStatusData, uint32_t(id));
+        return;
+    }
+    for (int64_t k = n; k < cap; ++k) out[k] = a.lv.sentinel;
 }
 
 int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
@@ -261,7 +266,9 @@ __global__ void __launch_bounds__(256) k_fill_compact(const __grid_constant__ Fi
     if (!bucket_of_bit(bk, w, int(g & 63), Lb, bx, by, id)) return;
     const int M = a.et.leaves.max_level;
     const float x0q = float(bx << (M - Lb + 1)), y0q = float(by << (M - Lb + 1));
-    const int64_t beg = a.lv.offsets[id], n = a.lv.offsets[id + 1] - beg;
+    const int64_t beg = a.lv.offsets[id];
+    int64_t n = a.lv.offsets[id + 1] - beg;
+    while (n > 0 && a.lv.idx[beg + n - 1] == a.lv.sentinel) --n;  // drop the padding
     const int64_t pb = cv.pair_offsets[id];
     for (int64_t m = 0; m < 2 * ((n + 1) / 2); m += 2) {
         float xs[2], ys[2];
@@ -442,18 +449,25 @@ __device__ __forceinline__ void texel_rbf(const DiscCascade& q, float K, const L
         return;
     }
     const int64_t beg = __ldg(lv.offsets + bucket);
-    const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
-    const int32_t* ids = lv.idx + beg;
+    const int ng = int(__ldg(lv.offsets + bucket + 1) - beg) / kListPad;
+    // lists start on 16-byte boundaries and are padded to groups of four
+    // entries (null records weigh exactly 0): one load brings four indices
+    const int4* groups = reinterpret_cast<const int4*>(lv.idx + beg);
     float sw = 0.f, swv = 0.f, swd = 0.f;
-#pragma unroll 4
-    for (int k = 0; k < n; ++k) {
-        const int id = __ldg(ids + k);
+    auto term = [&](int id) {
         const float4 r = __ldg(lv.recs + id);
         const float dx = r.x - px, dy = r.y - py;
         const float w = rbf_weight<KERNEL>(r.z * fmaf(dx, dx, dy * dy), K);
         sw += w;
         swv = fmaf(w, r.w, swv);
         if (WATER) swd = fmaf(w, __ldg(lv.depth + id), swd);
+    };
+    for (int g = 0; g < ng; ++g) {
+        const int4 q4 = __ldg(groups + g);
+        term(q4.x);
+        term(q4.y);
+        term(q4.z);
+        term(q4.w);
     }
     const float v = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
     *out = v;
@@ -476,7 +490,7 @@ __device__ __forceinline__ void tile_texel(int t, int& di, int& dj) {
 }
 
 template <bool WATER, int KERNEL>
-__global__ void __launch_bounds__(256) k_discretize_f32(const __grid_constant__ DiscParams p,
+__global__ void __launch_bounds__(256, 8) k_discretize_f32(const __grid_constant__ DiscParams p,
                                                         const __grid_constant__ LookupTables lt,
                                                         const ListsView lv, DevStatus* status) {
     wait_for_predecessor();
@@ -665,9 +679,10 @@ __global__ void __launch_bounds__(256) k_stats_f32(const __grid_constant__ DiscP
                 const int n = int(__ldg(lv.offsets + bucket + 1) - beg);
                 const int32_t* ids = lv.idx + beg;
                 vis = 1;
-                cand = unsigned(n);
                 for (int k = 0; k < n; ++k) {
-                    const float4 r = __ldg(lv.recs + __ldg(ids + k));
+                    const int id = __ldg(ids + k);
+                    cand += id != lv.sentinel ? 1u : 0u;  // padding is not a candidate
+                    const float4 r = __ldg(lv.recs + id);
                     const float dx = r.x - px, dy = r.y - py;
                     infl += rbf_weight<KERNEL>(r.z * fmaf(dx, dx, dy * dy), p.K) > 0.f ? 1u : 0u;
                 }

@@ -282,7 +282,9 @@ def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0, water
 
     Returns t (world distance), hit (0 miss, 1 + first cascade hit, + 0x80
     when that hit is on the water surface), seg (length of the first-hit
-    cascade's ray segment), visits.  ``water_textures`` (one per cascade)
+    cascade's ray segment), visits.  mode 0: per-patch DDA; 1: max-mip
+    traversal climbing one level per step; 2: climbing at once to the
+    coarsest node entered.  ``water_textures`` (one per cascade)
     adds the water surface: inside each cascade the first surface met wins."""
     C = len(cascades)
     rc = rcascades(cascades)
@@ -303,7 +305,7 @@ def raycast(cam, tree, cascades, textures, mips=None, pixels=None, mode=0, water
         ms = [np.ascontiguousarray(m, np.float32) for m in mips]
         mp = (ct.POINTER(ct.c_float) * C)(*[_p(m, ct.c_float) for m in ms])
     else:
-        if mode == 1:
+        if mode in (1, 2):
             raise ValueError("mip traversal needs the max mipmaps")
         mp = None
     if pixels is None:

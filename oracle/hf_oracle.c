@@ -760,9 +760,15 @@ static int trace_dda(const float* tex, int N, const prj_ray* r, double ta, doubl
  * current level-0 patch (ci, cj) is tracked as integers; after a step the
  * walk climbs one level when it has left its parent node.  The part of the
  * segment above the top entry (the global maximum) cannot hit and is
- * skipped first.                                                          */
+ * skipped first.
+ * With `jump` (the improved traversal after Dick et al., who refine Tevs et
+ * al.'s walk; the paper names it without describing it -- our reading): after
+ * a step the walk climbs at once to the coarsest node it has just entered,
+ * the level of the highest bit in which the old and new patch coordinates
+ * differ, instead of one level per step.  Neither rule skips a node that the
+ * ray could meet below its maximum, so both find the DDA's first hit.      */
 static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r, double ta,
-                     double tb, double* t_hit, long long* visits) {
+                     double tb, double* t_hit, long long* visits, int jump) {
     int P = mip_P(N), K = 0;
     while ((1 << K) < P) K++;
     long off[32];
@@ -793,7 +799,7 @@ static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r
             if (test_patch(tex, N, ci, cj, r, t, te, t_hit)) return 1;
         }
         if (te >= tb) return 0;
-        int oi = ni, oj = nj;
+        int oi = ni, oj = nj, pi = ci, pj = cj;
         if (tx <= ty) {
             ci = r->du > 0.0 ? (ni + 1) * size : ni * size - 1;
             int c2 = (int)floor(r->ev + te * r->dv);
@@ -807,7 +813,13 @@ static int trace_mip(const float* tex, const float* mip, int N, const prj_ray* r
         }
         if (ci < 0 || ci >= P || cj < 0 || cj >= P) return 0;
         t = te;
-        if (k < K && ((ci >> (k + 1)) != (oi >> 1) || (cj >> (k + 1)) != (oj >> 1))) k++;
+        if (jump) {
+            int diff = (ci ^ pi) | (cj ^ pj), b = -1;
+            while (diff) { diff >>= 1; b++; }
+            if (b > k) k = b < K ? b : K;
+        } else if (k < K && ((ci >> (k + 1)) != (oi >> 1) || (cj >> (k + 1)) != (oj >> 1))) {
+            k++;
+        }
     }
     return 0;
 }
@@ -849,7 +861,7 @@ static int trace_cascade(const float* tex, const float* wtex, const float* mip, 
     double t1 = 0.0, t2 = 0.0;
     int h1 = stop > 0 ? trace_boxes(mip, N, stop, r, ta, tb, &t1, visits)
              : mode == 0 ? trace_dda(tex, N, r, ta, tb, &t1, visits)
-                         : trace_mip(tex, mip, N, r, ta, tb, &t1, visits);
+                         : trace_mip(tex, mip, N, r, ta, tb, &t1, visits, mode == 2);
     int h2 = wtex ? trace_dda(wtex, N, r, ta, tb, &t2, visits) : 0;
     *on_water = h2 && (!h1 || t2 <= t1);
     if (*on_water) {

@@ -119,7 +119,9 @@ void orc_maxmip(const float* tex, int N, float* mip);
 /* first root of bilinear(a,b) - z along a ray segment inside one patch */
 int orc_ray_patch(double h00, double h10, double h01, double h11, double a0, double b0,
                   double z0, double da, double db, double dz, double dt, double* tau);
-/* mode 0: per-patch DDA; mode 1: max-mip traversal (needs mips) of the terrain;
+/* mode 0: per-patch DDA; mode 1: max-mip traversal (needs mips) of the terrain,
+ * one level up per step (Tevs et al.); mode 2: the same traversal climbing at once
+ * to the coarsest node entered (our reading of Dick et al.'s improved traversal);
  * wtex (NULL = none): water surface textures, traced by DDA, the first surface met
  * wins inside each cascade.  Outputs per pixel: t (world distance from the eye),
  * hit (0 = miss, 1 + first cascade hit, + 0x80 if that hit is on the water surface),

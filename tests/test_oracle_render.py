@@ -409,3 +409,32 @@ def test_coarse_stop_matches_box_field_marching(orc, tiny, seed, L):
     assert both.sum() > 100 and np.all(hit[hit0 > 0] > 0)
     assert np.all(t[both] <= t0[both] + 1e-9 * t0[both])
     assert np.mean(t[both] < t0[both] * (1 - 1e-6)) > 0.3     # the coarse surface is really coarser
+
+
+@pytest.mark.parametrize("N,C", [(128, 3), (97, 2), (256, 1)])
+def test_jump_ascent_traversal_equals_dda(orc, tiny, N, C):
+    """The max-mip walk that climbs at once to the coarsest node it entered
+    (the improved traversal after Dick et al.) finds the DDA's first hit on
+    every pixel, as the one-level-per-step walk does, and visits no more
+    nodes than the DDA walks patches."""
+    cells = orc.Cells(tiny.tree)
+    cam = tiny.cameras[0].with_(n_cascades=C, cascade_size=N)
+    v = orc.fit(cam, tiny.tree, cells)
+    casl, texs, mips = [], [], []
+    for k in range(v.n_cascades):
+        c = v.cas[k]
+        tex = orc.texel_heights(c, cells, tiny.sigma, tiny.radius).reshape(c.N, c.N).astype(np.float32)
+        casl.append(c)
+        texs.append(tex)
+        mips.append(orc.maxmip(tex))
+    t0, h0, s0, v0 = orc.raycast(cam, tiny.tree, casl, texs, mode=0)
+    t1, h1, s1, v1 = orc.raycast(cam, tiny.tree, casl, texs, mips, mode=1)
+    t2, h2, s2, v2 = orc.raycast(cam, tiny.tree, casl, texs, mips, mode=2)
+    assert np.array_equal(h0, h2) and np.array_equal(h1, h2)
+    both = h0 > 0
+    assert both.mean() > 0.3
+    assert np.max(np.abs(t0[both] - t2[both]) / s0[both]) < 1e-9
+    assert np.array_equal(t1[both], t2[both])
+    assert v2.sum() < v0.sum()
+    print(f"N={N} C={C}: visits per ray DDA {v0.mean():.1f}, one level per step {v1.mean():.1f}, "
+          f"climb to the node entered {v2.mean():.1f}")

@@ -575,6 +575,8 @@ def run_ours(args, rank, world, local_rank):
         line["temporal_reuse"] = time_temporal_reuse(scene, args.warmup, dev, flush, stream)
         line["coarse_stop"] = time_coarse_stop(scene, cams, sched[:min(len(sched), 120)], args.warmup, dev,
                                                flush, stream)
+        line["traversal_variants"] = time_traversal_variants(scene, cams, sched[:min(len(sched), 120)],
+                                                             args.warmup, dev, flush, stream)
     if world == 1 and not args.no_blocks:
         # the other workloads, short: terrain + water, 64-tile batched frames, serving
         line["flood"] = flood_block(args, min(len(sched), 20), args.warmup)
@@ -960,6 +962,46 @@ def batch_block(args, steps: int, warmup: int) -> dict:
         r.close()
     del rs, views
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def time_traversal_variants(scene, cams, sched, warmup, dev, flush, stream) -> dict:
+    """The two max-mipmap walks of the ray cast on the main line's frames
+    (L2 flushed between frames): ray-cast time and node visits per ray of
+    traversal 0 (one level up per step, Tevs et al.) and traversal 1 (climb
+    at once to the coarsest node entered; the reading of Dick et al.'s
+    improved traversal).  Both find the same first hit."""
+    import torch
+    from paper_2201_10887_gb300 import Renderer
+    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
+    out = {}
+    for trav in (0, 1):
+        cl = [c.with_(traversal=trav) for c in cams]
+        for f in sched[:warmup]:
+            r.render(cl[f])
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in sched]
+        for k, f in enumerate(sched):
+            r.set_camera(cl[f])
+            r.discretize()
+            r.build_maxmip()
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            r.raycast()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        visits = 0
+        frames = sorted(set(sched))[:12]
+        for f in frames:
+            r.render(cl[f])
+            visits += r.ray_stats()["visits"]
+        out[f"traversal_{trav}"] = {"raycast_ms": statistics.mean(e[0].elapsed_time(e[1]) for e in ev),
+                                    "visits_per_ray": visits / (len(frames) * cams[0].width * cams[0].height)}
+    out["note"] = ("traversal 0: one level up per step (Tevs et al.); 1: climb to the coarsest node entered "
+                   "(reading of Dick et al.'s improved traversal); L2 flushed before each ray cast")
+    r.sync()
+    r.close()
+    del r
     torch.cuda.empty_cache()
     return out
 

@@ -133,7 +133,14 @@ typedef struct {
  * multiple of h_m, so texel (i, j) sits on the lattice point (snap_x + i,
  * snap_y + j) of spacing h_m whatever the camera's position.  The lattice
  * fit needs cascade_size >= 4; its texels are up to 2^(1/n) coarser than
- * the stable fit's.  reserved must be 0.
+ * the stable fit's.
+ * traversal selects the max-mipmap walk of the ray cast (Section 5): 0 is
+ * Tevs et al.'s, which after each step climbs one level when the ray has left
+ * its parent node; 1 climbs at once to the coarsest node the ray has just
+ * entered -- our reading of the improved traversal the paper attributes to
+ * Dick et al. (Section 1), which it names without describing.  Both find the
+ * same first hit; 1 is not available with the water layer, the coarse-level
+ * stop or batched frames.
  * lod_pixels > 0 turns on the coarse-level stop (after the LOD-dependent early
  * ray termination the paper cites): in cascade c the ray stops at the box tops
  * of max-mipmap level L_c instead of descending to the bilinear patches, L_c
@@ -150,7 +157,7 @@ typedef struct {
     int32_t n_cascades, cascade_size;
     double split_lambda, overlap_frac;
     int32_t texel_ladder;
-    int32_t reserved;
+    int32_t traversal;
     double lod_pixels;
 } hf_camera;
 

@@ -167,6 +167,7 @@ struct ViewSlot {
 struct PersistentLayout {
     size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx;
     size_t pair_offsets, pairs;          // reduced-precision lists (0 bytes for FP32)
+    size_t cellmap;                      // per finest cell {first group, groups} (0 bytes if not kept)
     size_t depth;                         // water depths (0 bytes without the water layer)
     size_t total;
 };
@@ -210,6 +211,7 @@ struct hf_ctx {
         l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
         l.pairs = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
         l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves + 1) * 4 : 0));
+        l.cellmap = o; o = align256(o + (keep_cellmap() ? size_t(buckets.nx[M]) * size_t(buckets.ny[M]) * 8 : 0));
         l.total = o;
         return l;
     }
@@ -233,7 +235,13 @@ struct hf_ctx {
         t.inv_c_fin = float(1.0 / c_fin);
         t.nx_fin = buckets.nx[M];
         t.ny_fin = buckets.ny[M];
+        t.cellmap = device && keep_cellmap() ? reinterpret_cast<const uint2*>(dev + lay.cellmap) : nullptr;
         return t;
+    }
+    // the cell map is kept for grids of at most kCellMapMaxCells finest cells
+    // whose list groups are numbered in 32 bits
+    bool keep_cellmap() const {
+        return int64_t(buckets.nx[M]) * buckets.ny[M] <= kCellMapMaxCells && n_cand / kListPad < (int64_t(1) << 32);
     }
     CompactView compact() const {
         CompactView v;
@@ -315,7 +323,9 @@ int check_camera(const hf_camera& c) {
     if (!(c.overlap_frac >= 0.0 && c.overlap_frac <= 1.0)) return fail(HF_ERR_ARG, "overlap_frac must be in [0, 1]");
     if (c.texel_ladder < 0 || c.texel_ladder > 64) return fail(HF_ERR_ARG, "texel_ladder must be 0..64");
     if (c.texel_ladder > 0 && c.cascade_size < 4) return fail(HF_ERR_ARG, "the lattice fit needs cascade_size >= 4");
-    if (c.reserved != 0) return fail(HF_ERR_ARG, "hf_camera.reserved must be 0");
+    if (c.traversal != 0 && c.traversal != 1) return fail(HF_ERR_ARG, "hf_camera.traversal must be 0 or 1");
+    if (c.traversal == 1 && c.lod_pixels > 0.0)
+        return fail(HF_ERR_ARG, "traversal 1 is not available with the coarse-level stop");
     if (!(c.lod_pixels >= 0.0 && c.lod_pixels <= 1e6)) return fail(HF_ERR_ARG, "lod_pixels must be in [0, 1e6]");
     return HF_OK;
 }
@@ -624,6 +634,11 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
         ctx->dev_bytes = bytes;
         e = launch_fill_lists(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
         if (e) return cuda_fail(e, "influence-list kernel launch");
+        if (ctx->keep_cellmap()) {
+            e = launch_fill_cellmap(ctx->lookup_tables(true), ctx->lists(), reinterpret_cast<uint2*>(dev + l.cellmap),
+                                    ctx->d_status(), stream);
+            if (e) return cuda_fail(e, "cell-map kernel launch");
+        }
         if (ctx->rbf.precision != HF_PREC_FP32) {
             e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
                                     ctx->rbf.precision, stream);
@@ -713,6 +728,8 @@ int set_camera(hf_ctx* ctx, int32_t slot, const hf_camera* cam, void* dev_view, 
     if (int rc = check_camera(c)) return rc;
     if (c.lod_pixels > 0.0 && ctx->rbf.water)
         return fail(HF_ERR_ARG, "the coarse-level stop is not available with the water layer");
+    if (c.traversal == 1 && ctx->rbf.water)
+        return fail(HF_ERR_ARG, "traversal 1 is not available with the water layer");
     if (reinterpret_cast<uintptr_t>(dev_view) & 255) return fail(HF_ERR_ARG, "view buffer must be 256-byte aligned");
     const size_t need = per_view_bytes(c.n_cascades, c.cascade_size, ctx->rbf.water != 0);
     if (bytes < need) return fail(HF_ERR_NOMEM, "view buffer has %zu bytes, %zu needed", bytes, need);
@@ -960,6 +977,7 @@ RayParams ray_params(const ViewSlot* v, bool water) {
     std::memset(&rp, 0, sizeof(rp));
     rp.C = c.n_cascades;
     rp.water = water ? 1 : 0;
+    rp.jump = c.traversal == 1 ? 1 : 0;
     rp.W = c.width;
     rp.H = c.height;
     rp.ez = float(v->eye_local[2]);
@@ -1114,6 +1132,8 @@ int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
         if (it.ctx->rbf.water) return fail(HF_ERR_ARG, "batch item %d: batched frames do not carry the water layer", i);
         if (it.ctx->rbf.kernel != HF_RBF_GAUSSIAN)
             return fail(HF_ERR_ARG, "batch item %d: batched frames use the Gaussian kernel only", i);
+        if (v->cam.traversal != 0)
+            return fail(HF_ERR_ARG, "batch item %d: batched frames use traversal 0 only", i);
         if (!it.t_dev || !it.hit_dev) return fail(HF_ERR_ARG, "batch item %d: null output buffer", i);
         nc += v->cam.n_cascades;
     }

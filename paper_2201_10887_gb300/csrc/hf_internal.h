@@ -51,11 +51,17 @@ struct EnumTables {
 // Texel -> bucket lookup.  Buckets are the leaves at or below level
 // `bucket_level`; coarser leaves are split into their level-bucket_level
 // descendants, so that each list covers a small square.
+// cellmap (optional, for grids of at most kCellMapMaxCells finest cells):
+// per finest cell, row-major, the list of its bucket as {first group of four
+// entries, number of groups}, so that a texel finds its list with one load
+// instead of the per-level bitmap probes and the offsets.
+constexpr int64_t kCellMapMaxCells = int64_t(1) << 28;
 struct LookupTables {
     Bitmaps buckets;
     int32_t bucket_level;
     float inv_c_fin;  // 1 / finest cell edge
     int32_t nx_fin, ny_fin;
+    const uint2* cellmap;  // null: look the bucket up in the bitmaps
 };
 
 // Each bucket's list holds its candidates in ascending leaf order, padded to
@@ -171,6 +177,7 @@ struct RayParams {
     int32_t C, W, H;
     int32_t water;           // 1: rays meet the terrain or the water surface, whichever comes first
     int32_t coarse;          // 1: some cascade has a coarse-level stop (RayCascade.stop_level > 0)
+    int32_t jump;            // 1: after a step the walk climbs to the coarsest node entered (hf_camera.traversal)
     float ez;                // eye height (m)
     float F[3], R[3], U[3];  // camera basis
     float px_a, px_b, py_a, py_b;  // screen coordinates: s = fma(pixel, a, b), s in [-tan, tan]
@@ -231,6 +238,9 @@ struct BatchHeader {
 // Kernel launchers (hf_kernels.cu); they return a cudaError_t value.
 int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
+// Fills the cell map `cellmap` from lt's bucket bitmaps and the list offsets.
+int launch_fill_cellmap(const LookupTables& lt, const ListsView& lv, uint2* cellmap, DevStatus* status,
+                        void* stream);
 int launch_prep(const PrepParams& p, void* stream);
 int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                         const CompactView& cv, int precision, void* stream);

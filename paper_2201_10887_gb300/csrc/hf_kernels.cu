@@ -387,6 +387,40 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
     return found;
 }
 
+// The cell map: one thread per finest cell writes its bucket's list as
+// {first group, groups} (lists are padded to groups of kListPad entries).
+__global__ void __launch_bounds__(256) k_fill_cellmap(const __grid_constant__ LookupTables lt, const ListsView lv,
+                                                      uint2* cellmap, DevStatus* status) {
+    const int64_t cell = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= int64_t(lt.nx_fin) * lt.ny_fin) return;
+    const int fx = int(cell % lt.nx_fin), fy = int(cell / lt.nx_fin);
+    const Bitmaps& bk = lt.buckets;
+    const int M = bk.max_level;
+    int64_t found = -1;
+    for (int L = lt.bucket_level; L <= M; ++L) {
+        const int sh = M - L;
+        const int64_t b = int64_t(fy >> sh) * bk.nx[L] + (fx >> sh);
+        const int64_t w = bk.word_off[L] + (b >> 6);
+        const uint64_t word = bk.bits[w];
+        if ((word >> (b & 63)) & 1ull) found = bk.base[L] + bk.prefix[w] + popc64(word & ((1ull << (b & 63)) - 1ull));
+    }
+    if (found < 0) {
+        report(status, kStatusData, uint32_t(cell));
+        cellmap[cell] = make_uint2(0u, 0u);
+        return;
+    }
+    const int64_t beg = lv.offsets[found], end = lv.offsets[found + 1];
+    cellmap[cell] = make_uint2(uint32_t(beg / kListPad), uint32_t((end - beg) / kListPad));
+}
+
+int launch_fill_cellmap(const LookupTables& lt, const ListsView& lv, uint2* cellmap, DevStatus* status,
+                        void* stream) {
+    const int64_t cells = int64_t(lt.nx_fin) * lt.ny_fin;
+    if (cells == 0) return cudaSuccess;
+    k_fill_cellmap<<<dim3(unsigned((cells + 255) / 256)), 256, 0, cudaStream_t(stream)>>>(lt, lv, cellmap, status);
+    return cudaGetLastError();
+}
+
 // Temporal reuse (hf_discretize_reuse): the index of texel (i, j) in the
 // earlier frame's texture on the same lattice, or -1 (no source, or outside
 // it).  A texel that frame computed (anything but -inf) has the same position
@@ -441,18 +475,28 @@ __device__ __forceinline__ void texel_rbf(const DiscCascade& q, float K, const L
     const size_t o = size_t(j) * q.N + i;
     float* out = q.tex + o;
     const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
-    const int64_t bucket = lookup_bucket(lt, px, py);
-    if (bucket < 0) {
-        report(status, kStatusData, 0xFFFFFFFFu);
-        *out = __int_as_float(0x7fc00000);
-        if (WATER) q.wtex[o] = __int_as_float(0x7fc00000);
-        return;
-    }
-    const int64_t beg = __ldg(lv.offsets + bucket);
-    const int ng = int(__ldg(lv.offsets + bucket + 1) - beg) / kListPad;
     // lists start on 16-byte boundaries and are padded to groups of four
     // entries (null records weigh exactly 0): one load brings four indices
-    const int4* groups = reinterpret_cast<const int4*>(lv.idx + beg);
+    const int4* groups;
+    int ng;
+    if (lt.cellmap) {  // one load: the finest cell's {first group, groups}
+        const int fx = min(max(int(floorf(px * lt.inv_c_fin)), 0), lt.nx_fin - 1);
+        const int fy = min(max(int(floorf(py * lt.inv_c_fin)), 0), lt.ny_fin - 1);
+        const uint2 e = __ldg(lt.cellmap + size_t(fy) * lt.nx_fin + fx);
+        groups = reinterpret_cast<const int4*>(lv.idx) + e.x;
+        ng = int(e.y);
+    } else {
+        const int64_t bucket = lookup_bucket(lt, px, py);
+        if (bucket < 0) {
+            report(status, kStatusData, 0xFFFFFFFFu);
+            *out = __int_as_float(0x7fc00000);
+            if (WATER) q.wtex[o] = __int_as_float(0x7fc00000);
+            return;
+        }
+        const int64_t beg = __ldg(lv.offsets + bucket);
+        ng = int(__ldg(lv.offsets + bucket + 1) - beg) / kListPad;
+        groups = reinterpret_cast<const int4*>(lv.idx + beg);
+    }
     float sw = 0.f, swv = 0.f, swd = 0.f;
     auto term = [&](int id) {
         const float4 r = __ldg(lv.recs + id);
@@ -1028,7 +1072,7 @@ struct RayDir {
 // zero component takes the non-positive branch, which leaves the walk as it
 // would be: the exit time along it is infinite, and the clamp of the other
 // coordinate returns the current cell.
-template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE>
+template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE, bool JUMP = false>
 __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __restrict__ off, const RayDir& d,
                                               float ez, float ta, float tb, float& t_hit, bool& on_water,
                                               DevStatus* status, uint32_t pixel, unsigned& visits, unsigned& tests) {
@@ -1125,7 +1169,11 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
         ci = nci;
         cj = ncj;
         t = te;
-        if (k < K && (diff >> (k + 1)) != 0) ++k;
+        if (JUMP) {  // climb to the coarsest node entered: the highest bit in which the patches differ
+            if ((diff >> (k + 1)) != 0) k = min(31 - __clz(diff), K);
+        } else if (k < K && (diff >> (k + 1)) != 0) {
+            ++k;
+        }
     }
     report(status, kStatusTimeout, pixel);
     return false;
@@ -1171,7 +1219,7 @@ __device__ __forceinline__ bool cascade_interval(const RayCascade& c, const RayD
 // Section 5: the blend runs linearly in projected depth across the overlap
 // band of cascades c and c+1 when both are hit); 0x80 marks a first-hit
 // cascade whose hit is on the water surface.
-template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE>
+template <bool COUNT, bool COH, bool UNION, int SIGNS, bool COARSE, bool JUMP = false>
 __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_off)[kMaxLevels], const RayDir& d,
                                               DevStatus* status, uint32_t pix, unsigned& visits, unsigned& tests,
                                               float& t, int& hit) {
@@ -1182,7 +1230,8 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
         float ta, tb, tc;
         bool wet = false;
         if (!cascade_interval(cc, d, ta, tb)) continue;
-        if (!trace_cascade<COUNT, COH, UNION, SIGNS, COARSE>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix, visits, tests))
+        if (!trace_cascade<COUNT, COH, UNION, SIGNS, COARSE, JUMP>(cc, s_off[c], d, p.ez, ta, tb, tc, wet, status, pix,
+                                                                  visits, tests))
             continue;
         hit = (1 + c) | (wet ? 0x80 : 0);
         t = tc;
@@ -1193,8 +1242,8 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
                 float ta2, tb2, t2;
                 bool wet2 = false;
                 if (cascade_interval(cn, d, ta2, tb2) &&
-                    trace_cascade<COUNT, COH, UNION, SIGNS, COARSE>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2, status, pix,
-                                                     visits, tests)) {
+                    trace_cascade<COUNT, COH, UNION, SIGNS, COARSE, JUMP>(cn, s_off[c + 1], d, p.ez, ta2, tb2, t2, wet2,
+                                                                       status, pix, visits, tests)) {
                     const float al = fminf(fmaxf(__fsub_rn(s, cn.near_d) / (cc.far_ext - cn.near_d), 0.f), 1.f);
                     t = fmaf(al, t2 - tc, tc);
                 }
@@ -1203,7 +1252,7 @@ __device__ __forceinline__ void cast_cascades(const RayParams& p, const int (*s_
     }
 }
 
-template <bool COUNT, bool COH, bool WATER = false, bool COARSE = false>
+template <bool COUNT, bool COH, bool WATER = false, bool COARSE = false, bool JUMP = false>
 __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_off)[kMaxLevels], DevStatus* status,
                                               int x, int y, unsigned& visits, unsigned& tests) {
     if (x >= p.W || y >= p.H) return;
@@ -1229,14 +1278,14 @@ __device__ __forceinline__ void raycast_pixel(const RayParams& p, const int (*s_
     int hit;
     float t;
     switch ((d.dx > 0.f ? 1 : 0) | (d.dy > 0.f ? 2 : 0) | (d.dz < 0.f ? 4 : 0)) {
-    case 0: cast_cascades<COUNT, COH, WATER, 0, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 1: cast_cascades<COUNT, COH, WATER, 1, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 2: cast_cascades<COUNT, COH, WATER, 2, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 3: cast_cascades<COUNT, COH, WATER, 3, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 4: cast_cascades<COUNT, COH, WATER, 4, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 5: cast_cascades<COUNT, COH, WATER, 5, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    case 6: cast_cascades<COUNT, COH, WATER, 6, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
-    default: cast_cascades<COUNT, COH, WATER, 7, COARSE>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 0: cast_cascades<COUNT, COH, WATER, 0, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 1: cast_cascades<COUNT, COH, WATER, 1, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 2: cast_cascades<COUNT, COH, WATER, 2, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 3: cast_cascades<COUNT, COH, WATER, 3, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 4: cast_cascades<COUNT, COH, WATER, 4, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 5: cast_cascades<COUNT, COH, WATER, 5, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    case 6: cast_cascades<COUNT, COH, WATER, 6, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
+    default: cast_cascades<COUNT, COH, WATER, 7, COARSE, JUMP>(p, s_off, d, status, pix, visits, tests, t, hit); break;
     }
     if (!COUNT) {
         p.t_out[pix] = t;
@@ -1259,7 +1308,7 @@ __device__ __forceinline__ void load_level_offsets(const RayParams& p, int (*s_o
 // (8 and 64 registers for the walk over both surfaces).  A CTA covers 16 x 8
 // pixels, each warp an 8 x 4 patch of them: neighbouring rays in a square
 // patch take more of the same steps than in a 16 x 2 strip (2 % faster).
-template <bool COUNT, bool WATER, bool COARSE>
+template <bool COUNT, bool WATER, bool COARSE, bool JUMP = false>
 __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_constant__ RayParams p, DevStatus* status) {
     wait_for_predecessor();
     __shared__ int s_off[HF_MAX_CASCADES][kMaxLevels];
@@ -1267,7 +1316,7 @@ __global__ void __launch_bounds__(128, WATER ? 8 : 9) k_raycast(const __grid_con
     load_level_offsets<false>(p, s_off, t, 128);
     __syncthreads();
     unsigned visits = 0, tests = 0;
-    raycast_pixel<COUNT, false, WATER, COARSE>(p, s_off, status, blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7),
+    raycast_pixel<COUNT, false, WATER, COARSE, JUMP>(p, s_off, status, blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7),
                                        blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3), visits, tests);
     if (COUNT) {
         visits = __reduce_add_sync(0xffffffffu, visits);
@@ -1286,6 +1335,8 @@ int launch_raycast_t(const RayParams& p, DevStatus* status, void* stream) {
         return launch_dependent(k_raycast<COUNT, true, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
     if (p.coarse)
         return launch_dependent(k_raycast<COUNT, false, true>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
+    if (p.jump)
+        return launch_dependent(k_raycast<COUNT, false, false, true>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
     return launch_dependent(k_raycast<COUNT, false, false>, grid, dim3(16, 8), cudaStream_t(stream), p, status);
 }
 

@@ -58,7 +58,7 @@ class hf_camera(ct.Structure):
                 ("vfov", ct.c_double), ("znear", ct.c_double), ("zfar", ct.c_double),
                 ("width", ct.c_int32), ("height", ct.c_int32), ("n_cascades", ct.c_int32),
                 ("cascade_size", ct.c_int32), ("split_lambda", ct.c_double),
-                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int32), ("reserved", ct.c_int32),
+                ("overlap_frac", ct.c_double), ("texel_ladder", ct.c_int32), ("traversal", ct.c_int32),
                 ("lod_pixels", ct.c_double)]
 
 

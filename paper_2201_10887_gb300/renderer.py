@@ -16,12 +16,13 @@ from . import hf
 def camera_struct(cam) -> hf.hf_camera:
     """hf_camera from any object with eye, forward, up, vfov, znear, zfar,
     width, height, n_cascades, cascade_size, split_lambda, overlap_frac and
-    optionally texel_ladder (0 = the stable fit) and lod_pixels (0 = the exact
-    surface)."""
+    optionally texel_ladder (0 = the stable fit), lod_pixels (0 = the exact
+    surface) and traversal (0 = one level up per step, 1 = climb to the
+    coarsest node entered)."""
     return hf.hf_camera((ct.c_double * 3)(*cam.eye), (ct.c_double * 3)(*cam.forward),
                         (ct.c_double * 3)(*cam.up), cam.vfov, cam.znear, cam.zfar, cam.width,
                         cam.height, cam.n_cascades, cam.cascade_size, cam.split_lambda,
-                        cam.overlap_frac, int(getattr(cam, "texel_ladder", 0)), 0,
+                        cam.overlap_frac, int(getattr(cam, "texel_ladder", 0)), int(getattr(cam, "traversal", 0)),
                         float(getattr(cam, "lod_pixels", 0.0)))
 
 

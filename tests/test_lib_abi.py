@@ -145,7 +145,7 @@ def test_call_order_and_buffer_checks(hfmod, tiny):
         bad = camera_struct(bad_cam)
         assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
     bad = camera_struct(cam)
-    bad.reserved = 1
+    bad.traversal = 2
     assert lib.hf_set_camera(ctx, 1, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 30)) == hfmod.HF_ERR_ARG
     # reuse needs the persistent buffer first, like every device step
     assert lib.hf_discretize_reuse(ctx, 0, 1, None) == hfmod.HF_ERR_STATE
@@ -479,3 +479,20 @@ def test_noalloc_binding_checks_outputs_before_calling(hfmod):
     for what, outs in bad.items():
         with pytest.raises(ValueError):
             hfmod.check_noalloc_outputs(cam, outs, 0)
+
+
+def test_jump_traversal_refusals(hfmod, tiny):
+    """traversal = 1 (climb to the coarsest node entered) is refused with the
+    coarse-level stop and with the water layer before any device work."""
+    from paper_2201_10887_gb300.renderer import camera_struct
+    lib = hfmod.lib()
+    cam = tiny.cameras[0]
+    desc = hfmod.hf_quadtree_desc(tiny.tree.origin_x, tiny.tree.origin_y, tiny.tree.root_cell,
+                                  tiny.tree.root_nx, tiny.tree.root_ny, tiny.tree.max_level)
+    leaves = hfmod.leaves_array(tiny.tree.level, tiny.tree.ix, tiny.tree.iy, tiny.tree.value)
+    for water, kw in ((0, dict(lod_pixels=4.0)), (1, dict())):
+        ctx = hfmod.hf_create_quadtree(desc, leaves, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, water, 0))
+        bad = camera_struct(cam.with_(traversal=1, **kw))
+        rc = lib.hf_set_camera(ctx, 0, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 40))
+        assert rc == hfmod.HF_ERR_ARG and "traversal" in hfmod.hf_last_error()
+        hfmod.hf_destroy(ctx)

@@ -31,6 +31,7 @@ class Camera:
     overlap_frac: float = 0.05
     texel_ladder: int = 0         # 0: stable fit; n > 0: lattice fit, n texel sizes per octave
     lod_pixels: float = 0.0       # 0: exact surface; > 0: coarse-level stop at this many pixels
+    traversal: int = 0            # 0: max-mip walk one level up per step; 1: climb to the coarsest node entered
 
     def with_(self, **kw) -> "Camera":
         return replace(self, **kw)

@@ -168,6 +168,7 @@ struct PersistentLayout {
     size_t status, lbits, lprefix, bbits, bprefix, recs, offsets, idx;
     size_t pair_offsets, pairs;          // reduced-precision lists (0 bytes for FP32)
     size_t cellmap;                      // per finest cell {first group, groups} (0 bytes if not kept)
+    size_t pair_cellmap;                 // the same for the compact pair lists (reduced precision only)
     size_t depth;                         // water depths (0 bytes without the water layer)
     size_t total;
 };
@@ -186,7 +187,7 @@ struct hf_ctx {
     std::vector<int64_t> perm;     // input position -> sorted index
     std::vector<int64_t> offsets;  // n_buckets + 1
     std::vector<int64_t> pair_offsets;  // n_buckets + 1 (reduced precision only)
-    int64_t n_pairs = 0;
+    int64_t n_pairs = 0, max_pairs = 0;
     uint32_t kb2 = 0;              // packed level-0 scale bits of the compact lists
     std::vector<float> staged;     // values in sorted order for hf_update_values
     std::vector<float> depth;      // water depths in sorted order (water layer only)
@@ -212,6 +213,8 @@ struct hf_ctx {
         l.pairs = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
         l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves + 1) * 4 : 0));
         l.cellmap = o; o = align256(o + (keep_cellmap() ? size_t(buckets.nx[M]) * size_t(buckets.ny[M]) * 8 : 0));
+        l.pair_cellmap = o;
+        o = align256(o + (keep_pair_cellmap() ? size_t(buckets.nx[M]) * size_t(buckets.ny[M]) * 8 : 0));
         l.total = o;
         return l;
     }
@@ -243,6 +246,11 @@ struct hf_ctx {
     bool keep_cellmap() const {
         return int64_t(buckets.nx[M]) * buckets.ny[M] <= kCellMapMaxCells && n_cand / kListPad < (int64_t(1) << 32);
     }
+    // ... and for the compact lists: pairs numbered in 32 bits, at most 2^24 - 1 per list
+    bool keep_pair_cellmap() const {
+        return rbf.precision != HF_PREC_FP32 && int64_t(buckets.nx[M]) * buckets.ny[M] <= kCellMapMaxCells &&
+               n_pairs < (int64_t(1) << 32) && max_pairs < (int64_t(1) << 24);
+    }
     CompactView compact() const {
         CompactView v;
         v.pair_offsets = reinterpret_cast<const int64_t*>(dev + lay.pair_offsets);
@@ -250,6 +258,7 @@ struct hf_ctx {
         v.kb2 = kb2;
         v.q = float(0.5 * c_fin);
         v.inv_q = float(2.0 / c_fin);
+        v.cellmap = keep_pair_cellmap() ? reinterpret_cast<const uint2*>(dev + lay.pair_cellmap) : nullptr;
         return v;
     }
     ListsView lists() const {
@@ -572,6 +581,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
             for (int64_t b = 0; b < ctx->n_buckets; ++b) {
                 ctx->pair_offsets[size_t(b)] = pr;
                 pr += (counts[size_t(b)] + 1) / 2;
+                ctx->max_pairs = std::max(ctx->max_pairs, (counts[size_t(b)] + 1) / 2);
             }
             ctx->pair_offsets[size_t(ctx->n_buckets)] = pr;
             ctx->n_pairs = pr;
@@ -643,6 +653,12 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
             e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
                                     ctx->rbf.precision, stream);
             if (e) return cuda_fail(e, "compact-list kernel launch");
+            if (ctx->keep_pair_cellmap()) {
+                const CompactView cv = ctx->compact();
+                e = launch_fill_cellmap(ctx->lookup_tables(true), ctx->lists(),
+                                        reinterpret_cast<uint2*>(dev + l.pair_cellmap), ctx->d_status(), stream, &cv);
+                if (e) return cuda_fail(e, "compact cell-map kernel launch");
+            }
         }
         e = cudaStreamSynchronize(s);
         if (e) return cuda_fail(e, "influence-list build");

@@ -94,6 +94,9 @@ struct CompactView {
     uint4* pairs;                 // per pair
     float q, inv_q;               // half a finest cell (m) and its inverse
     uint32_t kb2;                 // (bits of the level-0 scale) * 0x10001, see above
+    // optional (as LookupTables.cellmap): per finest cell {first pair of its
+    // bucket's list, pairs | bucket level << 24}; null: bitmap lookup
+    const uint2* cellmap;
 };
 
 // Per-frame cascade data for the prep kernel (visible rows, texel coordinates).
@@ -238,9 +241,10 @@ struct BatchHeader {
 // Kernel launchers (hf_kernels.cu); they return a cudaError_t value.
 int launch_fill_lists(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
-// Fills the cell map `cellmap` from lt's bucket bitmaps and the list offsets.
+// Fills the cell map `cellmap` from lt's bucket bitmaps and the list offsets
+// (with `cv`, the map of the compact pair lists).
 int launch_fill_cellmap(const LookupTables& lt, const ListsView& lv, uint2* cellmap, DevStatus* status,
-                        void* stream);
+                        void* stream, const CompactView* cv = nullptr);
 int launch_prep(const PrepParams& p, void* stream);
 int launch_fill_compact(const EnumTables& et, const LookupTables& lt, const ListsView& lv,
                         const CompactView& cv, int precision, void* stream);

@@ -388,36 +388,51 @@ __device__ __forceinline__ int64_t lookup_bucket(const LookupTables& lt, float p
 }
 
 // The cell map: one thread per finest cell writes its bucket's list as
-// {first group, groups} (lists are padded to groups of kListPad entries).
+// {first group, groups} (lists are padded to groups of kListPad entries), or
+// for the compact lists {first pair, pairs | bucket level << 24}.
+template <bool COMPACT>
 __global__ void __launch_bounds__(256) k_fill_cellmap(const __grid_constant__ LookupTables lt, const ListsView lv,
-                                                      uint2* cellmap, DevStatus* status) {
+                                                      const CompactView cv, uint2* cellmap, DevStatus* status) {
     const int64_t cell = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (cell >= int64_t(lt.nx_fin) * lt.ny_fin) return;
     const int fx = int(cell % lt.nx_fin), fy = int(cell / lt.nx_fin);
     const Bitmaps& bk = lt.buckets;
     const int M = bk.max_level;
     int64_t found = -1;
+    int Lb = 0;
     for (int L = lt.bucket_level; L <= M; ++L) {
         const int sh = M - L;
         const int64_t b = int64_t(fy >> sh) * bk.nx[L] + (fx >> sh);
         const int64_t w = bk.word_off[L] + (b >> 6);
         const uint64_t word = bk.bits[w];
-        if ((word >> (b & 63)) & 1ull) found = bk.base[L] + bk.prefix[w] + popc64(word & ((1ull << (b & 63)) - 1ull));
+        if ((word >> (b & 63)) & 1ull) {
+            found = bk.base[L] + bk.prefix[w] + popc64(word & ((1ull << (b & 63)) - 1ull));
+            Lb = L;
+        }
     }
     if (found < 0) {
         report(status, kStatusData, uint32_t(cell));
         cellmap[cell] = make_uint2(0u, 0u);
         return;
     }
-    const int64_t beg = lv.offsets[found], end = lv.offsets[found + 1];
-    cellmap[cell] = make_uint2(uint32_t(beg / kListPad), uint32_t((end - beg) / kListPad));
+    if (COMPACT) {
+        const int64_t beg = cv.pair_offsets[found], end = cv.pair_offsets[found + 1];
+        cellmap[cell] = make_uint2(uint32_t(beg), uint32_t(end - beg) | (uint32_t(Lb) << 24));
+    } else {
+        const int64_t beg = lv.offsets[found], end = lv.offsets[found + 1];
+        cellmap[cell] = make_uint2(uint32_t(beg / kListPad), uint32_t((end - beg) / kListPad));
+    }
 }
 
 int launch_fill_cellmap(const LookupTables& lt, const ListsView& lv, uint2* cellmap, DevStatus* status,
-                        void* stream) {
+                        void* stream, const CompactView* cv) {
     const int64_t cells = int64_t(lt.nx_fin) * lt.ny_fin;
     if (cells == 0) return cudaSuccess;
-    k_fill_cellmap<<<dim3(unsigned((cells + 255) / 256)), 256, 0, cudaStream_t(stream)>>>(lt, lv, cellmap, status);
+    const dim3 grid(unsigned((cells + 255) / 256));
+    if (cv)
+        k_fill_cellmap<true><<<grid, 256, 0, cudaStream_t(stream)>>>(lt, lv, *cv, cellmap, status);
+    else
+        k_fill_cellmap<false><<<grid, 256, 0, cudaStream_t(stream)>>>(lt, lv, CompactView{}, cellmap, status);
     return cudaGetLastError();
 }
 
@@ -632,19 +647,32 @@ __device__ __forceinline__ void discretize_texel_mixed(const DiscCascade& q, flo
     }
     const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
     int Lb = 0, bx = 0, by = 0;
-    const int64_t bucket = lookup_bucket_at(lt, px, py, Lb, bx, by);
-    if (bucket < 0) {
-        report(status, kStatusData, 0xFFFFFFFFu);
-        *out = __int_as_float(0x7fc00000);
-        return;
+    int64_t pb;
+    int np;
+    if (cv.cellmap) {  // one load: the finest cell's {first pair, pairs | bucket level << 24}
+        const int fx = min(max(int(floorf(px * lt.inv_c_fin)), 0), lt.nx_fin - 1);
+        const int fy = min(max(int(floorf(py * lt.inv_c_fin)), 0), lt.ny_fin - 1);
+        const uint2 e = __ldg(cv.cellmap + size_t(fy) * lt.nx_fin + fx);
+        pb = e.x;
+        np = int(e.y & 0xFFFFFFu);
+        Lb = int(e.y >> 24);
+        bx = fx >> (lt.buckets.max_level - Lb);
+        by = fy >> (lt.buckets.max_level - Lb);
+    } else {
+        const int64_t bucket = lookup_bucket_at(lt, px, py, Lb, bx, by);
+        if (bucket < 0) {
+            report(status, kStatusData, 0xFFFFFFFFu);
+            *out = __int_as_float(0x7fc00000);
+            return;
+        }
+        pb = __ldg(cv.pair_offsets + bucket);
+        np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
     }
     const int sh = lt.buckets.max_level - Lb + 1;
     const T PX = Ops::make(fmaf(px, cv.inv_q, -float(bx << sh)));
     const T PY = Ops::make(fmaf(py, cv.inv_q, -float(by << sh)));
     const T NK = Ops::make(-K);
     const T ONE = Ops::make(1.f);
-    const int64_t pb = __ldg(cv.pair_offsets + bucket);
-    const int np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
     const uint4* cc = cv.pairs + pb;
     const uint32_t kb2 = cv.kb2;
     float sw = 0.f, swv = 0.f;

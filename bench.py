@@ -354,7 +354,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     scene = workloads.dem_config(n_frames=args.frames)
     cams = scene.cameras
-    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
+    r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev, precision=args.precision)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sched = frame_schedule(args.frames, args.steps, rank, world)
@@ -517,7 +517,8 @@ def run_ours(args, rank, world, local_rank):
     frame_bound = sum(v["bound_ms"] for v in kern.values())
     dom = max(("discretize", "maxmip", "raycast"), key=lambda k: kern[k]["ms"])
     d = kern[dom]
-    kname = {"discretize": "k_discretize_f32", "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]
+    kname = {"discretize": "k_discretize_f32" if args.precision == 0 else "k_discretize_mixed",
+             "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["achieved"] / d["peak"], "traffic": profiled_traffic(kname), "kernel": dom,
                 "peak_source": ("derived from unit counts, %d SMs (read from the device) at %d MHz"
@@ -525,7 +526,8 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": len(sched),
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": ("f32", "f16x2+f32", "bf16x2+f32")[args.precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": 1,
                    "parallelism": f"replicas{world}" if world > 1 else "none",
                    "l2": "flushed between steps (256 MB write outside the step events)",
@@ -1151,6 +1153,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the FP16/BF16 timing")
     ap.add_argument("--no-blocks", action="store_true", help="skip the flood, batch and serve blocks")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="discretization of the main line: 0 FP32 (default), 1 FP16x2, 2 BF16x2 (for profiling)")
     ap.add_argument("--err-texels", type=int, default=1500, help="sampled DEM texels per cascade (errors)")
     ap.add_argument("--workload", default="dem", choices=["dem", "batch", "serve", "flood"])
     ap.add_argument("--tiles", type=int, default=64)

@@ -1245,6 +1245,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             const DiscParams dp = disc_params(ctx, v);
             I.K = dp.K;
             I.precision = ctx->rbf.precision;
+            if (I.precision != HF_PREC_FP32) h.mixed = 1;
             I.first_cascade = kc;
             I.n_cascades = C;
             I.ray_tiles_x = (v->cam.width + h.ray_tile_w - 1) / h.ray_tile_w;

@@ -235,6 +235,7 @@ struct BatchHeader {
     int32_t flags;
     int32_t persistent_blocks, persistent_blocks_rays;
     int32_t max_rows_units;
+    int32_t mixed;  // 1: some item discretizes in FP16 / BF16 (else the texel phase is FP32 only)
     int64_t items_off, cascades_off, counters_off, desc_bytes, total_bytes;
 };
 

@@ -1651,6 +1651,7 @@ __global__ void __launch_bounds__(128) k_bat_rows(const uint8_t* __restrict__ bu
 // The CTA's cascade, its item's tables and the tile origin are looked up
 // once and staged in shared memory; the texel code then reads them from
 // there (uniform across the CTA) instead of through the descriptor buffer.
+template <bool MIXED>  // false: every item is FP32 (the reduced-precision code is left out)
 __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict__ buf) {
     wait_for_predecessor();
     const BatchHeader* h = reinterpret_cast<const BatchHeader*>(buf);
@@ -1689,7 +1690,7 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
         tile_texel(threadIdx.x, di, dj);
     }
     const int i = s_i0 + di, j = s_j0 + dj;
-    if (precision == HF_PREC_FP32)
+    if (!MIXED || precision == HF_PREC_FP32)
         discretize_texel<false>(s_disc, K, s_lt, s_lv, status, i, j);
     else if (precision == HF_PREC_FP16)
         discretize_texel_mixed<F16Ops, false>(s_disc, K, s_lt, s_cv, status, i, j);
@@ -1748,7 +1749,9 @@ int launch_batch(const BatchHeader& h, void* dev_buf, void* stream) {
         const int nmip = h.phase_base[kPhaseMipHi] - h.phase_base[kPhaseMipLo];
         if (nrow > 0 && (e = launch_dependent(k_bat_rows, dim3(2 * h.max_rows_units, h.n_cascades), dim3(128), s, buf)))
             return e;
-        if (ntex > 0 && (e = launch_dependent(k_bat_texels, dim3(ntex), dim3(256), s, buf))) return e;
+        if (ntex > 0 && (e = h.mixed ? launch_dependent(k_bat_texels<true>, dim3(ntex), dim3(256), s, buf)
+                                     : launch_dependent(k_bat_texels<false>, dim3(ntex), dim3(256), s, buf)))
+            return e;
         if (nmip > 0 && (e = launch_dependent(k_bat_miplo, dim3(nmip), dim3(256), s, buf))) return e;
         if ((e = launch_dependent(k_bat_miphi, dim3(h.n_cascades), dim3(1024), s, buf))) return e;
     }

@@ -190,7 +190,12 @@ typedef struct hf_ctx hf_ctx;
  * per-level occupancy bitmap, and for every leaf the exact size of its list
  * of potentially influencing cells (Section 4: the set I depends only on
  * the grid and is precomputed once).  Allocates host memory only.
- * Returns HF_ERR_ARG on invalid input; *out is set only on success. */
+ * Returns HF_ERR_ARG on invalid input; *out is set only on success.
+ * For grids of at most 2^28 finest cells the persistent buffer also holds a
+ * map from every finest cell to its list (8 bytes per finest cell per list
+ * set), which saves each texel the bucket lookup; the environment variable
+ * HF_CELLMAP_MAX_CELLS, read here, lowers that limit (0: never; the texel
+ * then probes the occupancy bitmaps, with identical results). */
 int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int64_t n_leaves,
                        const hf_rbf_params* rbf, hf_ctx** out);
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <memory>
@@ -196,6 +197,7 @@ struct hf_ctx {
     PersistentLayout lay{};
     std::unique_ptr<ViewSlot> views[HF_MAX_VIEWS];
     uint64_t data_version = 0;  // bumped by hf_update_values / hf_update_water
+    int64_t cellmap_max_cells = kCellMapMaxCells;  // HF_CELLMAP_MAX_CELLS at creation
 
     PersistentLayout layout() const {
         PersistentLayout l{};
@@ -241,14 +243,14 @@ struct hf_ctx {
         t.cellmap = device && keep_cellmap() ? reinterpret_cast<const uint2*>(dev + lay.cellmap) : nullptr;
         return t;
     }
-    // the cell map is kept for grids of at most kCellMapMaxCells finest cells
+    // the cell map is kept for grids of at most cellmap_max_cells finest cells
     // whose list groups are numbered in 32 bits
     bool keep_cellmap() const {
-        return int64_t(buckets.nx[M]) * buckets.ny[M] <= kCellMapMaxCells && n_cand / kListPad < (int64_t(1) << 32);
+        return int64_t(buckets.nx[M]) * buckets.ny[M] <= cellmap_max_cells && n_cand / kListPad < (int64_t(1) << 32);
     }
     // ... and for the compact lists: pairs numbered in 32 bits, at most 2^24 - 1 per list
     bool keep_pair_cellmap() const {
-        return rbf.precision != HF_PREC_FP32 && int64_t(buckets.nx[M]) * buckets.ny[M] <= kCellMapMaxCells &&
+        return rbf.precision != HF_PREC_FP32 && int64_t(buckets.nx[M]) * buckets.ny[M] <= cellmap_max_cells &&
                n_pairs < (int64_t(1) << 32) && max_pairs < (int64_t(1) << 24);
     }
     CompactView compact() const {
@@ -461,6 +463,11 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         ctx->M = M;
         ctx->B = rbf->bucket_level < 0 ? std::max(0, M - 1) : rbf->bucket_level;
         ctx->n_leaves = n_leaves;
+        if (const char* env = std::getenv("HF_CELLMAP_MAX_CELLS")) {
+            char* end = nullptr;
+            const long long v = std::strtoll(env, &end, 10);
+            if (end != env && *end == '\0' && v >= 0) ctx->cellmap_max_cells = std::min<int64_t>(v, kCellMapMaxCells);
+        }
         ctx->c_fin = d.root_cell / double(int64_t(1) << M);
         ctx->width = d.root_cell * d.root_nx;
         ctx->height = d.root_cell * d.root_ny;

@@ -323,3 +323,26 @@ def test_outputs_in_pinned_host_memory(torch_cuda, tiny):
     assert not pageable_t.any()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lookup_without_cell_map_is_identical(torch_cuda, tiny, monkeypatch, precision):
+    """Grids beyond the cell map's size limit look their bucket up in the
+    occupancy bitmaps instead; HF_CELLMAP_MAX_CELLS=0 forces that path here:
+    textures, mipmaps and rays equal the cell-map path's bit for bit."""
+    from paper_2201_10887_gb300 import Renderer
+    cam = tiny.cameras[0].with_(n_cascades=3, cascade_size=192, split_lambda=0.5)
+    a = Renderer(tiny.tree, tiny.sigma, tiny.radius, precision=precision)
+    monkeypatch.setenv("HF_CELLMAP_MAX_CELLS", "0")
+    b = Renderer(tiny.tree, tiny.sigma, tiny.radius, precision=precision)
+    assert b.persistent_bytes < a.persistent_bytes
+    ta, ha = a.render(cam)
+    tb, hb = b.render(cam)
+    a.sync()
+    b.sync()
+    for c in range(cam.n_cascades):
+        assert torch_cuda.equal(a.texture(0, c).view(torch_cuda.int32), b.texture(0, c).view(torch_cuda.int32))
+        assert torch_cuda.equal(a.mip(0, c).view(torch_cuda.int32), b.mip(0, c).view(torch_cuda.int32))
+    assert torch_cuda.equal(ta.view(torch_cuda.int32), tb.view(torch_cuda.int32)) and torch_cuda.equal(ha, hb)
+    a.close()
+    b.close()

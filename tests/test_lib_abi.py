@@ -496,3 +496,21 @@ def test_jump_traversal_refusals(hfmod, tiny):
         rc = lib.hf_set_camera(ctx, 0, ct.byref(bad), ct.c_void_p(1 << 30), ct.c_size_t(1 << 40))
         assert rc == hfmod.HF_ERR_ARG and "traversal" in hfmod.hf_last_error()
         hfmod.hf_destroy(ctx)
+
+
+def test_cell_map_limit_from_the_environment(hfmod, tiny, monkeypatch):
+    """HF_CELLMAP_MAX_CELLS (read at creation) drops the cell map: the
+    persistent buffer shrinks by 8 bytes per finest cell."""
+    desc = hfmod.hf_quadtree_desc(tiny.tree.origin_x, tiny.tree.origin_y, tiny.tree.root_cell,
+                                  tiny.tree.root_nx, tiny.tree.root_ny, tiny.tree.max_level)
+    leaves = hfmod.leaves_array(tiny.tree.level, tiny.tree.ix, tiny.tree.iy, tiny.tree.value)
+    rbf = hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 0, 0)
+    ctx = hfmod.hf_create_quadtree(desc, leaves, rbf)
+    with_map, _ = hfmod.hf_query_bytes(ctx, 1, 2)
+    hfmod.hf_destroy(ctx)
+    monkeypatch.setenv("HF_CELLMAP_MAX_CELLS", "0")
+    ctx = hfmod.hf_create_quadtree(desc, leaves, rbf)
+    without, _ = hfmod.hf_query_bytes(ctx, 1, 2)
+    hfmod.hf_destroy(ctx)
+    fine = (tiny.tree.root_nx << tiny.tree.max_level) * (tiny.tree.root_ny << tiny.tree.max_level)
+    assert with_map - without >= 8 * fine > 0

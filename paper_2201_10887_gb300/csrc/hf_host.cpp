@@ -1141,7 +1141,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct BatchPlan {
     int n_cascades = 0;
-    size_t items_off = 0, cascades_off = 0, counters_off = 0, total = 0;
+    size_t items_off = 0, cascades_off = 0, bases_off = 0, item_bases_off = 0, counters_off = 0, total = 0;
 };
 
 int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
@@ -1163,7 +1163,9 @@ int plan_batch(const hf_batch_item* items, int32_t n, BatchPlan* plan) {
     plan->n_cascades = nc;
     plan->items_off = align_up(sizeof(BatchHeader), 256);
     plan->cascades_off = align_up(plan->items_off + size_t(n) * sizeof(BatchItem), 256);
-    plan->counters_off = align_up(plan->cascades_off + size_t(nc) * sizeof(BatchCascade), 256);
+    plan->bases_off = align_up(plan->cascades_off + size_t(nc) * sizeof(BatchCascade), 256);
+    plan->item_bases_off = align_up(plan->bases_off + size_t(nc) * 4 * 4, 256);
+    plan->counters_off = align_up(plan->item_bases_off + size_t(n) * 4, 256);
     plan->total = align_up(plan->counters_off + (size_t(nc) * 4 + 4) * 4, 256);
     return HF_OK;
 }
@@ -1227,6 +1229,8 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
         h.items_off = int64_t(plan.items_off);
         h.cascades_off = int64_t(plan.cascades_off);
         h.counters_off = int64_t(plan.counters_off);
+        h.bases_off = int64_t(plan.bases_off);
+        h.item_bases_off = int64_t(plan.item_bases_off);
         h.desc_bytes = int64_t(plan.counters_off);
         h.total_bytes = int64_t(plan.total);
         int kc = 0, units[kPhases] = {0, 0, 0, 0, 0};
@@ -1258,6 +1262,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             I.ray_tiles_x = (v->cam.width + h.ray_tile_w - 1) / h.ray_tile_w;
             I.ray_units = I.ray_tiles_x * ((v->cam.height + h.ray_tile_h - 1) / h.ray_tile_h);
             I.ray_unit_base = units[kPhaseRays];
+            reinterpret_cast<int32_t*>(hb + plan.item_bases_off)[i] = I.ray_unit_base;
             units[kPhaseRays] += I.ray_units;
             for (int k = 0; k < C; ++k, ++kc) {
                 BatchCascade& B = bc[kc];
@@ -1291,8 +1296,12 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             base += units[ph];
         }
         h.phase_base[kPhases] = base;
+        int32_t* bases = reinterpret_cast<int32_t*>(hb + plan.bases_off);
         for (int k = 0; k < plan.n_cascades; ++k)
-            for (int ph = 0; ph < 4; ++ph) bc[k].unit_base[ph] += h.phase_base[ph];
+            for (int ph = 0; ph < 4; ++ph) {
+                bc[k].unit_base[ph] += h.phase_base[ph];
+                bases[ph * plan.n_cascades + k] = bc[k].unit_base[ph];
+            }
         return HF_OK;
     });
 }

@@ -237,6 +237,8 @@ struct BatchHeader {
     int32_t max_rows_units;
     int32_t mixed;  // 1: some item discretizes in FP16 / BF16 (else the texel phase is FP32 only)
     int64_t items_off, cascades_off, counters_off, desc_bytes, total_bytes;
+    int64_t bases_off;  // int32 [4][n_cascades]: the cascades' first units of phases 0..3, contiguous
+    int64_t item_bases_off;  // int32 [n_items]: the items' first ray units (BatchItem.ray_unit_base)
 };
 
 // Kernel launchers (hf_kernels.cu); they return a cudaError_t value.

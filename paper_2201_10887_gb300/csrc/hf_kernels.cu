@@ -6,6 +6,7 @@
 // used: the discretization is bound by exp (MUFU) and FP32 issue, the mip
 // build by HBM/L2 bandwidth, the ray caster by dependent loads.
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <thread>
 #include <vector>
@@ -1437,6 +1438,25 @@ __device__ __forceinline__ int find_cascade(const BatchCascade* cas, int n, int 
     return lo;
 }
 
+// The same search by the 32 lanes of one warp over the compact array of the
+// phase's first units (ascending): each round narrows the range by a factor
+// of 32 with one load per lane, so a CTA's preamble costs ~two dependent
+// loads instead of ~log2(n) loads at a cascade record's stride.
+__device__ __forceinline__ int find_cascade_warp(const int32_t* bases, int n, int u) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, len = n;  // the answer lies in [lo, lo + len)
+    while (len > 1) {
+        const int step = (len + 31) / 32;
+        const int k = lo + lane * step;
+        const bool le = k < lo + len && __ldg(bases + k) <= u;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(m);  // bases[lo] <= u always holds, so m != 0
+        lo += last * step;
+        len = min(step, n - lo);
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int find_item(const BatchItem* items, int n, int u) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -1463,10 +1483,39 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src) {
     for (int w = threadIdx.x; w < int(sizeof(T) / 4); w += blockDim.x) d[w] = s[w];
 }
 
+// The lookup tables an FP32 texel needs: with a cell map only the fields after
+// the bucket bitmaps (the FP32 walk reads the bitmaps only without a map; the
+// reduced-precision walk always needs their max_level, so FULL copies all).
+template <bool FULL>
+__device__ __forceinline__ void cta_copy_lookup(LookupTables* dst, const LookupTables* src) {
+    constexpr int from = int(offsetof(LookupTables, bucket_level)) / 4;
+    static_assert(offsetof(LookupTables, bucket_level) % 4 == 0, "word-aligned tail");
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    const int w0 = (!FULL && src->cellmap) ? from : 0;
+    for (int w = w0 + threadIdx.x; w < int(sizeof(LookupTables) / 4); w += blockDim.x) d[w] = s[w];
+}
+
+// The ray parameters of an item: the fixed fields, its C cascades and the
+// output pointers (the unused cascade slots are not copied).
+__device__ __forceinline__ void cta_copy_ray(RayParams* dst, const RayParams* src, int C) {
+    static_assert(offsetof(RayParams, cas) % 4 == 0 && sizeof(RayCascade) % 4 == 0 &&
+                  offsetof(RayParams, t_out) % 4 == 0, "word-aligned parts");
+    const int body = int(offsetof(RayParams, cas) + size_t(C) * sizeof(RayCascade)) / 4;
+    const int tail = int(offsetof(RayParams, t_out)) / 4;
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    for (int w = threadIdx.x; w < int(sizeof(RayParams) / 4); w += blockDim.x)
+        if (w < body || w >= tail) d[w] = s[w];
+}
+
 template <bool COH>
 __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const BatchItem* items, const BatchCascade* cas,
                                                const uint32_t* done, int u, int (*off)[kMaxLevels]) {
-    const int it = find_item(items, h->n_items, u - h->phase_base[kPhaseRays]);
+    // every warp finds the item itself (no barrier needed for it)
+    const int it = find_cascade_warp(reinterpret_cast<const int32_t*>(reinterpret_cast<const uint8_t*>(h) +
+                                                                      h->item_bases_off),
+                                     h->n_items, u - h->phase_base[kPhaseRays]);
     const BatchItem& I = items[it];
     if (COH) {
         for (int c = 0; c < I.n_cascades; ++c)
@@ -1476,7 +1525,7 @@ __device__ __forceinline__ void batch_ray_unit(const BatchHeader* h, const Batch
     // them from shared memory rather than through the descriptor buffer
     __shared__ RayParams s_ray;
     __syncthreads();  // the previous unit of this CTA is done with s_ray and off
-    cta_copy(&s_ray, &I.ray);
+    cta_copy_ray(&s_ray, &I.ray, I.n_cascades);
     __syncthreads();
     load_level_offsets<COH>(s_ray, off, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -1662,21 +1711,24 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
     __shared__ ListsView s_lv;
     __shared__ CompactView s_cv;
     __shared__ int s_k, s_i0, s_j0;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0 finds the CTA's cascade
         const int u = h->phase_base[kPhaseTexels] + int(blockIdx.x);
-        const int k = find_cascade(cas, h->n_cascades, kPhaseTexels, u);
-        const int local = u - cas[k].unit_base[kPhaseTexels], tx = cas[k].tiles_x;
-        s_k = k;
-        s_i0 = (local % tx) * 32;
-        s_j0 = (local / tx) * 8;
+        const int32_t* bases = reinterpret_cast<const int32_t*>(buf + h->bases_off) + kPhaseTexels * h->n_cascades;
+        const int k = find_cascade_warp(bases, h->n_cascades, u);
+        if (threadIdx.x == 0) {
+            const int local = u - __ldg(bases + k), tx = cas[k].tiles_x;
+            s_k = k;
+            s_i0 = (local % tx) * 32;
+            s_j0 = (local / tx) * 8;
+        }
     }
     __syncthreads();
     const BatchCascade& C = cas[s_k];
     const BatchItem& I = items[C.item];
-    cta_copy(&s_lt, &I.lt);
+    cta_copy_lookup<MIXED>(&s_lt, &I.lt);
     cta_copy(&s_disc, &C.disc);
     cta_copy(&s_lv, &I.lv);
-    cta_copy(&s_cv, &I.cv);
+    if (MIXED) cta_copy(&s_cv, &I.cv);
     const float K = I.K;
     const int precision = I.precision;
     DevStatus* const status = I.status;
@@ -1705,13 +1757,16 @@ __global__ void __launch_bounds__(256) k_bat_miplo(const uint8_t* __restrict__ b
     __shared__ float sm[16][17];
     __shared__ MipCascade s_mip;
     __shared__ int s_k, s_bx, s_by;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {  // warp 0 finds the CTA's cascade
         const int u = h->phase_base[kPhaseMipLo] + int(blockIdx.x);
-        const int k = find_cascade(cas, h->n_cascades, kPhaseMipLo, u);
-        const int local = u - cas[k].unit_base[kPhaseMipLo], bx = cas[k].mip_blocks_x;
-        s_k = k;
-        s_bx = local % bx;
-        s_by = local / bx;
+        const int32_t* bases = reinterpret_cast<const int32_t*>(buf + h->bases_off) + kPhaseMipLo * h->n_cascades;
+        const int k = find_cascade_warp(bases, h->n_cascades, u);
+        if (threadIdx.x == 0) {
+            const int local = u - __ldg(bases + k), bx = cas[k].mip_blocks_x;
+            s_k = k;
+            s_bx = local % bx;
+            s_by = local / bx;
+        }
     }
     __syncthreads();
     cta_copy(&s_mip, &cas[s_k].mip);

@@ -125,3 +125,34 @@ def test_autotune_picks_a_valid_shape(torch_cuda):
     assert all(v > 0 for v in times.values())
     for r, _ in views:
         r.sync()
+
+
+def test_batch_with_many_items_and_cascades(torch_cuda):
+    """More than 32 items and 32 cascades, so that each CTA's warp-wide search
+    for its item or cascade takes more than one round: every shape still
+    reproduces the per-view calls bit for bit."""
+    import math
+    from paper_2201_10887_gb300 import Batch, Renderer
+    from paper_2201_10887_gb300.batch import flag_candidates
+    tiny = _scenes()[1]
+    r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    views, cams = [], []
+    rng = np.random.default_rng(31)
+    for slot in range(41):
+        yaw = math.radians(90.0 + rng.uniform(-40, 40))
+        pitch = math.radians(rng.uniform(-50, -20))
+        fwd = (math.cos(pitch) * math.cos(yaw), math.cos(pitch) * math.sin(yaw), math.sin(pitch))
+        cams.append(tiny.cameras[0].with_(forward=fwd, n_cascades=int(rng.integers(1, 4)),
+                                          cascade_size=int(rng.integers(33, 97)),
+                                          width=int(rng.integers(16, 48)), height=int(rng.integers(12, 40))))
+        views.append((r, slot))
+    assert len(views) > 32 and sum(c.n_cascades for c in cams) > 32
+    ref = _reference(views, cams)
+    batch = Batch(views)
+    for flags in flag_candidates():
+        _clear(views, cams)
+        batch.prepare(flags)
+        batch.launch()
+        r.sync()
+        _check(batch, views, cams, ref)
+    r.close()

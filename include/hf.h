@@ -89,6 +89,12 @@ typedef struct {
  * candidates at a time in packed 16-bit arithmetic from compact per-bucket
  * lists (more device memory); candidate offsets must stay exact in the
  * 16-bit type, else hf_create_quadtree returns HF_ERR_ARG.
+ * HF_PREC_FP32 evaluates in FP32 arithmetic.  Where the offsets are exact in
+ * FP16 and the water layer is off, an FP32 context also keeps the compact
+ * lists and walks them (one 16-byte load per two candidates, no index); their
+ * values give up their 4 lowest mantissa bits to the cell's level (at most 15
+ * ulp).  Otherwise, or with the environment variable HF_FP32_INDEX_LISTS=1
+ * set at creation, it walks lists of leaf indices with exact values.
  * hf_discretize_noalloc always evaluates in FP32.
  * The lists of potentially influencing cells (Section 4) are kept per
  * square "bucket": every leaf at or below level bucket_level is a bucket,

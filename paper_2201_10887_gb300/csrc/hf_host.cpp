@@ -190,6 +190,12 @@ struct hf_ctx {
     std::vector<int64_t> pair_offsets;  // n_buckets + 1 (reduced precision only)
     int64_t n_pairs = 0, max_pairs = 0;
     uint32_t kb2 = 0;              // packed level-0 scale bits of the compact lists
+    uint32_t kf_bits = 0;          // FP32 finest-level scale per squared half-cell
+    // compact pair lists and the format of their coordinates: 0 none, HF_PREC_FP16 or
+    // HF_PREC_BF16. FP32 contexts without the water layer whose offsets are exact in
+    // FP16 keep FP16-format lists and discretize from them in FP32 arithmetic.
+    int compact_fmt = 0;
+    bool fp32_compact() const { return rbf.precision == HF_PREC_FP32 && compact_fmt == HF_PREC_FP16; }
     std::vector<float> staged;     // values in sorted order for hf_update_values
     std::vector<float> depth;      // water depths in sorted order (water layer only)
     char* dev = nullptr;
@@ -210,7 +216,7 @@ struct hf_ctx {
         l.recs = o; o = align256(o + size_t(n_leaves + 1) * 16);  // + the null record
         l.offsets = o; o = align256(o + size_t(n_buckets + 1) * 8);
         l.idx = o; o = align256(o + size_t(n_cand) * 4);
-        const bool compact = rbf.precision != HF_PREC_FP32;
+        const bool compact = compact_fmt != 0;
         l.pair_offsets = o; o = align256(o + (compact ? size_t(n_buckets + 1) * 8 : 0));
         l.pairs = o; o = align256(o + (compact ? size_t(n_pairs) * 16 : 0));
         l.depth = o; o = align256(o + (rbf.water ? size_t(n_leaves + 1) * 4 : 0));
@@ -250,7 +256,7 @@ struct hf_ctx {
     }
     // ... and for the compact lists: pairs numbered in 32 bits, at most 2^24 - 1 per list
     bool keep_pair_cellmap() const {
-        return rbf.precision != HF_PREC_FP32 && int64_t(buckets.nx[M]) * buckets.ny[M] <= cellmap_max_cells &&
+        return compact_fmt != 0 && int64_t(buckets.nx[M]) * buckets.ny[M] <= cellmap_max_cells &&
                n_pairs < (int64_t(1) << 32) && max_pairs < (int64_t(1) << 24);
     }
     CompactView compact() const {
@@ -258,6 +264,8 @@ struct hf_ctx {
         v.pair_offsets = reinterpret_cast<const int64_t*>(dev + lay.pair_offsets);
         v.pairs = reinterpret_cast<uint4*>(dev + lay.pairs);
         v.kb2 = kb2;
+        v.kf_bits = kf_bits;
+        v.max_level = M;
         v.q = float(0.5 * c_fin);
         v.inv_q = float(2.0 / c_fin);
         v.cellmap = keep_pair_cellmap() ? reinterpret_cast<const uint2*>(dev + lay.pair_cellmap) : nullptr;
@@ -346,7 +354,7 @@ int check_camera(const hf_camera& c) {
 int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
                                    char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
                                    PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
-                                   DevStatus** status) {
+                                   CompactView* cv, bool* compact, DevStatus** status) {
     if (!ctx || !cam || !tex) return fail(HF_ERR_ARG, "null argument");
     if (!ctx->dev) return fail(HF_ERR_STATE, "persistent buffer not bound");
     const hf_camera& c = *cam;
@@ -403,6 +411,10 @@ int hfi::noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* con
     }
     *lt = ctx->lookup_tables(true);
     *lv = ctx->lists();
+    // the FP32 walk the context's own FP32 discretization uses: over FP16-format
+    // compact lists where the context keeps them, else over the index lists
+    *compact = ctx->compact_fmt == HF_PREC_FP16;
+    if (*compact) *cv = ctx->compact();
     *status = ctx->d_status();
     return HF_OK;
 }
@@ -560,12 +572,30 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
         }
         ctx->offsets[size_t(ctx->n_buckets)] = run;
         ctx->n_cand = run;
+        // bucket-relative offsets of the compact lists must be exact small integers in the 16-bit type
+        double rmax = 0.0;
+        for (int L = 0; L <= M; ++L)
+            if (lf.base[L + 1] > lf.base[L]) rmax = std::max(rmax, ctx->reach_q[L]);
+        const double span = rmax + double(int64_t(1) << (M - ctx->B + 1)) + 1.0;
+        if (rbf->precision == HF_PREC_FP32) {
+            const char* env = std::getenv("HF_FP32_INDEX_LISTS");
+            const bool forced = env && env[0] && std::strcmp(env, "0") != 0;
+            if (!rbf->water && span <= 1024.0 && !forced) {
+                ctx->compact_fmt = HF_PREC_FP16;
+                // FP32 weight scale per squared half-cell of the finest level (c = 2 q):
+                // Gaussian -log2(e) / (8 sigma^2), Wendland 1 / (4 radius^2); level L's is
+                // 4^(M - L) times smaller, built in the exponent field
+                const float kM = rbf->kernel == HF_RBF_WENDLAND_C2 ? float(1.0 / (4.0 * rbf->radius * rbf->radius))
+                                                                   : float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
+                const float kL = float(std::ldexp(double(kM), -2 * (M - lmin)));
+                if (!(std::fabs(kL) >= std::numeric_limits<float>::min()) || !std::isfinite(kM))
+                    ctx->compact_fmt = 0;  // scales outside the normal range: the index lists serve
+                else
+                    std::memcpy(&ctx->kf_bits, &kM, 4);
+            }
+        }
         if (rbf->precision != HF_PREC_FP32) {
-            // bucket-relative offsets must be exact small integers in the 16-bit type
-            double rmax = 0.0;
-            for (int L = 0; L <= M; ++L)
-                if (lf.base[L + 1] > lf.base[L]) rmax = std::max(rmax, ctx->reach_q[L]);
-            const double span = rmax + double(int64_t(1) << (M - ctx->B + 1)) + 1.0;
+            ctx->compact_fmt = rbf->precision;
             const double limit = rbf->precision == HF_PREC_FP16 ? 1024.0 : 256.0;
             if (span > limit)
                 return fail(HF_ERR_ARG, "candidate offsets span %.0f half-cells, more than the %s path holds exactly (%.0f)",
@@ -574,6 +604,7 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
             // level L's lowers the exponent by 2 (M - L), which must stay a normal number
             const bool f16 = rbf->precision == HF_PREC_FP16;
             const float kM = float(-log2e / (8.0 * rbf->sigma * rbf->sigma));
+            std::memcpy(&ctx->kf_bits, &kM, 4);
             const uint32_t kMb = f16 ? f16_bits(kM) : bf16_bits(kM);
             const int shift = f16 ? 10 : 7, emask = f16 ? 31 : 255;
             const int eM = kMb == std::numeric_limits<uint32_t>::max() ? 0 : int((kMb >> shift) & uint32_t(emask));
@@ -583,6 +614,8 @@ int hf_create_quadtree(const hf_quadtree_desc* desc, const hf_leaf* leaves, int6
             const uint32_t step = 2u << shift;
             const uint32_t kb = kMb - uint32_t(M) * step;  // level 0's bits, modulo 2^32
             ctx->kb2 = kb * 0x10001u;
+        }
+        if (ctx->compact_fmt != 0) {
             ctx->pair_offsets.resize(size_t(ctx->n_buckets) + 1);
             int64_t pr = 0;
             for (int64_t b = 0; b < ctx->n_buckets; ++b) {
@@ -631,7 +664,7 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
         if (!e) e = cudaMemcpyAsync(dev + l.bprefix, ctx->buckets.prefix.data(), ctx->buckets.prefix.size() * 4, cudaMemcpyHostToDevice, s);
         if (!e) e = cudaMemcpyAsync(dev + l.recs, ctx->recs.data(), ctx->recs.size() * 16, cudaMemcpyHostToDevice, s);
         if (!e) e = cudaMemcpyAsync(dev + l.offsets, ctx->offsets.data(), ctx->offsets.size() * 8, cudaMemcpyHostToDevice, s);
-        if (!e && ctx->rbf.precision != HF_PREC_FP32)
+        if (!e && ctx->compact_fmt != 0)
             e = cudaMemcpyAsync(dev + l.pair_offsets, ctx->pair_offsets.data(), ctx->pair_offsets.size() * 8,
                                 cudaMemcpyHostToDevice, s);
         if (!e && ctx->rbf.water)
@@ -656,9 +689,9 @@ int hf_bind_persistent(hf_ctx* ctx, void* dev_persistent, size_t bytes, void* st
                                     ctx->d_status(), stream);
             if (e) return cuda_fail(e, "cell-map kernel launch");
         }
-        if (ctx->rbf.precision != HF_PREC_FP32) {
+        if (ctx->compact_fmt != 0) {
             e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
-                                    ctx->rbf.precision, stream);
+                                    ctx->compact_fmt, stream);
             if (e) return cuda_fail(e, "compact-list kernel launch");
             if (ctx->keep_pair_cellmap()) {
                 const CompactView cv = ctx->compact();
@@ -705,9 +738,9 @@ int hf_update_values(hf_ctx* ctx, const float* values, int64_t n_values, void* s
         cudaStream_t s = cudaStream_t(stream);
         int e = cudaMemcpy2DAsync(ctx->dev + ctx->lay.recs + 12, 16, ctx->staged.data(), 4, 4, size_t(n_values),
                                   cudaMemcpyHostToDevice, s);
-        if (!e && ctx->rbf.precision != HF_PREC_FP32)  // the compact lists carry copies of the values
+        if (!e && ctx->compact_fmt != 0)  // the compact lists carry copies of the values
             e = launch_fill_compact(ctx->enum_tables(true), ctx->lookup_tables(true), ctx->lists(), ctx->compact(),
-                                    ctx->rbf.precision, stream);
+                                    ctx->compact_fmt, stream);
         if (!e) e = cudaStreamSynchronize(s);
         if (e) return cuda_fail(e, "value upload");
         return HF_OK;
@@ -875,7 +908,10 @@ int discretize_view(hf_ctx* ctx, ViewSlot* v, void* stream) {
     for (int k = 0; k < C; ++k) fill_prep_cascade(v, k, pp.cas[k]);
     int e = launch_prep(pp, stream);
     if (e) return cuda_fail(e, "visible-row kernel launch");
-    if (ctx->rbf.precision == HF_PREC_FP32)
+    if (ctx->fp32_compact() && !ctx->rbf.water)
+        e = launch_discretize_f32c(disc_params(ctx, v), ctx->lookup_tables(true), ctx->compact(), ctx->d_status(),
+                                   stream);
+    else if (ctx->rbf.precision == HF_PREC_FP32)
         e = launch_discretize(disc_params(ctx, v), ctx->lookup_tables(true), ctx->lists(), ctx->d_status(), stream);
     else
         e = launch_discretize_mixed(disc_params(ctx, v), ctx->lookup_tables(true), ctx->compact(), ctx->d_status(),
@@ -1244,7 +1280,8 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
             I.ray.hit_out = items[i].hit_dev;
             I.lt = ctx->lookup_tables(true);
             I.lv = ctx->lists();
-            if (ctx->rbf.precision != HF_PREC_FP32) I.cv = ctx->compact();
+            if (ctx->compact_fmt != 0) I.cv = ctx->compact();
+            I.fp32c = ctx->fp32_compact() ? 1 : 0;
             I.status = ctx->d_status();
             I.dom_w = ctx->width;
             I.dom_h = ctx->height;

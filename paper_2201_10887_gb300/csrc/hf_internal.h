@@ -94,6 +94,8 @@ struct CompactView {
     uint4* pairs;                 // per pair
     float q, inv_q;               // half a finest cell (m) and its inverse
     uint32_t kb2;                 // (bits of the level-0 scale) * 0x10001, see above
+    uint32_t kf_bits;             // FP32 bits of the finest level's weight scale per squared half-cell
+    int32_t max_level;
     // optional (as LookupTables.cellmap): per finest cell {first pair of its
     // bucket's list, pairs | bucket level << 24}; null: bitmap lookup
     const uint2* cellmap;
@@ -224,6 +226,7 @@ struct BatchItem {
     double dom_w, dom_h, eps_frac;
     float K;
     int32_t precision;
+    int32_t fp32c;  // FP32 item discretized from its compact lists (see discretize_texel_f32c)
     int32_t first_cascade, n_cascades;
     int32_t ray_unit_base, ray_tiles_x, ray_units;
 };
@@ -256,6 +259,8 @@ int launch_discretize_mixed(const DiscParams& p, const LookupTables& lt, const C
                             DevStatus* status, void* stream);
 int launch_discretize(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
                       DevStatus* status, void* stream);
+int launch_discretize_f32c(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
+                           DevStatus* status, void* stream);
 int launch_maxmip(const MipParams& p, void* stream);
 int launch_stats(const DiscParams& p, const LookupTables& lt, const ListsView& lv,
                  DevStatus* status, void* stream);
@@ -267,11 +272,12 @@ int launch_selftest_wait(DevStatus* status, int limit, void* stream);
 
 // Allocation-free discretization (hf_noalloc.cu): fits `cam` and fills the
 // prep / discretize parameters for output textures `tex` and the scratch
-// block `scratch` (spans, then xs, then ys of every cascade).
+// block `scratch` (spans, then xs, then ys of every cascade).  *compact: the
+// FP32 walk over the compact lists (cv) serves, else the index lists (lv).
 int noalloc_discretize_params(hf_ctx* ctx, const hf_camera* cam, float* const* tex,
                               char* scratch, size_t scratch_bytes, hf_cascade_info* info_out,
                               PrepParams* pp, DiscParams* dp, LookupTables* lt, ListsView* lv,
-                              DevStatus** status);
+                              CompactView* cv, bool* compact, DevStatus** status);
 // Records a CUDA failure as the calling thread's last error; returns HF_ERR_CUDA.
 int set_cuda_error(int e, const char* what);
 

@@ -6,6 +6,7 @@
 // used: the discretization is bound by exp (MUFU) and FP32 issue, the mip
 // build by HBM/L2 bandwidth, the ray caster by dependent loads.
 #include <cmath>
+#include <cstdlib>
 #include <cstddef>
 #include <cstdint>
 #include <thread>
@@ -691,6 +692,85 @@ __device__ __forceinline__ void discretize_texel_mixed(const DiscCascade& q, flo
         swv = fmaf(w.x, __uint_as_float(c.z), fmaf(w.y, __uint_as_float(c.w), swv));
     }
     *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+// Eq. 2 in FP32 arithmetic from the compact pair lists (FP16-format
+// coordinates): one 16-byte load brings two candidates and no index
+// indirection is needed.  Positions are the lists' exact small integers (half
+// finest cells from the bucket corner) against the texel's position in the
+// same units; the weight scale of level L is the finest level's divided by
+// 4^(M - L), built exactly in the exponent field; exp2, weights and sums are
+// FP32.  The values carry the level in their 4 lowest mantissa bits (at most
+// 15 ulp of the value).
+template <bool COH, int KERNEL>
+__device__ __forceinline__ void discretize_texel_f32c(const DiscCascade& q, float K, const LookupTables& lt,
+                                                      const CompactView& cv, DevStatus* status, int i, int j) {
+    if (i >= q.N || j >= q.N) return;
+    if (texel_settled<COH, false>(q, i, j)) return;
+    float* out = q.tex + size_t(j) * q.N + i;
+    const float px = ldc<COH>(q.xs + i), py = ldc<COH>(q.ys + j);
+    int Lb = 0, bx = 0, by = 0;
+    int64_t pb;
+    int np;
+    if (cv.cellmap) {
+        const int fx = min(max(int(floorf(px * lt.inv_c_fin)), 0), lt.nx_fin - 1);
+        const int fy = min(max(int(floorf(py * lt.inv_c_fin)), 0), lt.ny_fin - 1);
+        const uint2 e = __ldg(cv.cellmap + size_t(fy) * lt.nx_fin + fx);
+        pb = e.x;
+        np = int(e.y & 0xFFFFFFu);
+        Lb = int(e.y >> 24);
+        bx = fx >> (cv.max_level - Lb);
+        by = fy >> (cv.max_level - Lb);
+    } else {
+        const int64_t bucket = lookup_bucket_at(lt, px, py, Lb, bx, by);
+        if (bucket < 0) {
+            report(status, kStatusData, 0xFFFFFFFFu);
+            *out = __int_as_float(0x7fc00000);
+            return;
+        }
+        pb = __ldg(cv.pair_offsets + bucket);
+        np = int(__ldg(cv.pair_offsets + bucket + 1) - pb);
+    }
+    const int sh = cv.max_level - Lb + 1;
+    const float PX = fmaf(px, cv.inv_q, -float(bx << sh));
+    const float PY = fmaf(py, cv.inv_q, -float(by << sh));
+    const uint4* cc = cv.pairs + pb;
+    const uint32_t kf = cv.kf_bits + (uint32_t(15 - cv.max_level) << 24);  // so that level L adds L << 24 - 15 << 24
+    float sw = 0.f, swv = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < np; ++k) {
+        const uint4 c = __ldg(cc + k);
+        const float2 X = __half22float2(F16Ops::bits(c.x)), Y = __half22float2(F16Ops::bits(c.y));
+        const float dx0 = X.x - PX, dy0 = Y.x - PY, dx1 = X.y - PX, dy1 = Y.y - PY;
+        const float k0 = __uint_as_float(kf - ((15u - (c.z & 15u)) << 24));
+        const float k1 = __uint_as_float(kf - ((15u - (c.w & 15u)) << 24));
+        const float w0 = rbf_weight<KERNEL>(k0 * fmaf(dx0, dx0, dy0 * dy0), K);
+        const float w1 = rbf_weight<KERNEL>(k1 * fmaf(dx1, dx1, dy1 * dy1), K);
+        sw += w0 + w1;
+        swv = fmaf(w0, __uint_as_float(c.z), fmaf(w1, __uint_as_float(c.w), swv));
+    }
+    *out = sw > 0.f ? swv / sw : __int_as_float(0x7fc00000);
+}
+
+template <int KERNEL>
+__global__ void __launch_bounds__(256, 8) k_discretize_f32c(const __grid_constant__ DiscParams p,
+                                                            const __grid_constant__ LookupTables lt,
+                                                            const CompactView cv, DevStatus* status) {
+    wait_for_predecessor();
+    int di, dj;
+    tile_texel(threadIdx.x, di, dj);
+    discretize_texel_f32c<false, KERNEL>(p.cas[blockIdx.z], p.K, lt, cv, status, blockIdx.x * 32 + di,
+                                         blockIdx.y * 8 + dj);
+}
+
+int launch_discretize_f32c(const DiscParams& p, const LookupTables& lt, const CompactView& cv,
+                           DevStatus* status, void* stream) {
+    if (p.C == 0) return cudaSuccess;
+    dim3 grid((p.max_N + 31) / 32, (p.max_N + 7) / 8, p.C);
+    if (p.kernel == HF_RBF_WENDLAND_C2)
+        return launch_dependent(k_discretize_f32c<HF_RBF_WENDLAND_C2>, grid, dim3(256), cudaStream_t(stream), p, lt, cv,
+                                status);
+    return launch_dependent(k_discretize_f32c<HF_RBF_GAUSSIAN>, grid, dim3(256), cudaStream_t(stream), p, lt, cv, status);
 }
 
 template <class Ops>
@@ -1483,16 +1563,15 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src) {
     for (int w = threadIdx.x; w < int(sizeof(T) / 4); w += blockDim.x) d[w] = s[w];
 }
 
-// The lookup tables an FP32 texel needs: with a cell map only the fields after
-// the bucket bitmaps (the FP32 walk reads the bitmaps only without a map; the
-// reduced-precision walk always needs their max_level, so FULL copies all).
-template <bool FULL>
-__device__ __forceinline__ void cta_copy_lookup(LookupTables* dst, const LookupTables* src) {
+// The lookup tables a texel needs: without `full`, only the fields after the
+// bucket bitmaps (a walk that finds its list through a cell map never reads
+// the bitmaps; the reduced-precision walk always needs their max_level).
+__device__ __forceinline__ void cta_copy_lookup(LookupTables* dst, const LookupTables* src, bool full) {
     constexpr int from = int(offsetof(LookupTables, bucket_level)) / 4;
     static_assert(offsetof(LookupTables, bucket_level) % 4 == 0, "word-aligned tail");
     const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-    const int w0 = (!FULL && src->cellmap) ? from : 0;
+    const int w0 = full ? 0 : from;
     for (int w = w0 + threadIdx.x; w < int(sizeof(LookupTables) / 4); w += blockDim.x) d[w] = s[w];
 }
 
@@ -1641,7 +1720,9 @@ __global__ void __launch_bounds__(256, RAYS_INSIDE ? 3 : 5) k_batch(const uint8_
                     tile_texel(threadIdx.x, di, dj);
                 }
                 const int i = (local % C.tiles_x) * 32 + di, j = (local / C.tiles_x) * 8 + dj;
-                if (I.precision == HF_PREC_FP32)
+                if (I.fp32c)
+                    discretize_texel_f32c<true, HF_RBF_GAUSSIAN>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
+                else if (I.precision == HF_PREC_FP32)
                     discretize_texel<true>(s_disc, I.K, s_lt, I.lv, I.status, i, j);
                 else if (I.precision == HF_PREC_FP16)
                     discretize_texel_mixed<F16Ops, true>(s_disc, I.K, s_lt, I.cv, I.status, i, j);
@@ -1725,10 +1806,11 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
     __syncthreads();
     const BatchCascade& C = cas[s_k];
     const BatchItem& I = items[C.item];
-    cta_copy_lookup<MIXED>(&s_lt, &I.lt);
+    // the FP32 walks read the bitmaps only without their cell map
+    cta_copy_lookup(&s_lt, &I.lt, MIXED || (I.fp32c ? I.cv.cellmap == nullptr : I.lt.cellmap == nullptr));
     cta_copy(&s_disc, &C.disc);
     cta_copy(&s_lv, &I.lv);
-    if (MIXED) cta_copy(&s_cv, &I.cv);
+    if (MIXED || I.fp32c) cta_copy(&s_cv, &I.cv);
     const float K = I.K;
     const int precision = I.precision;
     DevStatus* const status = I.status;
@@ -1742,7 +1824,9 @@ __global__ void __launch_bounds__(256, 8) k_bat_texels(const uint8_t* __restrict
         tile_texel(threadIdx.x, di, dj);
     }
     const int i = s_i0 + di, j = s_j0 + dj;
-    if (!MIXED || precision == HF_PREC_FP32)
+    if (I.fp32c)
+        discretize_texel_f32c<false, HF_RBF_GAUSSIAN>(s_disc, K, s_lt, s_cv, status, i, j);
+    else if (!MIXED || precision == HF_PREC_FP32)
         discretize_texel<false>(s_disc, K, s_lt, s_lv, status, i, j);
     else if (precision == HF_PREC_FP16)
         discretize_texel_mixed<F16Ops, false>(s_disc, K, s_lt, s_cv, status, i, j);

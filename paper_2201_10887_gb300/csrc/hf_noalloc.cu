@@ -48,15 +48,18 @@ extern "C" int hf_discretize_noalloc(hf_ctx* ctx, const hf_camera* cam, float* c
         hfi::DiscParams dp;
         hfi::LookupTables lt;
         hfi::ListsView lv;
+        hfi::CompactView cv{};
+        bool compact = false;
         hfi::DevStatus* status = nullptr;
         rc = hfi::noalloc_discretize_params(ctx, cam, tex_out, scratch, HF_NOALLOC_SCRATCH_BYTES, info_out,
-                                            &pp, &dp, &lt, &lv, &status);
+                                            &pp, &dp, &lt, &lv, &cv, &compact, &status);
         if (rc != HF_OK) return rc;
         // every span and coordinate read below is written first on the same
         // stream, so nothing in the scratch needs clearing between calls
         int e = hfi::launch_prep(pp, stream);
         if (e != cudaSuccess) return hfi::set_cuda_error(e, "visible-row kernel launch (allocation-free path)");
-        e = hfi::launch_discretize(dp, lt, lv, status, stream);
+        e = compact ? hfi::launch_discretize_f32c(dp, lt, cv, status, stream)
+                    : hfi::launch_discretize(dp, lt, lv, status, stream);
         if (e != cudaSuccess) return hfi::set_cuda_error(e, "discretization kernel launch (allocation-free path)");
         return HF_OK;
     });

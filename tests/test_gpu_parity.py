@@ -346,3 +346,14 @@ def test_lookup_without_cell_map_is_identical(torch_cuda, tiny, monkeypatch, pre
     assert torch_cuda.equal(ta.view(torch_cuda.int32), tb.view(torch_cuda.int32)) and torch_cuda.equal(ha, hb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_index_list_walk_frames(orc, torch_cuda, tiny, monkeypatch, kernel):
+    """The FP32 walk over lists of leaf indices (grids whose offsets do not fit
+    the compact lists, and the water layer, use it; HF_FP32_INDEX_LISTS=1
+    forces it here) passes the same frame rules as the walk over the compact
+    lists, for both interpolants."""
+    monkeypatch.setenv("HF_FP32_INDEX_LISTS", "1")
+    for cam in (tiny.cameras[0], tiny.cameras[0].with_(n_cascades=3, cascade_size=131, width=173, height=97)):
+        _frame_parity(orc, torch_cuda, tiny, cam, kernel=kernel)

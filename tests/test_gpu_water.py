@@ -95,9 +95,10 @@ def test_tiny_flood_ragged(orc, torch_cuda, N, W, H, C, lam, wet):
     assert water_px > 0.01
 
 
-def test_dry_field_matches_terrain_only(orc, torch_cuda):
+def test_dry_field_matches_terrain_only(orc, torch_cuda, monkeypatch):
     """All depths 0: no water texel anywhere, and the rays equal the
-    terrain-only library's bit for bit."""
+    terrain-only library's bit for bit (the terrain-only context on the index
+    lists, the walk the water layer uses)."""
     import workloads
     from paper_2201_10887_gb300 import Renderer
     s = workloads.tiny_config()
@@ -105,6 +106,7 @@ def test_dry_field_matches_terrain_only(orc, torch_cuda):
     rw = Renderer(s.tree, s.sigma, s.radius, water=True)
     rw.update_water(np.zeros(s.tree.n_leaves, np.float32))
     tw, hw = rw.render(cam)
+    monkeypatch.setenv("HF_FP32_INDEX_LISTS", "1")
     r0 = Renderer(s.tree, s.sigma, s.radius)
     t0, h0 = r0.render(cam)
     rw.sync()

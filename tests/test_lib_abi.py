@@ -269,18 +269,25 @@ def test_reduced_precision_exponent_scale_range(hfmod, tiny, sigma):
     assert e.value.code == hfmod.HF_ERR_ARG and "normal range" in str(e.value)
 
 
-def test_water_layer_flags_and_sizes(hfmod, tiny):
+def test_water_layer_flags_and_sizes(hfmod, tiny, monkeypatch):
     """The water layer: FP32 only, flag 0/1; it adds 4 bytes per
-    leaf to the persistent buffer and a second texture per cascade (one
-    mipmap bounds both surfaces).  RBF kernels: 0 or 1, FP32 only."""
+    leaf to the persistent buffer of an FP32 context on the index lists and a
+    second texture per cascade (one mipmap bounds both surfaces); a plain FP32
+    context also keeps the compact pair lists, which the water layer does not
+    use.  RBF kernels: 0 or 1, FP32 only."""
     t = tiny.tree
     lv = hfmod.leaves_array(t.level, t.ix, t.iy, t.value)
     desc = hfmod.hf_quadtree_desc(t.origin_x, t.origin_y, t.root_cell, t.root_nx, t.root_ny, t.max_level)
+    compact = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 0, 0))
+    monkeypatch.setenv("HF_FP32_INDEX_LISTS", "1")
     plain = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 0, 0))
+    monkeypatch.delenv("HF_FP32_INDEX_LISTS")
     wet = hfmod.hf_create_quadtree(desc, lv, hfmod.hf_rbf_params(tiny.sigma, tiny.radius, 0, -1, 1, 0))
+    pc, _ = hfmod.hf_query_bytes(compact, 3, 256)
     p0, v0 = hfmod.hf_query_bytes(plain, 3, 256)
     p1, v1 = hfmod.hf_query_bytes(wet, 3, 256)
     assert p1 - p0 >= 4 * t.n_leaves and p1 - p0 < 4 * t.n_leaves + 256
+    assert pc - p0 > 8 * 20 * t.n_leaves  # ~8 bytes per candidate (about 30 per leaf) in pairs
     assert v1 - v0 == 3 * 256 * 256 * 4
     # the coarse-level stop is defined for the terrain alone
     from paper_2201_10887_gb300.renderer import camera_struct
@@ -290,7 +297,7 @@ def test_water_layer_flags_and_sizes(hfmod, tiny):
                                      ct.c_size_t(need)) == hfmod.HF_ERR_ARG
     assert hfmod.lib().hf_set_camera(plain, 0, ct.byref(camera_struct(cam)), ct.c_void_p(1 << 30),
                                      ct.c_size_t(need)) == 0
-    for d in (plain, wet):
+    for d in (compact, plain, wet):
         hfmod.hf_destroy(d)
     for args in ((0, -1, 2, 0), (1, -1, 1, 0), (2, -1, 1, 0), (0, -1, 0, 7), (1, -1, 0, 1), (2, -1, 0, 1)):
         with pytest.raises(hfmod.HFError) as e:

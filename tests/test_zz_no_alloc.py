@@ -76,14 +76,19 @@ def test_noalloc_matches_regular_entry_point(torch_cuda, tiny):
 
 
 @pytest.mark.parametrize("kind", ["fp16", "water"])
-def test_noalloc_is_fp32_terrain_in_any_context(torch_cuda, tiny, kind):
-    """The allocation-free path always evaluates the terrain in FP32: in a
-    context created for the FP16 path, or with the water layer (depths set),
-    it gives the textures of a plain FP32 context over the same leaves."""
+def test_noalloc_is_fp32_terrain_in_any_context(torch_cuda, tiny, kind, monkeypatch):
+    """The allocation-free path always evaluates the terrain in FP32, with the
+    FP32 walk of the context's own lists: in a context created for the FP16
+    path (compact lists, as a plain FP32 context keeps), or with the water
+    layer (depths set; index lists, as a plain FP32 context forced onto them),
+    it gives the textures of that plain FP32 context over the same leaves."""
     import workloads
     from paper_2201_10887_gb300 import Renderer
     torch = torch_cuda
+    if kind == "water":
+        monkeypatch.setenv("HF_FP32_INDEX_LISTS", "1")
     plain = Renderer(tiny.tree, tiny.sigma, tiny.radius)
+    monkeypatch.delenv("HF_FP32_INDEX_LISTS", raising=False)
     if kind == "fp16":
         other = Renderer(tiny.tree, tiny.sigma, tiny.radius, precision=1)
     else:

@@ -517,7 +517,7 @@ def run_ours(args, rank, world, local_rank):
     frame_bound = sum(v["bound_ms"] for v in kern.values())
     dom = max(("discretize", "maxmip", "raycast"), key=lambda k: kern[k]["ms"])
     d = kern[dom]
-    kname = {"discretize": "k_discretize_f32" if args.precision == 0 else "k_discretize_mixed",
+    kname = {"discretize": "k_discretize_f32c" if args.precision == 0 else "k_discretize_mixed",
              "maxmip": "k_mip_lo", "raycast": "k_raycast"}[dom]
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["achieved"] / d["peak"], "traffic": profiled_traffic(kname), "kernel": dom,

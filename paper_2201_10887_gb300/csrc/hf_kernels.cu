@@ -687,7 +687,7 @@ __device__ __forceinline__ void discretize_texel_mixed(const DiscCascade& q, flo
     prefetch_l2(cc, np);
     const uint32_t kb2 = cv.kb2;
     float sw = 0.f, swv = 0.f;
-#pragma unroll 2
+#pragma unroll 3
     for (int k = 0; k < np; ++k) {
         const uint4 c = __ldg(cc + k);
         const T dx = __hsub2(Ops::bits(c.x), PX);
@@ -1123,6 +1123,7 @@ int launch_maxmip(const MipParams& p, void* stream) {
 // walk still climbs to any level above where it may skip.
 //
 // Per-step arithmetic is kept small: exit times are fma(boundary, 1/d, -e/d)
+// (both axes in one packed FP32x2 FMA, which rounds each as fmaf does)
 // with 1/d = 0, -e/d = +inf for an axis-parallel ray (no branch), integer
 // node boundaries become floats by one exact conversion (I2F, on the lightly
 // used conversion pipe), level offsets come from shared memory, and all
@@ -1239,6 +1240,7 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const float idu = d.rdx * c.h, idv = d.rdy * c.h;
     const float ou = d.dx != 0.f ? -r.eu * idu : INFINITY;
     const float ov = d.dy != 0.f ? -r.ev * idv : INFINITY;
+    const float2 iduv = make_float2(idu, idv), ouv = make_float2(ou, ov);
     constexpr int bu = SIGNS & 1, bv = (SIGNS >> 1) & 1;
     constexpr bool zneg = (SIGNS >> 2) & 1;
     const float slack = 2e-6f * fabsf(top);
@@ -1250,8 +1252,9 @@ __device__ __forceinline__ bool trace_cascade(const RayCascade& c, const int* __
     const int budget = c.budget;
     for (int it = 0; it < budget; ++it) {
         const int ni = ci >> k, nj = cj >> k;
-        const float tx = fmaf(__int2float_rn((ni + bu) << k), idu, ou);
-        const float ty = fmaf(__int2float_rn((nj + bv) << k), idv, ov);
+        const float2 txy = __ffma2_rn(make_float2(__int2float_rn((ni + bu) << k), __int2float_rn((nj + bv) << k)),
+                                      iduv, ouv);
+        const float tx = txy.x, ty = txy.y;
         const float te = fmaxf(fminf(fminf(tx, ty), tb), t);
         const float zmin = fmaf(zneg ? te : t, r.dz, ez);
         const float mx = ldc<COH>(mip + off[k] + nj * (P >> k) + ni);

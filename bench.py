@@ -566,18 +566,25 @@ def run_ours(args, rank, world, local_rank):
     }
     kept = {}
     err_frame = len(cams) // 2
+
+    def spread(n):
+        """n of the timed frames, evenly strided over the schedule (so over the
+        whole flight, like the main line), for the shorter variant runs."""
+        step = max(1, len(sched) // n)
+        return sched[::step][:n]
+
     if not args.no_variants:
-        line["precision_variants"] = time_precision_variants(scene, cams, sched[:min(len(sched), 240)],
+        line["precision_variants"] = time_precision_variants(scene, cams, spread(240),
                                                              args.warmup, dev, flush, stream,
                                                              keep_frame=err_frame, kept=kept)
         kept["fp32"] = frame_textures(r, cams[err_frame])
         line["interpolant_variants"] = time_precision_variants(
-            scene, cams, sched[:min(len(sched), 240)], args.warmup, dev, flush, stream,
+            scene, cams, spread(240), args.warmup, dev, flush, stream,
             variants=(("wendland_c2", {"kernel": 1}),))
         line["temporal_reuse"] = time_temporal_reuse(scene, args.warmup, dev, flush, stream)
-        line["coarse_stop"] = time_coarse_stop(scene, cams, sched[:min(len(sched), 120)], args.warmup, dev,
+        line["coarse_stop"] = time_coarse_stop(scene, cams, spread(120), args.warmup, dev,
                                                flush, stream)
-        line["traversal_variants"] = time_traversal_variants(scene, cams, sched[:min(len(sched), 120)],
+        line["traversal_variants"] = time_traversal_variants(scene, cams, spread(120),
                                                              args.warmup, dev, flush, stream)
     if world == 1 and not args.no_blocks:
         # the other workloads, short: terrain + water, 64-tile batched frames, serving

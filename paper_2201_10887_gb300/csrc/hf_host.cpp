@@ -1105,6 +1105,16 @@ int check_kernel_output(const void* p, const char* what) {
     return HF_OK;
 }
 
+// True for pinned host memory (an address check_kernel_output accepted).
+bool host_memory(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 }  // namespace
 
 int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* stream) {
@@ -1118,6 +1128,7 @@ int hf_raycast(hf_ctx* ctx, int32_t slot, float* t_dev, uint8_t* hit_dev, void* 
         RayParams rp = ray_params(v, ctx->rbf.water != 0);
         rp.t_out = t_dev;
         rp.hit_out = hit_dev;
+        rp.host_out = (host_memory(t_dev) || host_memory(hit_dev)) ? 1 : 0;
         int e = launch_raycast(rp, ctx->d_status(), stream);
         if (e) return cuda_fail(e, "ray-cast kernel launch");
         return HF_OK;

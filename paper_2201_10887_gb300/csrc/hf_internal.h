@@ -183,6 +183,7 @@ struct RayParams {
     int32_t water;           // 1: rays meet the terrain or the water surface, whichever comes first
     int32_t coarse;          // 1: some cascade has a coarse-level stop (RayCascade.stop_level > 0)
     int32_t jump;            // 1: after a step the walk climbs to the coarsest node entered (hf_camera.traversal)
+    int32_t host_out;        // 1: t_out or hit_out is pinned host memory (the stores go out in image rows)
     float ez;                // eye height (m)
     float F[3], R[3], U[3];  // camera basis
     float px_a, px_b, py_a, py_b;  // screen coordinates: s = fma(pixel, a, b), s in [-tan, tan]

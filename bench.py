@@ -128,6 +128,13 @@ class ClockSampler:
             self.thread.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # wait for the first sample: nvidia-smi's start-up (NVML initialisation)
+        # can hold up CUDA calls of this process for tens of milliseconds, which
+        # must not land in the timed region
+        deadline = time.perf_counter() + 3.0
+        while not self.lines and self.proc.poll() is None and time.perf_counter() < deadline:
+            time.sleep(0.01)
         return self
 
     def _read(self):
@@ -839,16 +846,18 @@ def time_temporal_reuse(scene, warmup, dev, flush, stream, n=120, ladder=4, seed
     return out
 
 
-def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(2.0, 4.0, 8.0, 16.0)):
+def time_coarse_stop(scene, cams, sched, warmup, dev, flush, stream, lods=(0.0, 2.0, 4.0, 8.0, 16.0)):
     """The coarse-level stop (hf_camera.lod_pixels) on the main line's frames:
     frame and ray-cast time (L2 flushed between frames), node visits per ray,
     and how far the image moves from the exact surface: the share of hit
-    pixels whose t changed and the mean and 99th percentile of |dt| / t."""
+    pixels whose t changed and the mean and 99th percentile of |dt| / t (on
+    24 of the frames, spread over the flight).  lod 0 is the exact walk."""
     import numpy as np
     import torch
     from paper_2201_10887_gb300 import Renderer
     r = Renderer(scene.tree, scene.sigma, scene.radius, device=dev)
-    frames = sorted(set(sched))[:24]
+    distinct = sorted(set(sched))
+    frames = distinct[::max(1, len(distinct) // 24)][:24]
     exact = {}
     for f in frames:
         t, h = r.render(cams[f])
@@ -1000,7 +1009,8 @@ def time_traversal_variants(scene, cams, sched, warmup, dev, flush, stream) -> d
             ev[k][1].record(stream)
         torch.cuda.synchronize(dev)
         visits = 0
-        frames = sorted(set(sched))[:12]
+        distinct = sorted(set(sched))
+        frames = distinct[::max(1, len(distinct) // 12)][:12]
         for f in frames:
             r.render(cl[f])
             visits += r.ray_stats()["visits"]
@@ -1036,7 +1046,8 @@ def serve_block(args) -> dict:
     t0 = time.perf_counter()
     r = Renderer(scene.tree, scene.sigma, scene.radius)
     t_ctx = time.perf_counter() - t0
-    srv = Server(r, int(args.serve_budget_gb * (1 << 30)), max_slots=64, n_streams=3, max_group=16)
+    srv = Server(r, int(args.serve_budget_gb * (1 << 30)), max_slots=64, n_streams=3, max_group=16,
+                 host_budget=4 << 30)
     warm = [workloads.Request(q.rid, 0.0, q.camera) for q in reqs[:24]]
     srv.run(warm, realtime=False)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -1048,6 +1059,7 @@ def serve_block(args) -> dict:
            "frames_per_s": live["frames_per_s"], "offered_rate": 200.0,
            "groups": live["groups"], "mean_group": live["mean_group"],
            "max_memory_used": live["max_memory_used"], "memory_budget": live["memory_budget"],
+           "max_host_memory_used": live["max_host_memory_used"], "host_memory_budget": live["host_memory_budget"],
            "resident_persistent_gb": r.persistent_bytes / 2 ** 30,
            "burst_frames_per_s": burst["frames_per_s"], "burst_mean_group": burst["mean_group"],
            "requests": len(reqs), "leaves": scene.tree.n_leaves, "generation_s": t_gen, "context_s": t_ctx,

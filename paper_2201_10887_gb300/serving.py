@@ -8,8 +8,11 @@ admitted group as one batched frame (``hf_frame_batch``) on the next of a few
 streams -- so groups admitted while others are still running overlap on the
 device.  Each view's ray cast writes its result straight into pinned host
 memory (``host_outputs``; else into device memory, copied afterwards), so the
-device budget holds only the views' cascades.  A request's latency runs from
-its arrival to its result being on the host.
+device budget holds only the views' cascades.  The host side of the results
+comes from one pinned buffer allocated up front (``host_budget`` bytes) and
+handed out like the device memory: pinning memory while serving would stall
+the stream for milliseconds.  A request's latency runs from its arrival to
+its result being on the host.
 Slots and memory are returned as soon as a group's event has completed.
 """
 
@@ -24,7 +27,7 @@ from .renderer import Renderer
 
 
 class Arena:
-    """First-fit allocator over one device buffer (256-byte aligned blocks)."""
+    """First-fit allocator over one buffer (256-byte aligned blocks)."""
 
     def __init__(self, nbytes: int):
         self.size = int(nbytes)
@@ -64,7 +67,7 @@ class Arena:
 class Server:
     def __init__(self, renderer: Renderer, memory_budget: int, max_slots: int = 32,
                  n_streams: int = 3, max_group: int = 16, flags: int = 0, keep_results=False,
-                 host_outputs: bool = True):
+                 host_outputs: bool = True, host_budget: int = 1 << 30):
         import torch
         self.torch = torch
         self.r = renderer
@@ -84,6 +87,10 @@ class Server:
         self.pool = torch.empty(self.budget, dtype=torch.uint8, device=renderer.device)
         self.arena = Arena(self.budget)
         self.max_used = 0
+        self.host_budget = int(host_budget)
+        self.host_pool = torch.empty(self.host_budget, dtype=torch.uint8, pin_memory=True)
+        self.host_arena = Arena(self.host_budget)
+        self.max_host_used = 0
 
     def request_bytes(self, cam) -> int:
         """Device memory of one view: per-view buffer (plus t and hit when
@@ -93,28 +100,27 @@ class Server:
         out = 0 if self.host_outputs else r(4 * npx) + r(npx)
         return r(self.r.view_bytes(cam.n_cascades, cam.cascade_size)) + out
 
-    def _bind(self, req, slot, off):
+    @staticmethod
+    def host_bytes(cam) -> int:
+        """Pinned host memory of one view's results (t and hit)."""
+        npx = cam.width * cam.height
+        return Arena._round(4 * npx) + Arena._round(npx)
+
+    def _bind(self, req, slot, off, hoff):
         cam = req.camera
         r = Arena._round
         vb = r(self.r.view_bytes(cam.n_cascades, cam.cascade_size))
         npx = cam.width * cam.height
         buf = self.pool[off: off + vb]
+        ht = self.host_pool[hoff: hoff + 4 * npx].view(self.torch.float32)
+        hh = self.host_pool[hoff + r(4 * npx): hoff + r(4 * npx) + npx]
+        self.host_out[slot] = (ht, hh)
         if self.host_outputs:
-            t, h = self._host_outputs(slot, cam)
+            t, h = ht, hh
         else:
             t = self.pool[off + vb: off + vb + 4 * npx].view(self.torch.float32)
             h = self.pool[off + vb + r(4 * npx): off + vb + r(4 * npx) + npx]
         self.r.bind_view(slot, cam, buf, t, h)
-
-    def _host_outputs(self, slot, cam):
-        n = cam.width * cam.height
-        cur = self.host_out.get(slot)
-        if cur is None or cur[0].numel() < n:
-            t = self.torch.empty(n, dtype=self.torch.float32, pin_memory=True)
-            h = self.torch.empty(n, dtype=self.torch.uint8, pin_memory=True)
-            cur = (t, h)
-            self.host_out[slot] = cur
-        return cur
 
     def _launch(self, group, k):
         torch = self.torch
@@ -135,7 +141,7 @@ class Server:
                 for req, slot in group:
                     v = self.r.views[slot]
                     n = req.camera.width * req.camera.height
-                    ht, hh = self._host_outputs(slot, req.camera)
+                    ht, hh = self.host_out[slot]
                     ht[:n].copy_(v["t"][:n], non_blocking=True)
                     hh[:n].copy_(v["hit"][:n], non_blocking=True)
         ev = torch.cuda.Event()
@@ -148,7 +154,7 @@ class Server:
         requests are available at once (a throughput run)."""
         waiting = collections.deque()
         inflight = []
-        lat, admitted_at, mem = {}, {}, {}
+        lat, admitted_at, mem, hmem = {}, {}, {}, {}
         results = {}
         nxt, k_stream, groups = 0, 0, 0
         sizes = []
@@ -171,6 +177,7 @@ class Server:
                             results[req.rid] = (ht[:c.width * c.height].numpy().copy(),
                                                 hh[:c.width * c.height].numpy().copy())
                         self.arena.release(mem[req.rid], self.request_bytes(req.camera))
+                        self.host_arena.release(hmem[req.rid], self.host_bytes(req.camera))
                         self.free_slots.append(slot)
                 else:
                     still.append((ev, group))
@@ -178,16 +185,24 @@ class Server:
             group = []
             while waiting and self.free_slots and len(group) < self.max_group:
                 need = self.request_bytes(waiting[0].camera)
-                if need > self.budget:
-                    raise ValueError(f"request {waiting[0].rid} needs {need} bytes, over the budget")
+                hneed = self.host_bytes(waiting[0].camera)
+                if need > self.budget or hneed > self.host_budget:
+                    raise ValueError(f"request {waiting[0].rid} needs {need} device and {hneed} host bytes, "
+                                     f"over the budgets")
                 off = self.arena.alloc(need)
                 if off is None:
+                    break
+                hoff = self.host_arena.alloc(hneed)
+                if hoff is None:
+                    self.arena.release(off, need)
                     break
                 req = waiting.popleft()
                 slot = self.free_slots.pop()
                 mem[req.rid] = off
+                hmem[req.rid] = hoff
                 self.max_used = max(self.max_used, self.arena.used())
-                self._bind(req, slot, off)
+                self.max_host_used = max(self.max_host_used, self.host_arena.used())
+                self._bind(req, slot, off, hoff)
                 admitted_at[req.rid] = time.perf_counter() - t0
                 group.append((req, slot))
             if group:
@@ -204,7 +219,8 @@ class Server:
                "p50_ms": 1e3 * statistics.median(vals), "p99_ms": 1e3 * vals[min(n - 1, int(0.99 * n))],
                "mean_ms": 1e3 * statistics.mean(vals), "groups": groups,
                "mean_group": statistics.mean(sizes) if sizes else 0.0,
-               "max_memory_used": self.max_used, "memory_budget": self.budget}
+               "max_memory_used": self.max_used, "memory_budget": self.budget,
+               "max_host_memory_used": self.max_host_used, "host_memory_budget": self.host_budget}
         if self.keep_results:
             out["results"] = results
         return out

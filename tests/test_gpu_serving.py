@@ -42,14 +42,16 @@ def test_server_results_equal_single_views(torch_cuda, tiny, realtime, host_outp
     from paper_2201_10887_gb300 import Renderer, Server
     r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     reqs = _requests(tiny)
-    probe = Server(r, 1 << 20, max_slots=1, host_outputs=host_outputs)
+    probe = Server(r, 1 << 20, max_slots=1, host_outputs=host_outputs, host_budget=1 << 20)
     sizes = [probe.request_bytes(q.camera) for q in reqs]
     budget = int(2.5 * max(sizes))              # only a few views fit at once
+    hbudget = int(3.5 * max(Server.host_bytes(q.camera) for q in reqs))  # and their results
     srv = Server(r, budget, max_slots=6, n_streams=3, max_group=4, keep_results=True,
-                 host_outputs=host_outputs)
+                 host_outputs=host_outputs, host_budget=hbudget)
     out = srv.run(reqs, realtime=realtime)
     assert out["requests"] == len(reqs) and len(out["results"]) == len(reqs)
     assert out["max_memory_used"] <= budget
+    assert out["max_host_memory_used"] <= hbudget
     assert out["p99_ms"] >= out["p50_ms"] > 0
     if not realtime:
         assert out["mean_group"] > 1.0           # requests were batched together
@@ -66,7 +68,7 @@ def test_server_rejects_a_request_over_the_budget(torch_cuda, tiny):
     from paper_2201_10887_gb300 import Renderer, Server
     r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     reqs = _requests(tiny, n=2)
-    srv = Server(r, 4096, max_slots=2)
+    srv = Server(r, 4096, max_slots=2, host_budget=1 << 20)
     with pytest.raises(ValueError):
         srv.run(reqs, realtime=False)
     r.close()

@@ -24,9 +24,12 @@ def torch_cuda():
     return torch
 
 
-def _water_frame(orc, scene, cam, depth, texel_sample=None, seed=0):
+def _water_frame(orc, scene, cam, depth, texel_sample=None, seed=0, r=None):
+    """The water frame of `cam` against the oracle (on renderer r, whose
+    depths are then replaced by `depth`, or on a fresh one)."""
     from paper_2201_10887_gb300 import Renderer
-    r = Renderer(scene.tree, scene.sigma, scene.radius, water=True)
+    if r is None:
+        r = Renderer(scene.tree, scene.sigma, scene.radius, water=True)
     r.update_water(depth)
     t, hit = r.render(cam)
     r.sync()
@@ -121,8 +124,9 @@ def test_dry_field_matches_terrain_only(orc, torch_cuda, monkeypatch):
 
 
 def test_depth_update_between_frames(orc, torch_cuda):
-    """A new depth field (a higher flood) replaces the old one without a
-    rebuild; the next frame matches the oracle on the new depths."""
+    """A new depth field (a higher flood) replaces the old one in the same
+    context without a rebuild; the next frame matches the oracle on the new
+    depths."""
     import workloads
     from paper_2201_10887_gb300 import Renderer
     s = workloads.tiny_flood_config(wet_area=0.1)
@@ -130,9 +134,8 @@ def test_depth_update_between_frames(orc, torch_cuda):
     r.update_water(s.depth)
     r.render(s.cameras[0])
     r.sync()
-    r.close()
     deeper, _ = workloads.flood_depths(s.tree, 0.45)
-    water_px, _ = _water_frame(orc, s, s.cameras[0], deeper)
+    water_px, _ = _water_frame(orc, s, s.cameras[0], deeper, r=r)
     assert water_px > 0.1
 
 

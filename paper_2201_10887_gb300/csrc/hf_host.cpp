@@ -1015,6 +1015,7 @@ int hf_build_maxmip(hf_ctx* ctx, int32_t slot, void* stream) {
         for (int k = 0; k < C; ++k) {
             mp.cas[k].tex = v->tex[k];
             mp.cas[k].wtex = v->wtex[k];
+            mp.cas[k].spans = v->spans[k];
             mp.cas[k].mip = v->mip[k];
             mp.cas[k].N = N;
             mp.cas[k].P = mp.max_P;
@@ -1317,6 +1318,7 @@ int hf_batch_prepare(const hf_batch_item* items, int32_t n, int32_t flags, void*
                 fill_prep_cascade(v, k, B.prep);
                 B.disc = dp.cas[k];
                 B.mip.tex = v->tex[k];
+                B.mip.spans = v->spans[k];
                 B.mip.mip = v->mip[k];
                 B.mip.N = N;
                 B.mip.P = P;

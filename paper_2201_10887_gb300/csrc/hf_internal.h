@@ -153,6 +153,7 @@ struct DiscParams {
 struct MipCascade {
     const float* tex;
     const float* wtex;  // water surface: level 0 bounds both patches (two = 1 only)
+    const int2* spans;  // visible span per texel row (texels outside it hold -inf); null: read every texel
     float* mip;
     int32_t N, P, K;
 };

@@ -35,10 +35,12 @@ def _requests(tiny, n=24, seed=3, span=0.15):
     return reqs
 
 
-@pytest.mark.parametrize("realtime,host_outputs", [(False, True), (True, True), (False, False)])
-def test_server_results_equal_single_views(torch_cuda, tiny, realtime, host_outputs):
+@pytest.mark.parametrize("realtime,host_outputs,single", [(False, True, True), (True, True, True),
+                                                          (False, False, True), (True, True, False)])
+def test_server_results_equal_single_views(torch_cuda, tiny, realtime, host_outputs, single):
     """Each result equals the view rendered alone, with the ray casts writing
-    into pinned host memory or into device memory copied afterwards."""
+    into pinned host memory or into device memory copied afterwards, and
+    groups of one request run through the per-view calls or as a batch."""
     from paper_2201_10887_gb300 import Renderer, Server
     r = Renderer(tiny.tree, tiny.sigma, tiny.radius)
     reqs = _requests(tiny)
@@ -47,7 +49,7 @@ def test_server_results_equal_single_views(torch_cuda, tiny, realtime, host_outp
     budget = int(2.5 * max(sizes))              # only a few views fit at once
     hbudget = int(3.5 * max(Server.host_bytes(q.camera) for q in reqs))  # and their results
     srv = Server(r, budget, max_slots=6, n_streams=3, max_group=4, keep_results=True,
-                 host_outputs=host_outputs, host_budget=hbudget)
+                 host_outputs=host_outputs, host_budget=hbudget, single_view_calls=single)
     out = srv.run(reqs, realtime=realtime)
     assert out["requests"] == len(reqs) and len(out["results"]) == len(reqs)
     assert out["max_memory_used"] <= budget

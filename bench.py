@@ -1070,7 +1070,9 @@ def serve_block(args) -> dict:
     srv = Server(r, int(args.serve_budget_gb * (1 << 30)), max_slots=64, n_streams=3, max_group=16,
                  host_budget=4 << 30)
     warm = [workloads.Request(q.rid, 0.0, q.camera) for q in reqs[:24]]
-    srv.run(warm, realtime=False)
+    srv.run(warm, realtime=False)                # batched groups
+    srv.run([workloads.Request(q.rid, 0.005 * i, q.camera) for i, q in enumerate(reqs[:24])],
+            realtime=True)                       # groups of one, as the live run forms them
     with ClockSampler(torch.cuda.current_device()) as clk:
         live = srv.run(reqs, realtime=True)
     burst = srv.run(reqs, realtime=False)
